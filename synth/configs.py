@@ -1,0 +1,130 @@
+"""Geometry descriptions of the workloads (plain data, no method arithmetic).
+
+Shared by the oracle-side tests, the GPU-side tests and the benchmark.  The
+ELT numbers follow the paper's parameter table and system-settings table
+(Sec. 5.1): 39 m pupil with ~28 % central obstruction, 84x84 Shack-Hartmann
+sensors, LGS at H = 90 km, alpha = 2, r0 = 0.129 m.  Where the paper gives no
+value (layer profile, asterism of the benchmark, grid sizes) the workload
+recipe below states the choice.
+"""
+import math
+from dataclasses import dataclass, field
+from typing import List
+
+ARCSEC = math.pi / 648000.0
+
+
+@dataclass
+class GuideStar:
+    theta_x: float  # direction [rad]
+    theta_y: float
+    H: float = 0.0  # LGS height [m]; 0 = natural guide star (no cone effect)
+
+
+@dataclass
+class Layer:
+    h: float        # height [m]
+    cn2: float      # fraction of the turbulence strength
+    n: int          # layer grid size (n x n nodes, power of two)
+    J: int          # wavelet levels
+    delta: float = 1.0  # scaling constant delta_l of Eq. fewha
+
+
+@dataclass
+class Geometry:
+    name: str
+    D: float
+    obstruction: float
+    n_sub: int
+    gs: List[GuideStar]
+    layers: List[Layer]
+    r0: float = 0.129
+    L0: float = 25.0
+    alpha: float = 2.0
+    wavelet_N: int = 3   # Daubechies-3 (6 taps)
+    k_recycle: int = 8
+    snr: float = 10.0
+    wind: List[tuple] = field(default_factory=list)  # per layer (speed m/s, direction rad)
+
+    @property
+    def n_unknowns(self):
+        return sum(l.n * l.n for l in self.layers)
+
+    @property
+    def n_slopes(self):
+        return 2 * self.n_sub * self.n_sub * len(self.gs)
+
+
+def _ring(n, radius_rad, H, phase=0.0):
+    return [GuideStar(radius_rad * math.cos(phase + 2 * math.pi * k / n),
+                      radius_rad * math.sin(phase + 2 * math.pi * k / n), H) for k in range(n)]
+
+
+def _winds(n_layers, seed):
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    speeds = rng.uniform(5.0, 20.0, n_layers)
+    dirs = rng.uniform(0.0, 2 * math.pi, n_layers)
+    return [(float(s), float(d)) for s, d in zip(speeds, dirs)]
+
+
+def tiny() -> Geometry:
+    """8 m, 16x16 SH, 4 NGS at 30'' (azimuth 0/90/180/270 deg), layers 0 m / 8 km
+    (Cn2 0.7 / 0.3) on 32x32 grids, Daubechies-3 with 3 levels."""
+    return Geometry("tiny", D=8.0, obstruction=0.0, n_sub=16,
+                    gs=_ring(4, 30 * ARCSEC, 0.0),
+                    layers=[Layer(0.0, 0.7, 32, 3), Layer(8000.0, 0.3, 32, 3)],
+                    r0=0.15, L0=25.0, wind=_winds(2, 1000))
+
+
+def elt() -> Geometry:
+    """39 m, 28 % obstruction, 6 LGS at 90 km on a 1' radius ring (60 deg
+    steps), 84x84 SH; 9 layers at 0, 2, ..., 16 km with Cn2 ~ exp(-h/4 km),
+    128x128 grids up to 8 km and 64x64 above; Daubechies-3 with 5 levels."""
+    hs = [2000.0 * i for i in range(9)]
+    w = [math.exp(-h / 4000.0) for h in hs]
+    tot = sum(w)
+    layers = [Layer(h, wi / tot, 128 if h <= 8000.0 else 64, 5) for h, wi in zip(hs, w)]
+    return Geometry("elt", D=39.0, obstruction=0.28, n_sub=84,
+                    gs=_ring(6, 60 * ARCSEC, 90000.0), layers=layers,
+                    r0=0.129, L0=25.0, k_recycle=8, wind=_winds(9, 1001))
+
+
+def medium() -> Geometry:
+    """16 m, 40x40 SH, 4 LGS at 90 km on a 45'' ring, 5 layers on 64x64 grids
+    (0-12 km), Daubechies-3 with 4 levels (the mid-size batched instance)."""
+    hs = [0.0, 3000.0, 6000.0, 9000.0, 12000.0]
+    w = [math.exp(-h / 4000.0) for h in hs]
+    tot = sum(w)
+    return Geometry("medium", D=16.0, obstruction=0.2, n_sub=40,
+                    gs=_ring(4, 45 * ARCSEC, 90000.0, phase=math.pi / 4),
+                    layers=[Layer(h, wi / tot, 64, 4) for h, wi in zip(hs, w)],
+                    r0=0.15, wind=_winds(5, 1002))
+
+
+def micro() -> Geometry:
+    """2 m, 4x4 SH, one NGS and one LGS, two 8x8 layers with 2 wavelet levels:
+    n = 128 unknowns, small enough for dense assembly and exact CG."""
+    return Geometry("micro", D=2.0, obstruction=0.0, n_sub=4,
+                    gs=[GuideStar(10 * ARCSEC, -5 * ARCSEC, 0.0),
+                        GuideStar(-20 * ARCSEC, 15 * ARCSEC, 90000.0)],
+                    layers=[Layer(0.0, 0.6, 8, 2), Layer(5000.0, 0.4, 8, 2, delta=1.5)],
+                    r0=0.2, wind=_winds(2, 1003))
+
+
+def mixed_ngs_lgs() -> Geometry:
+    """Small mixed asterism: 2 NGS + 3 LGS, 3 layers of different sizes and
+    scaling constants (exercises every code path of the operator)."""
+    return Geometry("mixed", D=10.0, obstruction=0.25, n_sub=20,
+                    gs=[GuideStar(40 * ARCSEC, 0.0, 0.0), GuideStar(-30 * ARCSEC, 25 * ARCSEC, 0.0)]
+                    + _ring(3, 35 * ARCSEC, 90000.0, phase=0.3),
+                    layers=[Layer(0.0, 0.5, 32, 3), Layer(4000.0, 0.3, 32, 4, delta=0.7),
+                            Layer(10000.0, 0.2, 16, 2, delta=1.3)],
+                    r0=0.14, wind=_winds(3, 1004))
+
+
+CONFIGS = {"tiny": tiny, "elt": elt, "medium": medium, "micro": micro, "mixed": mixed_ngs_lgs}
+
+
+def get(name: str) -> Geometry:
+    return CONFIGS[name]()

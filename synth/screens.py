@@ -1,0 +1,141 @@
+"""Seeded synthetic wavefront-sensor data: von Karman frozen-flow turbulence
+seen by Shack-Hartmann sensors.
+
+This is the stand-in for the paper's end-to-end simulator (MOST, Sec. 5.1),
+which is not available.  It models the sky, not the reconstructor: each layer
+is a periodic von Karman phase screen (FFT method, r0_l = r0 cn2_l^{-3/5},
+outer scale L0) on a grid twice as fine as the subapertures, moved by its wind
+vector every frame (frozen flow).  A sensor measures, per subaperture, the
+difference of the mean phase on opposite edges (three points per edge), with
+the phase at a point being the sum over layers of the screens sampled at the
+point's position on each layer (cone compression for laser guide stars).
+White Gaussian noise with sigma_g = rms(noise-free slopes of g)/SNR is added.
+None of the reconstructor's discrete operators (bilinear layer
+interpolation, the four-node gradient, wavelets) is used here.
+"""
+import math
+
+import numpy as np
+import torch
+
+
+def pupil_mask(geom) -> np.ndarray:
+    """Illuminated subapertures: centre radius within [obstruction*D/2, D/2]."""
+    ns, D = geom.n_sub, geom.D
+    c = -D / 2 + (np.arange(ns) + 0.5) * D / ns
+    r = np.hypot(c[None, :], c[:, None])
+    return ((r >= geom.obstruction * D / 2) & (r <= D / 2)).reshape(-1)
+
+
+def random_vector(n, seed, dtype=np.float64):
+    """Standard normal test vector of length n (seeded)."""
+    return np.random.default_rng(seed).standard_normal(n).astype(dtype)
+
+
+class FrozenFlowSensors:
+    """Noise-free and noisy Shack-Hartmann slopes for a sequence of frames."""
+
+    def __init__(self, geom, seed=0, device="cpu", oversample=2, frame_rate=500.0):
+        self.geom = geom
+        self.device = torch.device(device)
+        self.dt = 1.0 / frame_rate
+        ns, D = geom.n_sub, geom.D
+        self.ds = D / ns
+        self.step = self.ds / oversample
+        rmax = 0.0
+        for l in geom.layers:
+            for g in geom.gs:
+                s = (1.0 - l.h / g.H) if g.H > 0 else 1.0
+                rmax = max(rmax, s * D / 2 + max(abs(g.theta_x), abs(g.theta_y)) * l.h)
+        M = 64
+        while M < 2 * rmax / self.step + 8:
+            M *= 2
+        self.M = M
+        rng = np.random.default_rng(seed)
+        f = np.fft.fftfreq(M, self.step)
+        fx, fy = np.meshgrid(f, f)
+        f2 = fx * fx + fy * fy
+        df = 1.0 / (M * self.step)
+        screens = []
+        for l in geom.layers:
+            r0l = geom.r0 * l.cn2 ** (-3.0 / 5.0)
+            psd = 0.023 * r0l ** (-5.0 / 3.0) * (f2 + 1.0 / geom.L0 ** 2) ** (-11.0 / 6.0)
+            psd[0, 0] = 0.0
+            cn = (rng.standard_normal((M, M)) + 1j * rng.standard_normal((M, M))) * np.sqrt(psd) * df
+            screens.append(np.real(np.fft.ifft2(cn)) * M * M)
+        self.screens = torch.tensor(np.stack(screens), dtype=torch.float64, device=self.device)
+        winds = geom.wind if geom.wind else [(10.0, 0.0)] * len(geom.layers)
+        self.wind = [(s * math.cos(d), s * math.sin(d)) for s, d in winds]
+        # edge sample points on the pupil
+        t = torch.tensor([1.0 / 6, 0.5, 5.0 / 6], dtype=torch.float64, device=self.device)
+        nodes = -D / 2 + torch.arange(ns + 1, dtype=torch.float64, device=self.device) * self.ds
+        rows = -D / 2 + (torch.arange(ns, dtype=torch.float64, device=self.device)[:, None] + t) * self.ds
+        # vertical edges: x = nodes[j], y = rows[i, e]   -> (ns, ns+1, 3)
+        self.vx = nodes[None, :, None].expand(ns, ns + 1, 3)
+        self.vy = rows[:, None, :].expand(ns, ns + 1, 3)
+        # horizontal edges: y = nodes[i], x = rows[j, e] -> (ns+1, ns, 3)
+        self.hx = rows[None, :, :].expand(ns + 1, ns, 3)
+        self.hy = nodes[:, None, None].expand(ns + 1, ns, 3)
+        self.mask = pupil_mask(geom)
+
+    def _sample(self, l, px, py):
+        M, st = self.M, self.step
+        u = px / st + M / 2
+        v = py / st + M / 2
+        iu = torch.floor(u)
+        iv = torch.floor(v)
+        fu, fv = u - iu, v - iv
+        iu = iu.long() % M
+        iv = iv.long() % M
+        iu1, iv1 = (iu + 1) % M, (iv + 1) % M
+        S = self.screens[l]
+        return ((1 - fv) * ((1 - fu) * S[iv, iu] + fu * S[iv, iu1])
+                + fv * ((1 - fu) * S[iv1, iu] + fu * S[iv1, iu1]))
+
+    def _phase(self, g, frame, x, y):
+        tot = torch.zeros_like(x)
+        for l, lay in enumerate(self.geom.layers):
+            s = (1.0 - lay.h / g.H) if g.H > 0 else 1.0
+            wx, wy = self.wind[l]
+            ox = g.theta_x * lay.h - wx * frame * self.dt
+            oy = g.theta_y * lay.h - wy * frame * self.dt
+            tot = tot + self._sample(l, s * x + ox, s * y + oy)
+        return tot
+
+    def clean_slopes(self, frame) -> torch.Tensor:
+        """Noise-free slopes of all sensors, [x block | y block] per guide star."""
+        out = []
+        for g in self.geom.gs:
+            V = self._phase(g, frame, self.vx, self.vy).mean(-1)  # (ns, ns+1)
+            Hh = self._phase(g, frame, self.hx, self.hy).mean(-1)  # (ns+1, ns)
+            sx = V[:, 1:] - V[:, :-1]
+            sy = Hh[1:, :] - Hh[:-1, :]
+            out += [sx.reshape(-1), sy.reshape(-1)]
+        return torch.cat(out)
+
+    def noise_sigma(self) -> np.ndarray:
+        """sigma_g = rms of the noise-free slopes of g on lit subapertures / SNR."""
+        s0 = self.clean_slopes(0).cpu().numpy()
+        ns2 = self.geom.n_sub ** 2
+        sig = []
+        for g in range(len(self.geom.gs)):
+            blk = s0[2 * ns2 * g: 2 * ns2 * (g + 1)]
+            v = np.concatenate([blk[:ns2][self.mask], blk[ns2:][self.mask]])
+            sig.append(math.sqrt(float(np.mean(v * v))) / self.geom.snr)
+        return np.array(sig)
+
+    def sequence(self, n_frames, seed=1, noise=True, dtype=torch.float64, first_frame=0):
+        """Returns (slopes [n_frames, n_slopes] on self.device, noise weights 1/sigma^2)."""
+        sig = self.noise_sigma()
+        gen = torch.Generator(device=self.device)
+        gen.manual_seed(seed)
+        ns2 = self.geom.n_sub ** 2
+        sig_vec = torch.tensor(np.repeat(sig, 2 * ns2), dtype=torch.float64, device=self.device)
+        frames = torch.empty((n_frames, self.geom.n_slopes), dtype=dtype, device=self.device)
+        for t in range(n_frames):
+            s = self.clean_slopes(first_frame + t)
+            if noise:
+                s = s + sig_vec * torch.randn(s.shape, generator=gen, dtype=torch.float64,
+                                              device=self.device)
+            frames[t] = s.to(dtype)
+        return frames, 1.0 / sig ** 2
