@@ -1,0 +1,171 @@
+/*
+ * fewha.h - C ABI of the GB300 (sm_103a) augmented-FEWHA tomography library.
+ *
+ * The library applies the FEWHA normal operator
+ *     M = W^{-T} A^T C_eta^{-1} A W^{-1} + alpha D            (Ramlau & Stadler, Sec. 3, Eq. M)
+ * matrix-free on the GPU and solves M c = b with preconditioned CG
+ * (Algorithm 1) or augmented, Krylov-recycled PCG (Algorithm 2) inside one
+ * time step of the reconstructor loop (Algorithm 3: right-hand side, warm
+ * restart residual, solve).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Status: every function returns 0 (FEWHA_OK) or a negative FEWHA_ERR_*
+ *    code; nothing throws across the ABI.  Errors raised on the device
+ *    (barrier timeout, CG breakdown) are reported in fewha_stats.status,
+ *    valid after the stream has been synchronised.
+ *  - Memory: all vectors passed to the compute calls are DEVICE pointers owned
+ *    by the caller, allocated on the device the handle was created on.  The
+ *    handle owns its constant tables and its scratch memory.  Nothing is
+ *    retained after a call returns except the handle's own state.
+ *  - Element type of the vectors: double for FEWHA_F64 handles, float for
+ *    FEWHA_F32 and FEWHA_BF16S handles.  Slopes are double / float /
+ *    bfloat16 (raw 16-bit, round-to-nearest-even) respectively.
+ *  - Layout of a coefficient vector c (length n = sum_l n_l^2): layer after
+ *    layer; inside a layer the n_l x n_l array of periodic Daubechies wavelet
+ *    coefficients in row-major Mallat layout (coarsest approximation block in
+ *    the top-left corner; at every level the block right of it is low-pass in
+ *    y and high-pass in x, the block below high-pass in y and low-pass in x).
+ *  - Layout of a slope vector s (length 2 n_s^2 G): guide star after guide
+ *    star, each [x slopes | y slopes], each n_s x n_s row-major (row = y).
+ *    Entries of unlit subapertures are ignored.
+ *  - Asynchrony: compute calls enqueue work on the given stream and return.
+ */
+#ifndef FEWHA_H
+#define FEWHA_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *cudaStream_t;
+
+#define FEWHA_MAX_GS 16
+#define FEWHA_MAX_LAYERS 16
+#define FEWHA_MAX_K 16        /* largest recycled basis */
+#define FEWHA_MAX_ITER 1000   /* largest max_iter of one solve */
+#define FEWHA_MAX_GRID 128    /* largest layer grid (n_l); the layer must fit one SM's shared memory */
+
+enum {
+    FEWHA_OK = 0,
+    FEWHA_ERR_ARG = -1,       /* bad pointer, size or option */
+    FEWHA_ERR_GEOMETRY = -2,  /* inconsistent telescope / layer geometry */
+    FEWHA_ERR_CUDA = -3,      /* a CUDA runtime call failed */
+    FEWHA_ERR_TIMEOUT = -4,   /* a device-side wait gave up (grid barrier) */
+    FEWHA_ERR_BREAKDOWN = -5, /* CG breakdown: (p, Mp) <= 0 or not finite */
+    FEWHA_ERR_NOT_SPD = -6,   /* recycled Gram matrix not positive definite */
+    FEWHA_ERR_NOMEM = -7      /* device allocation failed */
+};
+
+enum { FEWHA_F64 = 0, FEWHA_F32 = 1, FEWHA_BF16S = 2 };
+
+/* Guide star (Sec. 2): direction theta [rad]; H = sodium-layer height [m] for
+ * a laser guide star (cone effect, P^LGS), H <= 0 for a natural guide star
+ * (P^NGS); weight = 1/sigma^2, the diagonal of C_eta^{-1} on its lit
+ * subapertures (Sec. 3). */
+typedef struct {
+    double theta_x, theta_y, H, weight;
+} fewha_gs;
+
+/* Turbulent layer (Sec. 2, Eq. atmo): height h [m], Cn2 fraction (prior D),
+ * node grid n x n (power of two, 8..FEWHA_MAX_GRID), J wavelet levels
+ * (n >> J >= 1), scaling constant delta of W = diag(delta_l W) (Eq. fewha). */
+typedef struct {
+    double h, cn2, delta;
+    int n, J;
+} fewha_layer;
+
+/* Telescope, sensors and layers (Sec. 2, Sec. 5.1 parameter table). */
+typedef struct {
+    double D;             /* pupil diameter [m] */
+    double obstruction;   /* central obstruction, fraction of D */
+    int n_sub;            /* Shack-Hartmann subapertures across the pupil (n_s) */
+    int n_gs;
+    fewha_gs gs[FEWHA_MAX_GS];
+    int n_layers;
+    fewha_layer layers[FEWHA_MAX_LAYERS];
+    double r0;            /* Fried parameter [m] of the prior D */
+    double alpha;         /* regularisation weight alpha of Eq. fewha */
+    int wavelet_N;        /* Daubechies vanishing moments (3 = Daubechies-3, 6 taps), 1..4 */
+    int precision;        /* FEWHA_F64, FEWHA_F32 or FEWHA_BF16S */
+    int tile;             /* WFS tile edge in pupil nodes (8, 16 or 32); 0 = default */
+    int grid;             /* CTAs of the solver launch; 0 = one per SM */
+} fewha_geometry;
+
+/* Per-time-step solver state (Algorithm 3 inputs and outputs), caller-owned
+ * device memory of the handle's vector type:
+ *   b_prev[n], r_prev[n]   previous right-hand side and residual (zero at frame 0);
+ *   basis_P[2*k_cap*n], basis_Q[2*k_cap*n]   two banks of recycled directions
+ *                          p and q = M p (the solve reads one bank, writes the other);
+ *   basis_pq[2*k_cap]      (p_j, q_j) in double;
+ *   meta[4]                ints: active bank, directions in it, newest slot,
+ *                          frames solved (all zero at frame 0). */
+typedef struct {
+    void *b_prev, *r_prev, *basis_P, *basis_Q;
+    double *basis_pq;
+    int *meta;
+    int k_cap;            /* 1..FEWHA_MAX_K */
+} fewha_state;
+
+enum { FEWHA_RECYCLE_LAST = 0, FEWHA_RECYCLE_ALL = 1 };
+enum { FEWHA_LAUNCH_PERSISTENT = 0, FEWHA_LAUNCH_PHASES = 1 };
+
+typedef struct {
+    int max_iter;         /* iterations k = 0..max_iter-1 (1..FEWHA_MAX_ITER) */
+    double rtol;          /* > 0: stop once ||r|| <= rtol ||b|| (recurrence residual) */
+    int augmented;        /* 0: PCG (Algorithm 1); 1: augmented PCG (Algorithm 2) */
+    int recycle_mode;     /* FEWHA_RECYCLE_LAST (paper) or FEWHA_RECYCLE_ALL */
+    int launch_mode;      /* FEWHA_LAUNCH_PERSISTENT (one kernel) or FEWHA_LAUNCH_PHASES */
+    int reserved;
+} fewha_solve_opts;
+
+/* Written on the device at the end of fewha_solve. */
+typedef struct {
+    int status;           /* FEWHA_OK or a device-side FEWHA_ERR_* */
+    int iterations;       /* PCG iterations run */
+    double rel_res;       /* ||r|| / ||b|| of the recurrence residual at exit */
+    double bnorm;         /* ||b|| */
+    double rz;            /* (r, z) at exit */
+    int basis_count;      /* recycled directions available to the next frame */
+    int pad;
+} fewha_stats;
+
+/* Builds the operator for one geometry (Sec. 2-4): layer grids, interpolation
+ * tables of P_g, subaperture mask, prior D, Daubechies taps, and the modified
+ * Jacobi preconditioner J (computed on the GPU in FP64 from sampled diagonal
+ * entries of M).  Uses the current CUDA device.  Blocking. */
+int fewha_create(const fewha_geometry *geom, void **handle_out);
+
+/* Frees the handle and its device memory (synchronises the device). */
+void fewha_destroy(void *handle);
+
+/* n (unknowns), slopes (2 n_s^2 G), and the layer spacing d_l [m]. */
+long fewha_n_unknowns(const void *handle);
+long fewha_n_slopes(const void *handle);
+double fewha_layer_spacing(const void *handle, int layer);
+
+/* Copies the diagonal of alpha*D (Sec. 3) or of J^{-1} (Sec. 4) to host memory (n doubles). */
+int fewha_get_prior(const void *handle, double *alpha_d_host);
+int fewha_get_precond(const void *handle, double *invJ_host);
+
+/* y = M x (Eq. M).  x, y: device vectors of length n; must not overlap. */
+int fewha_apply_op(void *handle, const void *x, void *y, cudaStream_t stream);
+
+/* b = W^{-T} A^T C_eta^{-1} s (right-hand side of Eq. fewha; Algorithm 3). */
+int fewha_rhs(void *handle, const void *s, void *b, cudaStream_t stream);
+
+/* One reconstructor time step (Algorithm 3, RHS to augPCG):
+ *   b = rhs(s); r0 = (b - b_prev) + r_prev; b_prev <- b;
+ *   (aug)PCG from the warm start c, updating c (in/out, device, n) and r_prev;
+ *   the directions of this solve become the recycled basis of the next one.
+ * stats_dev: device pointer to a fewha_stats, written at the end. */
+int fewha_solve(void *handle, const void *s, void *c, const fewha_state *state,
+                const fewha_solve_opts *opts, fewha_stats *stats_dev, cudaStream_t stream);
+
+/* Text of a status code. */
+const char *fewha_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FEWHA_H */

@@ -1,0 +1,413 @@
+// Kernels of the FEWHA hot path and the per-precision implementation
+// object that launches them (internal to libfewha).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstddef>
+#include <cstring>
+#include <vector>
+
+#include "plan.h"
+#include "solver.cuh"
+
+namespace fewha {
+
+// ---------------------------------------------------------------------------
+// kernels
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T *dyn_smem()
+{
+    extern __shared__ __align__(16) unsigned char fewha_smem[];
+    return reinterpret_cast<T *>(fewha_smem);
+}
+
+// apply: nodal = W^{-1} x
+template <typename T, typename S>
+__global__ void __launch_bounds__(kThreads, 1) k_apply_idwt(Args<T, S> A)
+{
+    layer_idwt<T, S>(A, dyn_smem<T>(), [&](long e) -> T { return A.x[e]; });
+}
+
+// psi = Gamma^T C Gamma P nodal (RHS = false) or Gamma^T C s (RHS = true)
+template <typename T, typename S, bool RHS>
+__global__ void __launch_bounds__(kThreads, 1) k_wfs(Args<T, S> A)
+{
+    __shared__ double sred[8 * 32];
+    if (ldcgi(&A.rec->done) || ldcgi(&A.rec->status)) return;
+    double acc[1] = {wfs_phase<T, S, RHS>(A, dyn_smem<T>())};
+    const int slots[1] = {kSlotB};
+    block_partials<1>(acc, A.part, slots, sred);
+}
+
+// y = W^{-T} P^T psi + alpha D x  (APPLY) or y = W^{-T} P^T psi (RHS)
+template <typename T, typename S, bool RHS>
+__global__ void __launch_bounds__(kThreads, 1) k_adj(Args<T, S> A)
+{
+    layer_adj<T, S>(A, dyn_smem<T>(), [&](long e, T v) {
+        A.y[e] = RHS ? v : v + A.geo.alpha_d[e] * A.x[e];
+    });
+}
+
+// --- solver phases, one kernel each (FEWHA_LAUNCH_PHASES) -------------------
+#define FEWHA_PHASE_GUARD                                             \
+    __shared__ Scal sc;                                               \
+    __shared__ double sred[8 * 32];                                   \
+    (void)sred;                                                       \
+    if (ldcgi(&A.rec->done) || ldcgi(&A.rec->status)) return;         \
+    const Basis b = basis_info(A);                                    \
+    (void)b;
+
+template <typename T, typename S>
+__global__ void __launch_bounds__(kThreads, 1) k_rhs_wfs(Args<T, S> A)
+{
+    wfs_phase<T, S, true>(A, dyn_smem<T>());
+}
+
+template <typename T, typename S>
+__global__ void __launch_bounds__(kThreads, 1) k_rhs_adj(Args<T, S> A)
+{
+    FEWHA_PHASE_GUARD
+    (void)sc;
+    phase_rhs_adj<T, S>(A, dyn_smem<T>(), sred);
+}
+
+template <typename T, typename S>
+__global__ void __launch_bounds__(kThreads, 1) k_gram(Args<T, S> A)
+{
+    FEWHA_PHASE_GUARD
+    (void)sc;
+    if (b.kv > 0) phase_gram<T, S>(A, b);
+}
+
+template <typename T, typename S>
+__global__ void __launch_bounds__(kThreads, 1) k_init(Args<T, S> A)
+{
+    FEWHA_PHASE_GUARD
+    if (b.kv > 0) phase_init<T, S>(A, b, sc);
+}
+
+template <typename T, typename S>
+__global__ void __launch_bounds__(kThreads, 1) k_A(Args<T, S> A, int k)
+{
+    FEWHA_PHASE_GUARD
+    phase_A<T, S>(A, b, k, dyn_smem<T>(), sc, sred);
+}
+
+template <typename T, typename S>
+__global__ void __launch_bounds__(kThreads, 1) k_B(Args<T, S> A, int k)
+{
+    FEWHA_PHASE_GUARD
+    (void)sc;
+    double acc[1] = {wfs_phase<T, S, false>(A, dyn_smem<T>())};
+    const int slots[1] = {kSlotB + (k & 1)};
+    block_partials<1>(acc, A.part, slots, sred);
+}
+
+template <typename T, typename S>
+__global__ void __launch_bounds__(kThreads, 1) k_CD(Args<T, S> A, int k)
+{
+    FEWHA_PHASE_GUARD
+    phase_CD<T, S>(A, b, k, dyn_smem<T>(), sc);
+}
+
+template <typename T, typename S>
+__global__ void __launch_bounds__(kThreads, 1) k_E(Args<T, S> A, int k)
+{
+    FEWHA_PHASE_GUARD
+    (void)sc;
+    phase_E<T, S>(A, b, k, sred);
+}
+
+template <typename T, typename S>
+__global__ void __launch_bounds__(kThreads, 1) k_finish(Args<T, S> A)
+{
+    __shared__ Scal sc;
+    if (blockIdx.x != 0) return;
+    const Basis b = basis_info(A);
+    int K = ldcgi(&A.rec->done) ? ldcgi(&A.rec->iters) : A.max_iter;
+    phase_finish<T, S>(A, b, K, sc);
+}
+
+// --- the whole time step in one persistent cooperative kernel ---------------
+template <typename T, typename S>
+__global__ void __launch_bounds__(kThreads, 1) k_solve_persistent(Args<T, S> A)
+{
+    __shared__ Scal sc;
+    __shared__ double sred[8 * 32];
+    T *sm = dyn_smem<T>();
+    const unsigned long long to = A.timeout_ns;
+    const Basis b = basis_info(A);
+    int K = A.max_iter;
+    do {
+        wfs_phase<T, S, true>(A, sm);
+        if (!grid_sync(A.rec, to)) break;
+        phase_rhs_adj<T, S>(A, sm, sred);
+        if (!grid_sync(A.rec, to)) break;
+        if (b.kv > 0) {
+            phase_gram<T, S>(A, b);
+            if (!grid_sync(A.rec, to)) break;
+            bool ok = phase_init<T, S>(A, b, sc);
+            if (!grid_sync(A.rec, to) || !ok) break;
+        }
+        for (int k = 0; k < A.max_iter; k++) {
+            if (!phase_A<T, S>(A, b, k, sm, sc, sred)) {
+                K = k;
+                break;
+            }
+            if (!grid_sync(A.rec, to)) break;
+            {
+                double acc[1] = {wfs_phase<T, S, false>(A, sm)};
+                const int slots[1] = {kSlotB + (k & 1)};
+                block_partials<1>(acc, A.part, slots, sred);
+            }
+            if (!grid_sync(A.rec, to)) break;
+            if (!phase_CD<T, S>(A, b, k, sm, sc)) {
+                K = k;
+                break;
+            }
+            if (!grid_sync(A.rec, to)) break;
+            phase_E<T, S>(A, b, k, sred);
+            if (!grid_sync(A.rec, to)) break;
+        }
+    } while (0);
+    // on a device-side error the stats carry the status; the other fields are
+    // then not meaningful
+    if (blockIdx.x == 0) phase_finish<T, S>(A, b, K, sc);
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+#define CK(x)                                   \
+    do {                                        \
+        cudaError_t _e = (x);                   \
+        if (_e != cudaSuccess) return FEWHA_ERR_CUDA; \
+    } while (0)
+
+template <typename T>
+static int upload(const std::vector<T> &v, T **d)
+{
+    *d = nullptr;
+    if (v.empty()) return FEWHA_OK;
+    if (cudaMalloc(d, v.size() * sizeof(T)) != cudaSuccess) return FEWHA_ERR_NOMEM;
+    CK(cudaMemcpy(*d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return FEWHA_OK;
+}
+
+struct ImplBase {
+    virtual ~ImplBase() {}
+    virtual int init(int grid) = 0;
+    virtual int get_invJ(double *host) const = 0;
+    virtual int apply(const void *x, void *y, cudaStream_t s) = 0;
+    virtual int rhs(const void *sl, void *b, cudaStream_t s) = 0;
+    virtual int solve(const void *sl, void *c, const fewha_state *st, const fewha_solve_opts *o,
+                      fewha_stats *stats, cudaStream_t s) = 0;
+    virtual int set_invJ(const std::vector<double> &invJ) = 0;
+};
+
+template <typename T, typename S>
+struct Impl : ImplBase {
+    const Plan &P;
+    Args<T, S> base{};
+    int ncta = 1;
+    size_t smem = 0;
+    std::vector<void *> owned;
+
+    explicit Impl(const Plan &p) : P(p) {}
+    ~Impl() override
+    {
+        for (void *q : owned) cudaFree(q);
+    }
+
+    template <typename U>
+    int up(const std::vector<U> &v, const U **d)
+    {
+        U *dd;
+        int st = upload(v, &dd);
+        if (dd) owned.push_back(dd);
+        *d = dd;
+        return st;
+    }
+    template <typename U>
+    int alloc(size_t count, U **d)
+    {
+        if (cudaMalloc(d, count * sizeof(U)) != cudaSuccess) return FEWHA_ERR_NOMEM;
+        owned.push_back(*d);
+        CK(cudaMemset(*d, 0, count * sizeof(U)));
+        return FEWHA_OK;
+    }
+
+    int init(int grid) override
+    {
+        Geo<T> &G = base.geo;
+        G.G = P.G;
+        G.L = P.L;
+        G.ns = P.ns;
+        G.m = P.m;
+        G.n = P.n;
+        for (int l = 0; l < P.L; l++) {
+            G.lay_n[l] = P.geom.layers[l].n;
+            G.lay_J[l] = P.geom.layers[l].J;
+            G.lay_off[l] = P.lay_off[l];
+            G.inv_delta[l] = (T)(1.0 / P.geom.layers[l].delta);
+        }
+        G.lay_off[P.L] = P.lay_off[P.L];
+        G.n_taps = (int)P.taps.size();
+        for (int t = 0; t < kMaxT; t++) {
+            G.h[t] = t < G.n_taps ? (T)P.taps[t] : T(0);
+            G.g[t] = t < G.n_taps ? (T)(((t & 1) ? -1.0 : 1.0) * P.taps[G.n_taps - 1 - t]) : T(0);
+        }
+        int tile = P.geom.tile ? P.geom.tile : 16;
+        G.tile = tile;
+        G.tiles_x = (P.m + tile - 1) / tile;
+        int st;
+        if ((st = up(P.fk, &G.fk)) || (st = up(P.alo, &G.alo)) || (st = up(P.ahi, &G.ahi))) return st;
+        std::vector<T> fw(P.fw.begin(), P.fw.end());
+        std::vector<T> wm((size_t)P.G * P.ns * P.ns);
+        for (int g = 0; g < P.G; g++)
+            for (int i = 0; i < P.ns * P.ns; i++)
+                wm[(size_t)g * P.ns * P.ns + i] = P.mask[i] ? (T)P.geom.gs[g].weight : T(0);
+        std::vector<T> ad(P.alpha_d.begin(), P.alpha_d.end());
+        std::vector<T> one(P.n, T(1));
+        if ((st = up(fw, &G.fw)) || (st = up(wm, &G.wmask)) || (st = up(ad, &G.alpha_d)) ||
+            (st = up(one, &G.invJ)))
+            return st;
+        if ((st = alloc((size_t)P.n, &base.nodal)) || (st = alloc((size_t)P.G * P.m * P.m, &base.psi)) ||
+            (st = alloc((size_t)kSlots * kMaxCtas, &base.part)) || (st = alloc((size_t)1, &base.rec)))
+            return st;
+        // launch geometry: dynamic shared memory = max over phases
+        int nmax = 0;
+        for (int l = 0; l < P.L; l++) nmax = std::max(nmax, P.geom.layers[l].n);
+        size_t sm_layer = (size_t)nmax * nmax * sizeof(T);
+        int H = tile + 2, SB = tile + 1;
+        size_t sm_wfs = ((size_t)P.L * H * H + 2 * SB * SB) * sizeof(T);
+        smem = std::max(sm_layer, sm_wfs);
+        int dev, nsm;
+        CK(cudaGetDevice(&dev));
+        CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+        auto setattr = [&](const void *f) {
+            return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        };
+        CK(setattr((const void *)k_apply_idwt<T, S>));
+        CK(setattr((const void *)k_wfs<T, S, false>));
+        CK(setattr((const void *)k_wfs<T, S, true>));
+        CK(setattr((const void *)k_adj<T, S, false>));
+        CK(setattr((const void *)k_adj<T, S, true>));
+        CK(setattr((const void *)k_rhs_wfs<T, S>));
+        CK(setattr((const void *)k_rhs_adj<T, S>));
+        CK(setattr((const void *)k_gram<T, S>));
+        CK(setattr((const void *)k_init<T, S>));
+        CK(setattr((const void *)k_A<T, S>));
+        CK(setattr((const void *)k_B<T, S>));
+        CK(setattr((const void *)k_CD<T, S>));
+        CK(setattr((const void *)k_E<T, S>));
+        CK(setattr((const void *)k_finish<T, S>));
+        CK(setattr((const void *)k_solve_persistent<T, S>));
+        int per_sm = 0;
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve_persistent<T, S>, kThreads, smem));
+        if (per_sm < 1) return FEWHA_ERR_CUDA;
+        ncta = grid > 0 ? grid : nsm;
+        if (ncta > nsm * per_sm) ncta = nsm * per_sm;
+        if (ncta > kMaxCtas) ncta = kMaxCtas;
+        base.timeout_ns = 1000000000ull;
+        base.ncta = ncta;
+        return FEWHA_OK;
+    }
+
+    int get_invJ(double *host) const override
+    {
+        std::vector<T> v(P.n);
+        CK(cudaMemcpy(v.data(), base.geo.invJ, P.n * sizeof(T), cudaMemcpyDeviceToHost));
+        for (long i = 0; i < P.n; i++) host[i] = (double)v[i];
+        return FEWHA_OK;
+    }
+
+    int set_invJ(const std::vector<double> &invJ) override
+    {
+        std::vector<T> v(invJ.begin(), invJ.end());
+        CK(cudaMemcpy(const_cast<T *>(base.geo.invJ), v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+        return FEWHA_OK;
+    }
+
+    int launch_check() { return cudaGetLastError() == cudaSuccess ? FEWHA_OK : FEWHA_ERR_CUDA; }
+
+    int apply(const void *x, void *y, cudaStream_t s) override
+    {
+        Args<T, S> A = base;
+        A.x = static_cast<const T *>(x);
+        A.y = static_cast<T *>(y);
+        CK(cudaMemsetAsync(A.rec, 0, offsetof(Record, rz), s));
+        k_apply_idwt<T, S><<<ncta, kThreads, smem, s>>>(A);
+        k_wfs<T, S, false><<<ncta, kThreads, smem, s>>>(A);
+        k_adj<T, S, false><<<ncta, kThreads, smem, s>>>(A);
+        return launch_check();
+    }
+
+    int rhs(const void *sl, void *b, cudaStream_t s) override
+    {
+        Args<T, S> A = base;
+        A.slopes = static_cast<const S *>(sl);
+        A.y = static_cast<T *>(b);
+        CK(cudaMemsetAsync(A.rec, 0, offsetof(Record, rz), s));
+        k_wfs<T, S, true><<<ncta, kThreads, smem, s>>>(A);
+        k_adj<T, S, true><<<ncta, kThreads, smem, s>>>(A);
+        return launch_check();
+    }
+
+    int solve(const void *sl, void *c, const fewha_state *st, const fewha_solve_opts *o,
+              fewha_stats *stats, cudaStream_t s) override
+    {
+        Args<T, S> A = base;
+        A.slopes = static_cast<const S *>(sl);
+        A.c = static_cast<T *>(c);
+        A.r = static_cast<T *>(st->r_prev);
+        A.b_prev = static_cast<T *>(st->b_prev);
+        A.P = static_cast<T *>(st->basis_P);
+        A.Q = static_cast<T *>(st->basis_Q);
+        A.pq = st->basis_pq;
+        A.meta = st->meta;
+        A.kcap = st->k_cap;
+        A.max_iter = o->max_iter;
+        A.rtol = o->rtol;
+        A.augmented = o->augmented ? 1 : 0;
+        A.recycle_all = o->recycle_mode == FEWHA_RECYCLE_ALL ? 1 : 0;
+        A.stats = stats;
+        CK(cudaMemsetAsync(A.rec, 0, offsetof(Record, rz), s));
+        CK(cudaMemsetAsync(&A.rec->bar, 0, sizeof(Bar), s));
+        if (o->launch_mode == FEWHA_LAUNCH_PERSISTENT) {
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(ncta);
+            cfg.blockDim = dim3(kThreads);
+            cfg.dynamicSmemBytes = smem;
+            cfg.stream = s;
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeCooperative;
+            attr[0].val.cooperative = 1;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            CK(cudaLaunchKernelEx(&cfg, k_solve_persistent<T, S>, A));
+            return launch_check();
+        }
+        k_rhs_wfs<T, S><<<ncta, kThreads, smem, s>>>(A);
+        k_rhs_adj<T, S><<<ncta, kThreads, smem, s>>>(A);
+        k_gram<T, S><<<ncta, kThreads, smem, s>>>(A);
+        k_init<T, S><<<ncta, kThreads, smem, s>>>(A);
+        for (int k = 0; k < A.max_iter; k++) {
+            k_A<T, S><<<ncta, kThreads, smem, s>>>(A, k);
+            k_B<T, S><<<ncta, kThreads, smem, s>>>(A, k);
+            k_CD<T, S><<<ncta, kThreads, smem, s>>>(A, k);
+            k_E<T, S><<<ncta, kThreads, smem, s>>>(A, k);
+        }
+        k_finish<T, S><<<1, kThreads, smem, s>>>(A);
+        return launch_check();
+    }
+};
+
+
+ImplBase *make_impl_f64(const Plan &p);
+ImplBase *make_impl_f32(const Plan &p);
+ImplBase *make_impl_bf16(const Plan &p);
+
+}  // namespace fewha

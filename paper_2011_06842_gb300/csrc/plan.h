@@ -1,0 +1,45 @@
+// Host-side planning of the FEWHA operator: geometry, interpolation tables,
+// Daubechies taps, prior and the preconditioner's sampling plan.
+// Internal header of libfewha (not part of the C ABI).
+#pragma once
+#include <vector>
+
+#include "../../include/fewha.h"
+
+namespace fewha {
+
+constexpr int kMaxTaps = 8;
+
+struct Plan {
+    fewha_geometry geom;
+    int G = 0, L = 0, ns = 0, m = 0;  // guide stars, layers, subapertures across, pupil nodes across
+    long n = 0;                       // unknowns
+    double ds = 0;                    // subaperture size
+    std::vector<double> taps;         // Daubechies low-pass h_0..h_{2N-1}
+    std::vector<unsigned char> mask;  // ns*ns lit subapertures
+    std::vector<double> lay_d;        // layer grid spacing
+    std::vector<long> lay_off;        // L+1 offsets into the coefficient vector
+    // P_g tables, index ((g*L + l)*2 + axis)*m + j  (axis 0 = x, 1 = y)
+    std::vector<int> fk;              // lower node index of pupil node j on layer l
+    std::vector<double> fw;           // fractional position in that cell
+    // P_g^T ranges, index ((g*L + l)*2 + axis)*FEWHA_MAX_GRID + k: pupil nodes
+    // [alo, ahi) whose cell touches layer node k
+    std::vector<int> alo, ahi;
+    std::vector<double> alpha_d;      // n, alpha * D
+    // preconditioner sampling: class of every coefficient, and the sampled
+    // coefficients (global index, class)
+    int n_classes = 0;
+    std::vector<int> coef_class;
+    std::vector<long> sample_idx;
+    std::vector<int> sample_class;
+};
+
+// Daubechies-N low-pass taps from the spectral factorisation of the
+// half-band polynomial (own complex root finder).  Returns false on failure.
+bool daubechies_taps(int N, std::vector<double> &h);
+
+// Validates the geometry and fills every host table.  Returns FEWHA_OK or
+// FEWHA_ERR_ARG / FEWHA_ERR_GEOMETRY.
+int build_plan(const fewha_geometry &g, Plan &p);
+
+}  // namespace fewha

@@ -1,0 +1,260 @@
+"""Python binding of libfewha (include/fewha.h): argument marshalling only.
+
+Every computation runs in the CUDA library; this module builds the C
+structures, passes device pointers of torch tensors and the current CUDA
+stream, and turns status codes into exceptions.  There is no fallback: if
+libfewha.so is missing or no GPU is present the calls raise.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfewha.so")
+
+MAX_GS, MAX_LAYERS, MAX_K, MAX_ITER = 16, 16, 16, 1000
+F64, F32, BF16S = 0, 1, 2
+RECYCLE_LAST, RECYCLE_ALL = 0, 1
+LAUNCH_PERSISTENT, LAUNCH_PHASES = 0, 1
+PRECISIONS = {"f64": F64, "f32": F32, "bf16s": BF16S}
+
+ERRORS = {0: "ok", -1: "FEWHA_ERR_ARG", -2: "FEWHA_ERR_GEOMETRY", -3: "FEWHA_ERR_CUDA",
+          -4: "FEWHA_ERR_TIMEOUT", -5: "FEWHA_ERR_BREAKDOWN", -6: "FEWHA_ERR_NOT_SPD",
+          -7: "FEWHA_ERR_NOMEM"}
+
+
+class FewhaError(RuntimeError):
+    def __init__(self, status, what=""):
+        self.status = status
+        super().__init__("%s failed: %s (%d)" % (what, ERRORS.get(status, "?"), status))
+
+
+class GS(C.Structure):
+    _fields_ = [("theta_x", C.c_double), ("theta_y", C.c_double), ("H", C.c_double),
+                ("weight", C.c_double)]
+
+
+class LAYER(C.Structure):
+    _fields_ = [("h", C.c_double), ("cn2", C.c_double), ("delta", C.c_double), ("n", C.c_int),
+                ("J", C.c_int)]
+
+
+class GEOMETRY(C.Structure):
+    _fields_ = [("D", C.c_double), ("obstruction", C.c_double), ("n_sub", C.c_int),
+                ("n_gs", C.c_int), ("gs", GS * MAX_GS), ("n_layers", C.c_int),
+                ("layers", LAYER * MAX_LAYERS), ("r0", C.c_double), ("alpha", C.c_double),
+                ("wavelet_N", C.c_int), ("precision", C.c_int), ("tile", C.c_int), ("grid", C.c_int)]
+
+
+class STATE(C.Structure):
+    _fields_ = [("b_prev", C.c_void_p), ("r_prev", C.c_void_p), ("basis_P", C.c_void_p),
+                ("basis_Q", C.c_void_p), ("basis_pq", C.c_void_p), ("meta", C.c_void_p),
+                ("k_cap", C.c_int)]
+
+
+class OPTS(C.Structure):
+    _fields_ = [("max_iter", C.c_int), ("rtol", C.c_double), ("augmented", C.c_int),
+                ("recycle_mode", C.c_int), ("launch_mode", C.c_int), ("reserved", C.c_int)]
+
+
+class STATS(C.Structure):
+    _fields_ = [("status", C.c_int), ("iterations", C.c_int), ("rel_res", C.c_double),
+                ("bnorm", C.c_double), ("rz", C.c_double), ("basis_count", C.c_int),
+                ("pad", C.c_int)]
+
+
+STATS_BYTES = C.sizeof(STATS)
+_lib = None
+
+
+def load_library(path=LIB_PATH):
+    """Loads libfewha.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("libfewha.so not found at %s: run paper_2011_06842_gb300.build.build()" % path)
+    lib = C.CDLL(path)
+    vp, dp = C.c_void_p, C.POINTER(C.c_double)
+    lib.fewha_create.argtypes = [C.POINTER(GEOMETRY), C.POINTER(vp)]
+    lib.fewha_create.restype = C.c_int
+    lib.fewha_destroy.argtypes = [vp]
+    lib.fewha_destroy.restype = None
+    lib.fewha_n_unknowns.argtypes = [vp]
+    lib.fewha_n_unknowns.restype = C.c_long
+    lib.fewha_n_slopes.argtypes = [vp]
+    lib.fewha_n_slopes.restype = C.c_long
+    lib.fewha_layer_spacing.argtypes = [vp, C.c_int]
+    lib.fewha_layer_spacing.restype = C.c_double
+    lib.fewha_get_prior.argtypes = [vp, dp]
+    lib.fewha_get_precond.argtypes = [vp, dp]
+    lib.fewha_apply_op.argtypes = [vp, vp, vp, vp]
+    lib.fewha_rhs.argtypes = [vp, vp, vp, vp]
+    lib.fewha_solve.argtypes = [vp, vp, vp, C.POINTER(STATE), C.POINTER(OPTS), vp, vp]
+    lib.fewha_strerror.argtypes = [C.c_int]
+    lib.fewha_strerror.restype = C.c_char_p
+    for name in ("fewha_create", "fewha_get_prior", "fewha_get_precond", "fewha_apply_op",
+                 "fewha_rhs", "fewha_solve"):
+        getattr(lib, name).restype = C.c_int
+    _lib = lib
+    return lib
+
+
+def exported_symbols():
+    """Entry points declared in include/fewha.h."""
+    return ["fewha_create", "fewha_destroy", "fewha_n_unknowns", "fewha_n_slopes",
+            "fewha_layer_spacing", "fewha_get_prior", "fewha_get_precond", "fewha_apply_op",
+            "fewha_rhs", "fewha_solve", "fewha_strerror"]
+
+
+def make_geometry(geom, noise_w, precision="f64", tile=0, grid=0) -> GEOMETRY:
+    """C geometry from a description object (attributes D, obstruction, n_sub,
+    gs[theta_x, theta_y, H], layers[h, cn2, n, J, delta], r0, alpha, wavelet_N)."""
+    g = GEOMETRY()
+    g.D, g.obstruction, g.n_sub = geom.D, geom.obstruction, geom.n_sub
+    if len(geom.gs) > MAX_GS or len(geom.layers) > MAX_LAYERS:
+        raise ValueError("too many guide stars or layers")
+    g.n_gs = len(geom.gs)
+    for i, (s, w) in enumerate(zip(geom.gs, noise_w)):
+        g.gs[i] = GS(s.theta_x, s.theta_y, s.H, float(w))
+    g.n_layers = len(geom.layers)
+    for i, l in enumerate(geom.layers):
+        g.layers[i] = LAYER(l.h, l.cn2, l.delta, l.n, l.J)
+    g.r0, g.alpha, g.wavelet_N = geom.r0, geom.alpha, geom.wavelet_N
+    g.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    g.tile, g.grid = tile, grid
+    return g
+
+
+def _stream_ptr(torch):
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+class FewhaState:
+    """Caller-owned per-time-step state (device tensors) of fewha_solve."""
+
+    def __init__(self, torch, n, kcap, dtype, device):
+        if not 1 <= kcap <= MAX_K:
+            raise ValueError("k_cap must be in 1..%d" % MAX_K)
+        self.kcap = kcap
+        self.b_prev = torch.zeros(n, dtype=dtype, device=device)
+        self.r_prev = torch.zeros(n, dtype=dtype, device=device)
+        self.P = torch.zeros((2, kcap, n), dtype=dtype, device=device)
+        self.Q = torch.zeros((2, kcap, n), dtype=dtype, device=device)
+        self.pq = torch.zeros((2, kcap), dtype=torch.float64, device=device)
+        self.meta = torch.zeros(4, dtype=torch.int32, device=device)
+        self.c_struct = STATE(self.b_prev.data_ptr(), self.r_prev.data_ptr(), self.P.data_ptr(),
+                              self.Q.data_ptr(), self.pq.data_ptr(), self.meta.data_ptr(), kcap)
+
+    def basis(self):
+        """Recycled directions (P, Q, pq), oldest first (synchronises)."""
+        active, count, head, _ = [int(v) for v in self.meta.cpu()]
+        slots = [(head - count + 1 + j) % self.kcap for j in range(count)]
+        return self.P[active, slots], self.Q[active, slots], self.pq[active, slots]
+
+
+class Fewha:
+    """One operator / solver instance on the current CUDA device."""
+
+    def __init__(self, geom, noise_w, precision="f64", tile=0, grid=0):
+        import torch
+        self._torch = torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("libfewha needs a CUDA device")
+        self.lib = load_library()
+        self.precision = precision
+        self._g = make_geometry(geom, noise_w, precision, tile, grid)
+        h = C.c_void_p()
+        st = self.lib.fewha_create(C.byref(self._g), C.byref(h))
+        if st != 0:
+            raise FewhaError(st, "fewha_create")
+        self._h = h
+        self.n = self.lib.fewha_n_unknowns(h)
+        self.n_slopes = self.lib.fewha_n_slopes(h)
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self.dtype = torch.float64 if precision == "f64" else torch.float32
+        self.slope_dtype = {"f64": torch.float64, "f32": torch.float32, "bf16s": torch.bfloat16}[precision]
+        self.n_layers = len(geom.layers)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self.lib.fewha_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- host-side tables -------------------------------------------------
+    def layer_spacing(self, l):
+        return self.lib.fewha_layer_spacing(self._h, l)
+
+    def prior(self):
+        out = np.empty(self.n)
+        self._check(self.lib.fewha_get_prior(self._h, out.ctypes.data_as(C.POINTER(C.c_double))), "get_prior")
+        return out
+
+    def precond(self):
+        out = np.empty(self.n)
+        self._check(self.lib.fewha_get_precond(self._h, out.ctypes.data_as(C.POINTER(C.c_double))),
+                    "get_precond")
+        return out
+
+    def _check(self, st, what):
+        if st != 0:
+            raise FewhaError(st, what)
+
+    def _vec(self, t, n, dtype, name):
+        torch = self._torch
+        if not isinstance(t, torch.Tensor) or t.device.type != "cuda" or t.dtype != dtype:
+            raise TypeError("%s must be a CUDA tensor of %s" % (name, dtype))
+        if t.numel() != n or not t.is_contiguous():
+            raise ValueError("%s must be contiguous with %d elements" % (name, n))
+        return C.c_void_p(t.data_ptr())
+
+    # -- compute ------------------------------------------------------------
+    def apply_op(self, x, out=None):
+        """y = M x (Eq. M)."""
+        y = out if out is not None else self._torch.empty(self.n, dtype=self.dtype, device=self.device)
+        self._check(self.lib.fewha_apply_op(self._h, self._vec(x, self.n, self.dtype, "x"),
+                                            self._vec(y, self.n, self.dtype, "y"),
+                                            _stream_ptr(self._torch)), "fewha_apply_op")
+        return y
+
+    def rhs(self, s, out=None):
+        """b = W^{-T} A^T C_eta^{-1} s."""
+        b = out if out is not None else self._torch.empty(self.n, dtype=self.dtype, device=self.device)
+        self._check(self.lib.fewha_rhs(self._h, self._vec(s, self.n_slopes, self.slope_dtype, "s"),
+                                       self._vec(b, self.n, self.dtype, "b"), _stream_ptr(self._torch)),
+                    "fewha_rhs")
+        return b
+
+    def new_state(self, kcap):
+        return FewhaState(self._torch, self.n, kcap, self.dtype, self.device)
+
+    def new_stats(self):
+        return self._torch.zeros(STATS_BYTES, dtype=self._torch.uint8, device=self.device)
+
+    def solve(self, s, c, state, max_iter, rtol=0.0, augmented=True, recycle_all=False,
+              persistent=True, stats=None):
+        """One time step; c is updated in place.  Returns the device stats buffer."""
+        o = OPTS(int(max_iter), float(rtol), 1 if augmented else 0,
+                 RECYCLE_ALL if recycle_all else RECYCLE_LAST,
+                 LAUNCH_PERSISTENT if persistent else LAUNCH_PHASES, 0)
+        stats = stats if stats is not None else self.new_stats()
+        self._check(self.lib.fewha_solve(self._h, self._vec(s, self.n_slopes, self.slope_dtype, "s"),
+                                         self._vec(c, self.n, self.dtype, "c"), C.byref(state.c_struct),
+                                         C.byref(o), C.c_void_p(stats.data_ptr()),
+                                         _stream_ptr(self._torch)), "fewha_solve")
+        return stats
+
+    @staticmethod
+    def read_stats(stats):
+        """Host copy of a stats buffer as a dict (synchronises)."""
+        raw = bytes(stats.cpu().numpy().tobytes())
+        st = STATS.from_buffer_copy(raw)
+        return {"status": st.status, "iterations": st.iterations, "rel_res": st.rel_res,
+                "bnorm": st.bnorm, "rz": st.rz, "basis_count": st.basis_count}

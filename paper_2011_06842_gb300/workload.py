@@ -1,0 +1,58 @@
+"""Algorithmic work of one PCG iteration: the paper's FLOP model and the byte
+count used for the roofline.
+
+``pcg_flops_per_iter`` is the per-iteration formula of Table FEWHAFLOPs
+(Sec. 7.1), generalised to layers of different sizes by summing the
+per-layer terms.  ``aug_init_flops`` and ``aug_proj_flops`` are the two
+augmented rows of that table (per iteration / per solve, n_augIter factor
+left to the caller).
+
+``bytes_per_iter`` counts the algorithmic traffic of one iteration of the
+persistent solver: every intermediate written once and read once, solver
+vectors at their storage width.
+"""
+
+
+def pcg_flops_per_iter(G_NGS, G_LGS, n_s, layer_sizes):
+    G = G_NGS + G_LGS
+    L = len(layer_sizes)
+    f = (14 * G_LGS + 2 * G_NGS + 12 * G) * n_s ** 2 + 4 * G * n_s
+    f += ((L - 1) * (15.6 * G_LGS + 18 * G_NGS) + L * (G - 1)) * (n_s + 1) ** 2
+    f += sum(176.0 / 3.0 * (4 * n * n - 1) + 13 * n * n for n in layer_sizes)
+    return f
+
+
+def aug_init_flops(layer_sizes):
+    return 9 * sum(n * n for n in layer_sizes)
+
+
+def aug_proj_flops(layer_sizes):
+    return 4 * sum(n * n for n in layer_sizes)
+
+
+def aug_memory_bytes(layer_sizes, k, word=4):
+    """(2 n_lay^2 L + 1) k words of extra storage (Sec. 7.2)."""
+    return (2 * sum(n * n for n in layer_sizes) + 1) * k * word
+
+
+def geometry_counts(geom):
+    g_lgs = sum(1 for g in geom.gs if g.H > 0)
+    return dict(G_NGS=len(geom.gs) - g_lgs, G_LGS=g_lgs, n_s=geom.n_sub,
+                layer_sizes=[l.n for l in geom.layers])
+
+
+def bytes_per_iter(geom, word=4, augmented=True):
+    """Algorithmic bytes of one solver iteration (operator + vector updates).
+
+    Operator intermediates, each written once and read once: nodal layers (n),
+    adjoint wavefronts (G (n_s+1)^2).  Solver vectors: read p, r, c, q, J^{-1},
+    prior, p_m, q_m (augmented) and write p, q, c, r (q and p land in the
+    recycled-basis slot, no copy).
+    """
+    n = sum(l.n * l.n for l in geom.layers)
+    G = len(geom.gs)
+    m2 = (geom.n_sub + 1) ** 2
+    op = 2 * n + 2 * G * m2
+    vec_reads = 6 + (2 if augmented else 0)
+    vec_writes = 4
+    return word * (op + (vec_reads + vec_writes) * n)

@@ -1,0 +1,184 @@
+"""GPU parity: the CUDA library (through its C ABI) against the FP64 oracle on
+the same seeded inputs.
+
+Tolerances (relative L2 error over the whole vector): 1e-10 for the FP64
+path, 1e-5 for the FP32 path (operator applications and few-iteration
+solves); the BF16-storage path is compared with the error bound derived in
+the design notes.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import Oracle  # noqa: E402
+from synth import FrozenFlowSensors, configs, random_vector  # noqa: E402
+
+TOL = {"f64": 1e-10, "f32": 1e-5}
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2011_06842_gb300 import build
+    build.build()
+    import paper_2011_06842_gb300 as P
+    return P
+
+
+_cache = {}
+
+
+def setup(name, nframes=6, seed=7):
+    key = (name, nframes, seed)
+    if key not in _cache:
+        geom = configs.get(name)
+        sim = FrozenFlowSensors(geom, seed=seed)
+        s, w = sim.sequence(nframes, seed=seed + 1)
+        o = Oracle(geom, w)
+        _cache[key] = (geom, s.numpy(), w, o)
+    return _cache[key]
+
+
+def dev(x, dtype):
+    return torch.tensor(np.asarray(x), dtype=dtype, device="cuda")
+
+
+@pytest.mark.parametrize("name", ["micro", "tiny", "mixed"])
+def test_tables_match_oracle(lib, name):
+    geom, s, w, o = setup(name)
+    f = lib.Fewha(geom, w, "f64")
+    for l in range(len(geom.layers)):
+        assert abs(f.layer_spacing(l) - o.layer_spacing(l)) <= 1e-14 * o.layer_spacing(l)
+    assert rel(f.prior(), geom.alpha * o.prior()) < 1e-13
+    assert rel(f.precond(), o.invJ()) < 1e-11
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("name", ["micro", "tiny", "mixed"])
+def test_apply_op_and_rhs(lib, name, prec):
+    geom, s, w, o = setup(name)
+    f = lib.Fewha(geom, w, prec)
+    dt = torch.float64 if prec == "f64" else torch.float32
+    for seed in (1, 2):
+        x = random_vector(o.n, seed)
+        y = f.apply_op(dev(x, dt)).cpu().numpy()
+        assert rel(y, o.apply_op(x)) < TOL[prec], (name, prec)
+    b = f.rhs(dev(s[0], dt)).cpu().numpy()
+    assert rel(b, o.rhs(s[0])) < TOL[prec]
+
+
+@pytest.mark.parametrize("tile", [8, 16, 32])
+@pytest.mark.parametrize("grid", [1, 3, 0])
+def test_apply_op_tiles_and_grids(lib, tile, grid):
+    """Ragged tiles (n_s + 1 not a multiple of the tile) and CTAs that own
+    several layers / tiles give the same operator."""
+    geom, s, w, o = setup("mixed")
+    f = lib.Fewha(geom, w, "f64", tile=tile, grid=grid)
+    x = random_vector(o.n, 5)
+    assert rel(f.apply_op(dev(x, torch.float64)).cpu().numpy(), o.apply_op(x)) < 1e-10
+
+
+def _run_sequence(lib, o, f, s, nframes, max_iter, aug, kcap, persistent, prec, rtol=0.0,
+                  recycle_all=False):
+    dt = torch.float64 if prec == "f64" else torch.float32
+    st_o = o.new_state(kcap)
+    st_g = f.new_state(kcap)
+    c = torch.zeros(o.n, dtype=dt, device="cuda")
+    out = []
+    for t in range(nframes):
+        ro = o.solve(s[t], st_o, max_iter=max_iter, augmented=aug, rtol=rtol,
+                     loop_mode=Oracle.LOOP_ALL if recycle_all else Oracle.LOOP_LAST)
+        stats = f.solve(dev(s[t], dt), c, st_g, max_iter=max_iter, rtol=rtol, augmented=aug,
+                        recycle_all=recycle_all, persistent=persistent)
+        rg = f.read_stats(stats)
+        assert rg["status"] == 0, rg
+        out.append((ro, rg, rel(c.cpu().numpy(), st_o["c"]), rel(st_g.r_prev.cpu().numpy(), st_o["r_prev"]),
+                    st_o, st_g))
+    return out
+
+
+@pytest.mark.parametrize("persistent", [True, False])
+@pytest.mark.parametrize("aug", [False, True])
+@pytest.mark.parametrize("name", ["micro", "tiny"])
+def test_solve_sequence_f64(lib, name, aug, persistent):
+    geom, s, w, o = setup(name)
+    f = lib.Fewha(geom, w, "f64")
+    res = _run_sequence(lib, o, f, s, 5, max_iter=4, aug=aug, kcap=4, persistent=persistent, prec="f64")
+    for ro, rg, ec, er, st_o, st_g in res:
+        assert rg["iterations"] == ro["iterations"]
+        assert ec < 1e-10 and er < 1e-9, (ec, er)
+        assert abs(rg["rel_res"] - ro["rel_res"]) <= 1e-9 * ro["rel_res"]
+    # recycled basis, oldest first
+    P, Q, pq = st_g.basis()
+    kv = st_o["k_valid"]
+    assert P.shape[0] == kv
+    assert rel(P.cpu().numpy(), st_o["P"][:kv]) < 1e-9
+    assert rel(Q.cpu().numpy(), st_o["Q"][:kv]) < 1e-9
+    assert rel(pq.cpu().numpy(), st_o["pq"][:kv]) < 1e-10
+
+
+def test_solve_recycle_all_f64(lib):
+    geom, s, w, o = setup("tiny")
+    f = lib.Fewha(geom, w, "f64")
+    res = _run_sequence(lib, o, f, s, 4, max_iter=5, aug=True, kcap=5, persistent=True, prec="f64",
+                        recycle_all=True)
+    for ro, rg, ec, er, _, _ in res:
+        assert ec < 1e-9 and er < 1e-8
+
+
+@pytest.mark.parametrize("aug", [False, True])
+def test_solve_sequence_f32(lib, aug):
+    geom, s, w, o = setup("tiny")
+    f = lib.Fewha(geom, w, "f32")
+    res = _run_sequence(lib, o, f, s, 4, max_iter=4, aug=aug, kcap=4, persistent=True, prec="f32")
+    for ro, rg, ec, er, _, _ in res:
+        assert ec < 1e-5, ec
+
+
+def test_solve_rtol_stopping_f64(lib):
+    geom, s, w, o = setup("tiny")
+    f = lib.Fewha(geom, w, "f64")
+    res = _run_sequence(lib, o, f, s, 4, max_iter=60, aug=True, kcap=8, persistent=True, prec="f64",
+                        rtol=1e-2)
+    for ro, rg, ec, er, _, _ in res:
+        assert rg["iterations"] == ro["iterations"] < 60
+        assert rg["rel_res"] <= 1e-2 < ro["rel_res"] * 10
+        assert ec < 1e-9
+
+
+def test_edge_cases(lib):
+    geom, s, w, o = setup("micro")
+    f = lib.Fewha(geom, w, "f64")
+    # kcap = 1 and a single iteration
+    res = _run_sequence(lib, o, f, s, 3, max_iter=1, aug=True, kcap=1, persistent=True, prec="f64")
+    for ro, rg, ec, er, _, _ in res:
+        assert ec < 1e-10
+    # zero slopes: r0 = 0 -> no iteration, c unchanged
+    st = f.new_state(2)
+    c = torch.zeros(o.n, dtype=torch.float64, device="cuda")
+    rg = f.read_stats(f.solve(torch.zeros(o.n_slopes, dtype=torch.float64, device="cuda"), c, st, 5))
+    assert rg["status"] == 0 and rg["iterations"] == 0
+    assert float(c.abs().max()) == 0.0
+    # a tolerance that holds at the start: zero iterations, basis unchanged
+    rg = f.read_stats(f.solve(dev(s[0], torch.float64), c, st, 5, rtol=10.0))
+    assert rg["iterations"] == 0
+
+
+def test_invalid_arguments(lib):
+    geom, s, w, o = setup("micro")
+    f = lib.Fewha(geom, w, "f64")
+    st = f.new_state(2)
+    c = torch.zeros(o.n, dtype=torch.float64, device="cuda")
+    with pytest.raises(lib.FewhaError):
+        f.solve(dev(s[0], torch.float64), c, st, 0)
+    with pytest.raises(lib.FewhaError):
+        f.solve(dev(s[0], torch.float64), c, st, 10000)
