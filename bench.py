@@ -1,0 +1,385 @@
+#!/usr/bin/env python
+"""Benchmark of the augmented FEWHA time step on GB300.
+
+A step is one reconstructor time step (Algorithm 3: right-hand side, warm
+restart residual, augmented PCG to a fixed relative residual) on one frame of
+the ELT-size workload: 39 m pupil, 6 LGS at 90 km with 84x84 Shack-Hartmann
+sensors, 9 layers (5 x 128^2 + 4 x 64^2, n = 98304), Daubechies-3 with 5
+levels, recycled basis k = 8.  Inputs are a seeded frozen-flow slope sequence
+resident in HBM; L2 is flushed (256 MB written) before every timed frame.
+
+--impl reference runs the FP64 CPU oracle on the same workload (a bounded
+sample of frames per step) on the host cores.
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = json.load(open(os.path.join(ROOT, "BASELINE.json")))["metric"]
+UNIT = "frames/s"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=200)
+    p.add_argument("--warmup", type=int, default=10)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--config", default="elt")
+    p.add_argument("--precision", default="f32", choices=["f64", "f32", "bf16s"])
+    p.add_argument("--rtol", type=float, default=1e-2)
+    p.add_argument("--max-iter", type=int, default=200)
+    p.add_argument("--k", type=int, default=8)
+    p.add_argument("--snr", type=float, default=None)
+    p.add_argument("--plain", action="store_true", help="PCG instead of augmented PCG")
+    p.add_argument("--launch", default="persistent", choices=["persistent", "phases"])
+    p.add_argument("--no-flush", action="store_true")
+    p.add_argument("--no-compare", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--cpu-frames", type=int, default=3)
+    p.add_argument("--tile", type=int, default=0)
+    p.add_argument("--grid", type=int, default=0)
+    return p.parse_args()
+
+
+def workload_name(geom, args):
+    return ("%s: D=%.0f m, %d GS (%s), %dx%d SH, %d layers (%s), n=%d, Daubechies-%d, k=%d, "
+            "%s PCG to rel. residual %g, %s"
+            % (geom.name, geom.D, len(geom.gs), "LGS H=90 km" if geom.gs[0].H > 0 else "NGS",
+               geom.n_sub, geom.n_sub, len(geom.layers),
+               "+".join("%d^2" % l.n for l in geom.layers), geom.n_unknowns, geom.wavelet_N,
+               args.k, "plain" if args.plain else "augmented", args.rtol, args.precision))
+
+
+def source_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2011_06842_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx = max(mx, float(r[2]))
+                for nm, v in zip(names, r[5:9]):
+                    if v.strip() == "Active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d["hbm_gbs"], "measured"
+    return 6800.0, "fallback"
+
+
+def dist_setup(args):
+    import torch
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    return ws, rank, local
+
+
+def make_frames(geom, nframes, seed, device):
+    from synth import FrozenFlowSensors
+    sim = FrozenFlowSensors(geom, seed=seed, device=device)
+    s, w = sim.sequence(nframes, seed=seed + 1)
+    return s, w
+
+
+def time_solves(f, frames, dtype, args, nwarm, nsteps, aug, flush_buf, stats_buf, rtol):
+    """Per-frame CUDA-event timing; returns (times_ms, stats list)."""
+    import torch
+    n = f.n
+    c = torch.zeros(n, dtype=f.dtype, device="cuda")
+    st = f.new_state(args.k)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(nsteps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(nsteps)]
+    sl = frames.to(dtype)
+    for t in range(nwarm):
+        f.solve(sl[t], c, st, args.max_iter, rtol=rtol, augmented=aug,
+                persistent=args.launch == "persistent", stats=stats_buf[t % len(stats_buf)])
+    torch.cuda.synchronize()
+    for t in range(nsteps):
+        if flush_buf is not None:
+            flush_buf.zero_()
+        starts[t].record()
+        f.solve(sl[nwarm + t], c, st, args.max_iter, rtol=rtol, augmented=aug,
+                persistent=args.launch == "persistent", stats=stats_buf[t])
+        ends[t].record()
+    torch.cuda.synchronize()
+    times = [starts[t].elapsed_time(ends[t]) for t in range(nsteps)]
+    stats = [f.read_stats(stats_buf[t]) for t in range(nsteps)]
+    return times, stats
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    ws, rank, local = dist_setup(args)
+    from paper_2011_06842_gb300 import Fewha, build, workload
+    build.build()
+    from synth import configs
+    geom = configs.get(args.config)
+    if args.snr:
+        geom.snr = args.snr
+    geom.k_recycle = args.k
+    nframes = args.warmup + args.steps
+    frames, w = make_frames(geom, nframes, seed=100 + rank, device="cuda")
+    sdt = {"f64": torch.float64, "f32": torch.float32, "bf16s": torch.bfloat16}[args.precision]
+    f = Fewha(geom, w, args.precision, tile=args.tile, grid=args.grid)
+    flush = None if args.no_flush else torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    stats_buf = [f.new_stats() for _ in range(max(args.steps, args.warmup, 1))]
+    aug = not args.plain
+
+    # timed region: K frames, per-frame events; barrier + sync on both sides
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clk = Clocks(local) if rank == 0 else None
+    times, stats = time_solves(f, frames, sdt, args, args.warmup, args.steps, aug, flush, stats_buf,
+                               args.rtol)
+    clocks = clk.stop() if clk else None
+    total_ms = sum(times)
+    if ws > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+        torch.distributed.barrier()
+    bad = [s for s in stats if s["status"] != 0]
+    if bad:
+        raise RuntimeError("device-side error in a timed frame: %s" % bad[0])
+    iters = [s["iterations"] for s in stats]
+    relres = [s["rel_res"] for s in stats]
+    fps = ws * args.steps / (total_ms / 1e3)
+    us_frame = total_ms / args.steps * 1e3
+
+    # roofline of the dominant kernel (the persistent solver kernel; one launch per frame)
+    word = 8 if args.precision == "f64" else 4
+    mean_it = float(np.mean(iters))
+    algo_bytes = workload.solve_bytes(geom, mean_it, min(args.k, max(1, int(round(mean_it)))) if aug else 0,
+                                      word)
+    achieved = algo_bytes / (us_frame * 1e-6) / 1e9
+    peak, peak_kind = measured_peaks()
+    traffic = None
+    tp = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tp):
+        tj = json.load(open(tp))
+        key = "%s/%s/%s" % (args.config, args.precision, "aug" if aug else "plain")
+        if tj.get("source_hash") == source_hash() and key in tj.get("per_launch", {}):
+            traffic = tj["per_launch"][key]
+
+    out = {"metric": METRIC, "value": fps, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": us_frame / 1e3, "us_per_frame": us_frame,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": args.precision, "data": "synthetic: seeded von Karman frozen-flow screens "
+           "(r0=%.3f m, L0=%.0f m, wind 5-20 m/s) seen by SH sensors, SNR %g" % (geom.r0, geom.L0, geom.snr),
+           "config": {"workload": workload_name(geom, args), "n_unknowns": geom.n_unknowns,
+                      "n_slopes": geom.n_slopes, "rtol": args.rtol, "max_iter": args.max_iter,
+                      "k_recycle": args.k, "launch": args.launch, "frames": nframes,
+                      "l2": "flushed (256 MB written) before every timed frame" if flush is not None
+                      else "not flushed", "parallelism": "replicas" if ws > 1 else "single GPU"},
+           "iterations": {"mean": mean_it, "min": min(iters), "max": max(iters)},
+           "rel_res": {"mean": float(np.mean(relres)), "max": float(np.max(relres))},
+           "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                        "frac": achieved / peak, "traffic": traffic,
+                        "kernel": "k_solve_persistent" if args.launch == "persistent" else "all phases",
+                        "algorithmic_bytes_per_launch": algo_bytes, "peak_source": peak_kind},
+           "gpu_launches": args.steps * (1 if args.launch == "persistent" else 6 + 5 * args.max_iter)}
+    if clocks:
+        out["clocks"] = clocks
+
+    if rank == 0:
+        out["e2e"] = run_e2e(f, geom, frames, sdt, args, aug)
+        if not args.no_compare:
+            out["compare"] = run_compare(geom, w, frames, args, stats_buf, flush)
+        if not args.no_cpu and ws == 1:
+            out["cpu_baseline"] = run_cpu_baseline(geom, w, frames, iters, args, aug)
+    f.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return out if rank == 0 else None
+
+
+def run_e2e(f, geom, frames, sdt, args, aug):
+    """Same metric through the public API with host buffers: per frame the
+    slopes are copied from pinned host memory and the solution c is read back."""
+    import torch
+    K = args.steps
+    host = frames[args.warmup:args.warmup + K].to(sdt).cpu().pin_memory()
+    out_host = torch.empty((K, f.n), dtype=f.dtype).pin_memory()
+    dev_s = torch.empty(f.n_slopes, dtype=sdt, device="cuda")
+    c = torch.zeros(f.n, dtype=f.dtype, device="cuda")
+    st = f.new_state(args.k)
+    stats = f.new_stats()
+    for t in range(min(args.warmup, K)):
+        dev_s.copy_(host[t], non_blocking=True)
+        f.solve(dev_s, c, st, args.max_iter, rtol=args.rtol, augmented=aug,
+                persistent=args.launch == "persistent", stats=stats)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for t in range(K):
+        dev_s.copy_(host[t], non_blocking=True)
+        f.solve(dev_s, c, st, args.max_iter, rtol=args.rtol, augmented=aug,
+                persistent=args.launch == "persistent", stats=stats)
+        out_host[t].copy_(c, non_blocking=True)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    esz = torch.tensor([], dtype=sdt).element_size()
+    return {"value": K / (ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": f.n_slopes * esz,
+            "d2h_bytes_per_step": f.n * c.element_size(), "us_per_frame": ms / K * 1e3}
+
+
+def run_compare(geom, w, frames, args, stats_buf, flush):
+    """Plain PCG and the FP64 forms on the same frames and residual target."""
+    import numpy as np
+    import torch
+    from paper_2011_06842_gb300 import Fewha
+    K = min(args.steps, 60)
+    res = {}
+    for prec, aug in (("f32", False), ("f64", False), ("f64", True), ("f32", True)):
+        if prec == args.precision and aug == (not args.plain):
+            continue
+        f = Fewha(geom, w, prec, tile=args.tile, grid=args.grid)
+        sdt = torch.float64 if prec == "f64" else torch.float32
+        times, stats = time_solves(f, frames, sdt, args, args.warmup, K, aug, flush, stats_buf, args.rtol)
+        f.close()
+        it = [s["iterations"] for s in stats]
+        res["%s_%s" % ("aug" if aug else "plain", prec)] = {
+            "frames_per_s": K / (sum(times) / 1e3), "us_per_frame": sum(times) / K * 1e3,
+            "iterations_mean": float(np.mean(it)), "frames": K,
+            "status_ok": all(s["status"] == 0 for s in stats)}
+    return res
+
+
+def run_cpu_baseline(geom, w, frames, gpu_iters, args, aug):
+    """The FP64 oracle, single-threaded, on the first frames of the same sequence
+    with the same per-frame iteration counts as the GPU run."""
+    import numpy as np
+    from oracle import Oracle
+    nf = max(1, min(args.cpu_frames, args.steps))
+    s = frames[:args.warmup + nf].double().cpu().numpy()
+    o = Oracle(geom, w)
+    st = o.new_state(args.k)
+    for t in range(args.warmup):
+        o.solve(s[t], st, max_iter=args.max_iter, rtol=args.rtol, augmented=aug)
+    t0 = time.perf_counter()
+    for t in range(nf):
+        o.solve(s[args.warmup + t], st, max_iter=gpu_iters[t], rtol=0.0, augmented=aug)
+    dt = time.perf_counter() - t0
+    return {"value": nf / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d ELT frames after %d warm-up frames, FP64, same iteration counts as the GPU "
+                      "frames (%s)" % (nf, args.warmup, ",".join(str(i) for i in gpu_iters[:nf]))}
+
+
+def run_reference(args):
+    """Reference arm: the FP64 CPU oracle on the host cores (rank 0 only)."""
+    import numpy as np
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return None
+    from oracle import Oracle, build_oracle
+    from synth import FrozenFlowSensors, configs
+    build_oracle()
+    geom = configs.get(args.config)
+    if args.snr:
+        geom.snr = args.snr
+    sim = FrozenFlowSensors(geom, seed=100)
+    s, w = sim.sequence(args.warmup + args.steps, seed=101)
+    s = s.numpy()
+    o = Oracle(geom, w)
+    st = o.new_state(args.k)
+    aug = not args.plain
+    for t in range(args.warmup):
+        o.solve(s[t], st, max_iter=args.max_iter, rtol=args.rtol, augmented=aug)
+    t0 = time.perf_counter()
+    its = []
+    for t in range(args.steps):
+        r = o.solve(s[args.warmup + t], st, max_iter=args.max_iter, rtol=args.rtol, augmented=aug)
+        its.append(r["iterations"])
+    dt = time.perf_counter() - t0
+    v = args.steps / dt
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (same seeded frozen-flow workload)",
+            "config": {"workload": workload_name(geom, args) + " [FP64 CPU oracle]", "rtol": args.rtol},
+            "iterations": {"mean": float(np.mean(its))},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "%d full frames, one per step, single-threaded" % args.steps},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        out = run_reference(args)
+    else:
+        out = run_ours(args)
+    if out is not None:
+        print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

@@ -14,7 +14,10 @@
 //   wfs          per guide star and pupil tile: P_g (Sec. 2, P^NGS / P^LGS),
 //                Gamma (Sec. 2), C_eta^{-1}, Gamma^T, plus the data part of
 //                (p, Mp) as a sum of weighted squared slopes
-//   layer_adj    P_g^T (gather form) and W^{-T} per layer, fused with + alpha D p
+//   band_gather  P_g^T in gather form, per (layer, band of rows): the adjoint
+//                wavefronts are staged in shared memory and contracted
+//                separably (x then y), no atomics
+//   layer_fdwt   W^{-T} per layer, fused with + alpha D p
 //   axpy         c += alpha p, r -= alpha q and the inner products of
 //                Algorithm 1/2 (z = J^{-1} r is never stored)
 //   gram/init    projection of the warm start onto the recycled basis
@@ -71,6 +74,11 @@ struct Geo {
     const T *wmask;             // [G][ns*ns] weight on lit subapertures, 0 elsewhere
     const T *alpha_d;           // [n]
     const T *invJ;              // [n]
+    int lay_lg[FEWHA_MAX_LAYERS];  // log2(n_l)
+    int nbands;                 // P^T work items (layer, band of rows)
+    const int *band_layer, *band_row0, *band_rows;  // [nbands]
+    const int *band_ilo, *band_ihi;  // [G][nbands] pupil rows the band touches
+    int rows_chunk;             // pupil rows staged per pass of band_gather
 };
 
 enum Mode { kApply = 0, kRhs = 1, kSolve = 2 };
@@ -81,6 +89,7 @@ struct Args {
     // operator buffers
     S *nodal;        // [n]  W^{-1} p (layer nodal values)
     S *psi;          // [G][m*m] Gamma^T C Gamma P_g (...) per guide star
+    T *u;            // [n]  P^T psi (layer nodal adjoint)
     const T *x;      // apply: input
     T *y;            // apply / rhs: output
     const S *slopes; // rhs / solve: measured slopes
@@ -147,15 +156,35 @@ __device__ __forceinline__ double warp_sum(double v)
     return v;
 }
 
+// Per-thread / per-warp accumulation type: FP32 in the FP32 paths (FP64
+// arithmetic runs at 1/64 of the FP32 rate on this part), FP64 in the FP64
+// path.  Sums across warps and CTAs are always FP64.
+template <typename T>
+struct AccT {
+    typedef float type;
+};
+template <>
+struct AccT<double> {
+    typedef double type;
+};
+
+template <typename A>
+__device__ __forceinline__ A warp_sum_t(A v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
 // Block-wide sum of NV values per thread, written as partials of this CTA.
-template <int NV>
-__device__ void block_partials(double (&v)[NV], double *part, const int (&slot)[NV], double *sred)
+template <int NV, typename A>
+__device__ void block_partials(A (&v)[NV], double *part, const int (&slot)[NV], double *sred)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
     for (int i = 0; i < NV; i++) {
-        double s = warp_sum(v[i]);
-        if (lane == 0) sred[i * 32 + warp] = s;
+        A s = warp_sum_t(v[i]);
+        if (lane == 0) sred[i * 32 + warp] = (double)s;
     }
     __syncthreads();
     if (warp < NV) {
@@ -261,64 +290,56 @@ __device__ inline bool grid_sync(Record *rec, unsigned long long timeout_ns)
 // block synchronises and writes them back.
 // ---------------------------------------------------------------------------
 template <typename T, bool ROWS, bool SYNTH>
-__device__ void dwt_pass(T *buf, int pitch, int N, const Geo<T> &G)
+__device__ void dwt_pass(T *buf, int pitch, int lgN, const Geo<T> &G)
 {
-    const int half = N >> 1, total = N * half, L = G.n_taps;
+    const int N = 1 << lgN, half = N >> 1, total = N * half, Lh = G.n_taps >> 1;
+    const int lgh = lgN - 1;
+    const int stride = ROWS ? 1 : pitch;
     T o0[kPairs], o1[kPairs];
 #pragma unroll
     for (int t = 0; t < kPairs; t++) {
-        int idx = threadIdx.x + t * blockDim.x;
+        const int idx = threadIdx.x + t * blockDim.x;
         o0[t] = o1[t] = T(0);
         if (idx < total) {
-            int line, m;
-            if (ROWS) {
-                line = idx / half;
-                m = idx - line * half;
-            } else {
-                m = idx / N;
-                line = idx - m * N;
-            }
-            const int stride = ROWS ? 1 : pitch;
+            // ROWS: line = row, m along the row; COLS: line = column (consecutive
+            // threads take consecutive columns), m along the column
+            const int line = ROWS ? (idx >> lgh) : (idx & (N - 1));
+            const int m = ROWS ? (idx & (half - 1)) : (idx >> lgN);
             const T *base = ROWS ? buf + line * pitch : buf + line;
+            T x0 = 0, x1 = 0;
             if (SYNTH) {
-                T x0 = 0, x1 = 0;
-                for (int u = 0; u < (L >> 1); u++) {
-                    int k = (m - u) % half;
-                    if (k < 0) k += half;
-                    T a = base[k * stride], d = base[(half + k) * stride];
-                    x0 += G.h[2 * u] * a + G.g[2 * u] * d;
-                    x1 += G.h[2 * u + 1] * a + G.g[2 * u + 1] * d;
+#pragma unroll
+                for (int u = 0; u < kMaxT / 2; u++) {
+                    if (u < Lh) {
+                        const int k = (m - u) & (half - 1);
+                        const T a = base[k * stride], d = base[(half + k) * stride];
+                        x0 += G.h[2 * u] * a + G.g[2 * u] * d;
+                        x1 += G.h[2 * u + 1] * a + G.g[2 * u + 1] * d;
+                    }
                 }
-                o0[t] = x0;
-                o1[t] = x1;
             } else {
-                T a = 0, d = 0;
-                for (int u = 0; u < L; u++) {
-                    T v = base[((2 * m + u) % N) * stride];
-                    a += G.h[u] * v;
-                    d += G.g[u] * v;
+#pragma unroll
+                for (int u = 0; u < kMaxT; u++) {
+                    if (u < 2 * Lh) {
+                        const T v = base[((2 * m + u) & (N - 1)) * stride];
+                        x0 += G.h[u] * v;
+                        x1 += G.g[u] * v;
+                    }
                 }
-                o0[t] = a;
-                o1[t] = d;
             }
+            o0[t] = x0;
+            o1[t] = x1;
         }
     }
     __syncthreads();
 #pragma unroll
     for (int t = 0; t < kPairs; t++) {
-        int idx = threadIdx.x + t * blockDim.x;
+        const int idx = threadIdx.x + t * blockDim.x;
         if (idx < total) {
-            int line, m;
-            if (ROWS) {
-                line = idx / half;
-                m = idx - line * half;
-            } else {
-                m = idx / N;
-                line = idx - m * N;
-            }
-            const int stride = ROWS ? 1 : pitch;
+            const int line = ROWS ? (idx >> lgh) : (idx & (N - 1));
+            const int m = ROWS ? (idx & (half - 1)) : (idx >> lgN);
             T *base = ROWS ? buf + line * pitch : buf + line;
-            int p0 = SYNTH ? 2 * m : m, p1 = SYNTH ? 2 * m + 1 : half + m;
+            const int p0 = SYNTH ? 2 * m : m, p1 = SYNTH ? 2 * m + 1 : half + m;
             base[p0 * stride] = o0[t];
             base[p1 * stride] = o1[t];
         }
@@ -327,22 +348,20 @@ __device__ void dwt_pass(T *buf, int pitch, int N, const Geo<T> &G)
 }
 
 template <typename T>
-__device__ void idwt2(T *buf, int n, int J, const Geo<T> &G)
+__device__ void idwt2(T *buf, int lgn, int J, const Geo<T> &G)
 {
     for (int t = J - 1; t >= 0; t--) {
-        int N = n >> t;
-        dwt_pass<T, false, true>(buf, n, N, G);
-        dwt_pass<T, true, true>(buf, n, N, G);
+        dwt_pass<T, false, true>(buf, 1 << lgn, lgn - t, G);
+        dwt_pass<T, true, true>(buf, 1 << lgn, lgn - t, G);
     }
 }
 
 template <typename T>
-__device__ void fdwt2(T *buf, int n, int J, const Geo<T> &G)
+__device__ void fdwt2(T *buf, int lgn, int J, const Geo<T> &G)
 {
     for (int t = 0; t < J; t++) {
-        int N = n >> t;
-        dwt_pass<T, true, false>(buf, n, N, G);
-        dwt_pass<T, false, false>(buf, n, N, G);
+        dwt_pass<T, true, false>(buf, 1 << lgn, lgn - t, G);
+        dwt_pass<T, false, false>(buf, 1 << lgn, lgn - t, G);
     }
 }
 
@@ -360,7 +379,7 @@ __device__ void layer_idwt(const Args<T, S> &A, T *buf, Load load)
         const long off = G.lay_off[l];
         for (int e = threadIdx.x; e < nn; e += blockDim.x) buf[e] = load(off + e);
         __syncthreads();
-        idwt2<T>(buf, n, G.lay_J[l], G);
+        idwt2<T>(buf, G.lay_lg[l], G.lay_J[l], G);
         const T sc = G.inv_delta[l];
         for (int e = threadIdx.x; e < nn; e += blockDim.x) A.nodal[off + e] = Cv<S>::st(buf[e] * sc);
         __syncthreads();
@@ -376,15 +395,16 @@ __device__ void layer_idwt(const Args<T, S> &A, T *buf, Load load)
 //   both    : psi_g = Gamma^T (weighted slopes) on the tile's nodes.
 // ---------------------------------------------------------------------------
 template <typename T, typename S, bool RHS>
-__device__ double wfs_phase(const Args<T, S> &A, T *sm)
+__device__ typename AccT<T>::type wfs_phase(const Args<T, S> &A, T *sm)
 {
+    typedef typename AccT<T>::type Acc;
     const Geo<T> &G = A.geo;
     const int TS = G.tile, H = TS + 2, SB = TS + 1, m = G.m, ns = G.ns;
     const int per_g = G.tiles_x * G.tiles_x, total = G.G * per_g;
     T *phi = sm;                         // [L][H*H] per-layer contributions (OP)
     T *sx = sm + (size_t)G.L * H * H;    // [SB*SB]
     T *sy = sx + SB * SB;
-    double ws = 0.0;
+    Acc ws = 0;
     for (int w = blockIdx.x; w < total; w += gridDim.x) {
         const int g = w / per_g, tt = w - g * per_g;
         const int i0 = (tt / G.tiles_x) * TS, j0 = (tt % G.tiles_x) * TS;
@@ -396,8 +416,8 @@ __device__ double wfs_phase(const Args<T, S> &A, T *sm)
                 T v = 0;
                 if (i >= 0 && i < m && j >= 0 && j < m) {
                     const int bx = ((g * G.L + l) * 2 + 0) * m, by = ((g * G.L + l) * 2 + 1) * m;
-                    const int kx = G.fk[bx + j], ky = G.fk[by + i];
-                    const T wx = G.fw[bx + j], wy = G.fw[by + i];
+                    const int kx = __ldg(G.fk + bx + j), ky = __ldg(G.fk + by + i);
+                    const T wx = __ldg(G.fw + bx + j), wy = __ldg(G.fw + by + i);
                     const int n = G.lay_n[l];
                     const S *Lp = A.nodal + G.lay_off[l] + (long)ky * n + kx;
                     const T v00 = Cv<S>::ld(ldcg(Lp)), v01 = Cv<S>::ld(ldcg(Lp + 1));
@@ -420,7 +440,7 @@ __device__ double wfs_phase(const Args<T, S> &A, T *sm)
             const int i = i0 - 1 + a, j = j0 - 1 + b;
             T vx = 0, vy = 0;
             if (i >= 0 && i < ns && j >= 0 && j < ns) {
-                const T wgt = G.wmask[(size_t)g * ns * ns + i * ns + j];
+                const T wgt = __ldg(G.wmask + (size_t)g * ns * ns + i * ns + j);
                 if (RHS) {
                     const S *sg = A.slopes + (size_t)g * 2 * ns * ns;
                     vx = wgt * Cv<S>::ld(sg[i * ns + j]);
@@ -432,7 +452,7 @@ __device__ double wfs_phase(const Args<T, S> &A, T *sm)
                     const T gy = T(0.5) * ((p10 - p00) + (p11 - p01));
                     vx = wgt * gx;
                     vy = wgt * gy;
-                    if (a >= 1 && b >= 1) ws += (double)vx * (double)gx + (double)vy * (double)gy;
+                    if (a >= 1 && b >= 1) ws += (Acc)vx * (Acc)gx + (Acc)vy * (Acc)gy;
                 }
             }
             sx[e] = vx;
@@ -456,41 +476,79 @@ __device__ double wfs_phase(const Args<T, S> &A, T *sm)
 }
 
 // ---------------------------------------------------------------------------
-// Layer phase 2: u = P^T psi (gather over all guide stars), then
-// W u / delta_l; `store(e, value)` consumes each coefficient.
+// P^T phase: u = sum_g P_g^T psi_g, gather form, one work item per (layer l,
+// band of layer rows [a0, a0+BR)).  P_g restricted to layer l is separable,
+// Wy (x) Wx, so per guide star
+//     T[i][b] = sum_j Wx[j][b] psi_g[i][j]     (pupil rows i the band touches)
+//     u[a][b] += sum_i Wy[i][a] T[i][b]
+// with psi rows staged in shared memory in chunks of rows_chunk rows.
+// Thread (a - a0, b) owns output u[a][b]; no atomics, fixed summation order.
 // ---------------------------------------------------------------------------
-template <typename T, typename S, class Store>
-__device__ void layer_adj(const Args<T, S> &A, T *buf, Store store)
+template <typename T, typename S>
+__device__ void band_gather(const Args<T, S> &A, T *sm)
 {
     const Geo<T> &G = A.geo;
-    const int m = G.m;
+    const int m = G.m, RC = G.rows_chunk;
+    for (int w = blockIdx.x; w < G.nbands; w += gridDim.x) {
+        const int l = __ldg(G.band_layer + w), a0 = __ldg(G.band_row0 + w), BR = __ldg(G.band_rows + w);
+        const int n = G.lay_n[l], nout = BR * n;
+        T *ps = sm;               // [RC][m]   staged psi rows
+        T *Tb = sm + RC * m;      // [RC][n]   x-contracted rows
+        T acc = 0;
+        const int oa = threadIdx.x / n, ob = threadIdx.x - oa * n;  // owned output (a0 + oa, ob)
+        for (int g = 0; g < G.G; g++) {
+            const int bx = (g * G.L + l) * 2, by = bx + 1;
+            const int ilo = __ldg(G.band_ilo + g * G.nbands + w), ihi = __ldg(G.band_ihi + g * G.nbands + w);
+            const S *psg = A.psi + (size_t)g * m * m;
+            for (int c0 = ilo; c0 < ihi; c0 += RC) {
+                const int rows = min(RC, ihi - c0);
+                for (int e = threadIdx.x; e < rows * m; e += blockDim.x)
+                    ps[e] = Cv<S>::ld(ldcg(psg + (size_t)c0 * m + e));
+                __syncthreads();
+                for (int e = threadIdx.x; e < rows * n; e += blockDim.x) {
+                    const int i = e / n, b = e - i * n;
+                    const int jlo = __ldg(G.alo + bx * FEWHA_MAX_GRID + b);
+                    const int jhi = __ldg(G.ahi + bx * FEWHA_MAX_GRID + b);
+                    T v = 0;
+                    for (int j = jlo; j < jhi; j++) {
+                        const T w0 = __ldg(G.fw + bx * m + j);
+                        const T wx = (__ldg(G.fk + bx * m + j) == b) ? T(1) - w0 : w0;
+                        v += wx * ps[i * m + j];
+                    }
+                    Tb[e] = v;
+                }
+                __syncthreads();
+                if (oa < BR) {
+                    const int a = a0 + oa;
+                    const int rlo = max(__ldg(G.alo + by * FEWHA_MAX_GRID + a), c0);
+                    const int rhi = min(__ldg(G.ahi + by * FEWHA_MAX_GRID + a), c0 + rows);
+                    for (int i = rlo; i < rhi; i++) {
+                        const T w0 = __ldg(G.fw + by * m + i);
+                        const T wy = (__ldg(G.fk + by * m + i) == a) ? T(1) - w0 : w0;
+                        acc += wy * Tb[(i - c0) * n + ob];
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        if (oa < BR && threadIdx.x < nout) A.u[G.lay_off[l] + (long)(a0 + oa) * n + ob] = acc;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Layer phase 2: W u / delta_l per layer; `store(e, value)` consumes each
+// coefficient (u was written by band_gather in another CTA: L2 loads).
+// ---------------------------------------------------------------------------
+template <typename T, typename S, class Store>
+__device__ void layer_fdwt(const Args<T, S> &A, T *buf, Store store)
+{
+    const Geo<T> &G = A.geo;
     for (int l = blockIdx.x; l < G.L; l += gridDim.x) {
         const int n = G.lay_n[l], nn = n * n;
         const long off = G.lay_off[l];
-        for (int e = threadIdx.x; e < nn; e += blockDim.x) {
-            const int a = e / n, b = e - a * n;
-            T acc = 0;
-            for (int g = 0; g < G.G; g++) {
-                const int bx = (g * G.L + l) * 2, by = bx + 1;
-                const int jlo = G.alo[bx * FEWHA_MAX_GRID + b], jhi = G.ahi[bx * FEWHA_MAX_GRID + b];
-                const int ilo = G.alo[by * FEWHA_MAX_GRID + a], ihi = G.ahi[by * FEWHA_MAX_GRID + a];
-                const S *ps = A.psi + (size_t)g * m * m;
-                for (int i = ilo; i < ihi; i++) {
-                    const T wy0 = G.fw[by * m + i];
-                    const T wy = (G.fk[by * m + i] == a) ? T(1) - wy0 : wy0;
-                    T rowacc = 0;
-                    for (int j = jlo; j < jhi; j++) {
-                        const T wx0 = G.fw[bx * m + j];
-                        const T wx = (G.fk[bx * m + j] == b) ? T(1) - wx0 : wx0;
-                        rowacc += wx * Cv<S>::ld(ldcg(ps + i * m + j));
-                    }
-                    acc += wy * rowacc;
-                }
-            }
-            buf[e] = acc;
-        }
+        for (int e = threadIdx.x; e < nn; e += blockDim.x) buf[e] = ldcg(A.u + off + e);
         __syncthreads();
-        fdwt2<T>(buf, n, G.lay_J[l], G);
+        fdwt2<T>(buf, G.lay_lg[l], G.lay_J[l], G);
         const T sc = G.inv_delta[l];
         for (int e = threadIdx.x; e < nn; e += blockDim.x) store(off + e, buf[e] * sc);
         __syncthreads();

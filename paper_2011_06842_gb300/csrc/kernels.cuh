@@ -35,17 +35,24 @@ template <typename T, typename S, bool RHS>
 __global__ void __launch_bounds__(kThreads, 1) k_wfs(Args<T, S> A)
 {
     __shared__ double sred[8 * 32];
-    if (ldcgi(&A.rec->done) || ldcgi(&A.rec->status)) return;
-    double acc[1] = {wfs_phase<T, S, RHS>(A, dyn_smem<T>())};
+    typename AccT<T>::type acc[1] = {wfs_phase<T, S, RHS>(A, dyn_smem<T>())};
     const int slots[1] = {kSlotB};
     block_partials<1>(acc, A.part, slots, sred);
 }
 
-// y = W^{-T} P^T psi + alpha D x  (APPLY) or y = W^{-T} P^T psi (RHS)
-template <typename T, typename S, bool RHS>
-__global__ void __launch_bounds__(kThreads, 1) k_adj(Args<T, S> A)
+// u = P^T psi
+template <typename T, typename S>
+__global__ void __launch_bounds__(kThreads, 1) k_gather(Args<T, S> A)
 {
-    layer_adj<T, S>(A, dyn_smem<T>(), [&](long e, T v) {
+    if (ldcgi(&A.rec->done) || ldcgi(&A.rec->status)) return;
+    band_gather<T, S>(A, dyn_smem<T>());
+}
+
+// y = W^{-T} u + alpha D x  (APPLY) or y = W^{-T} u (RHS)
+template <typename T, typename S, bool RHS>
+__global__ void __launch_bounds__(kThreads, 1) k_fdwt(Args<T, S> A)
+{
+    layer_fdwt<T, S>(A, dyn_smem<T>(), [&](long e, T v) {
         A.y[e] = RHS ? v : v + A.geo.alpha_d[e] * A.x[e];
     });
 }
@@ -66,11 +73,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_rhs_wfs(Args<T, S> A)
 }
 
 template <typename T, typename S>
-__global__ void __launch_bounds__(kThreads, 1) k_rhs_adj(Args<T, S> A)
+__global__ void __launch_bounds__(kThreads, 1) k_rhs_fdwt(Args<T, S> A)
 {
     FEWHA_PHASE_GUARD
     (void)sc;
-    phase_rhs_adj<T, S>(A, dyn_smem<T>(), sred);
+    phase_rhs_fdwt<T, S>(A, dyn_smem<T>(), sred);
 }
 
 template <typename T, typename S>
@@ -100,16 +107,24 @@ __global__ void __launch_bounds__(kThreads, 1) k_B(Args<T, S> A, int k)
 {
     FEWHA_PHASE_GUARD
     (void)sc;
-    double acc[1] = {wfs_phase<T, S, false>(A, dyn_smem<T>())};
+    typename AccT<T>::type acc[1] = {wfs_phase<T, S, false>(A, dyn_smem<T>())};
     const int slots[1] = {kSlotB + (k & 1)};
     block_partials<1>(acc, A.part, slots, sred);
 }
 
 template <typename T, typename S>
-__global__ void __launch_bounds__(kThreads, 1) k_CD(Args<T, S> A, int k)
+__global__ void __launch_bounds__(kThreads, 1) k_C(Args<T, S> A, int k)
 {
     FEWHA_PHASE_GUARD
-    phase_CD<T, S>(A, b, k, dyn_smem<T>(), sc);
+    phase_C<T, S>(A, b, k, dyn_smem<T>(), sc);
+}
+
+template <typename T, typename S>
+__global__ void __launch_bounds__(kThreads, 1) k_D(Args<T, S> A, int k)
+{
+    FEWHA_PHASE_GUARD
+    (void)sc;
+    phase_D<T, S>(A, b, k, dyn_smem<T>());
 }
 
 template <typename T, typename S>
@@ -143,7 +158,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_solve_persistent(Args<T, S> A)
     do {
         wfs_phase<T, S, true>(A, sm);
         if (!grid_sync(A.rec, to)) break;
-        phase_rhs_adj<T, S>(A, sm, sred);
+        band_gather<T, S>(A, sm);
+        if (!grid_sync(A.rec, to)) break;
+        phase_rhs_fdwt<T, S>(A, sm, sred);
         if (!grid_sync(A.rec, to)) break;
         if (b.kv > 0) {
             phase_gram<T, S>(A, b);
@@ -158,15 +175,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_solve_persistent(Args<T, S> A)
             }
             if (!grid_sync(A.rec, to)) break;
             {
-                double acc[1] = {wfs_phase<T, S, false>(A, sm)};
+                typename AccT<T>::type acc[1] = {wfs_phase<T, S, false>(A, sm)};
                 const int slots[1] = {kSlotB + (k & 1)};
                 block_partials<1>(acc, A.part, slots, sred);
             }
             if (!grid_sync(A.rec, to)) break;
-            if (!phase_CD<T, S>(A, b, k, sm, sc)) {
+            if (!phase_C<T, S>(A, b, k, sm, sc)) {
                 K = k;
                 break;
             }
+            if (!grid_sync(A.rec, to)) break;
+            phase_D<T, S>(A, b, k, sm);
             if (!grid_sync(A.rec, to)) break;
             phase_E<T, S>(A, b, k, sred);
             if (!grid_sync(A.rec, to)) break;
@@ -274,7 +293,43 @@ struct Impl : ImplBase {
         if ((st = up(fw, &G.fw)) || (st = up(wm, &G.wmask)) || (st = up(ad, &G.alpha_d)) ||
             (st = up(one, &G.invJ)))
             return st;
-        if ((st = alloc((size_t)P.n, &base.nodal)) || (st = alloc((size_t)P.G * P.m * P.m, &base.psi)) ||
+        // P^T work items: bands of rows with band_rows * n_l <= kThreads outputs
+        std::vector<int> bl, br0, brs;
+        for (int l = 0; l < P.L; l++) {
+            int n = P.geom.layers[l].n, lg = 0;
+            while ((1 << lg) < n) lg++;
+            G.lay_lg[l] = lg;
+            int BR = std::max(1, std::min(n, kThreads / n));
+            for (int a0 = 0; a0 < n; a0 += BR) {
+                bl.push_back(l);
+                br0.push_back(a0);
+                brs.push_back(std::min(BR, n - a0));
+            }
+        }
+        G.nbands = (int)bl.size();
+        std::vector<int> bilo((size_t)P.G * G.nbands), bihi((size_t)P.G * G.nbands);
+        int max_rows = 1;
+        for (int g = 0; g < P.G; g++)
+            for (int w = 0; w < G.nbands; w++) {
+                int lo = P.m, hi = 0;
+                size_t by = ((size_t)g * P.L + bl[w]) * 2 + 1;
+                for (int a = br0[w]; a < br0[w] + brs[w]; a++) {
+                    int alo = P.alo[by * FEWHA_MAX_GRID + a], ahi = P.ahi[by * FEWHA_MAX_GRID + a];
+                    if (alo < ahi) {
+                        lo = std::min(lo, alo);
+                        hi = std::max(hi, ahi);
+                    }
+                }
+                if (lo >= hi) lo = hi = 0;
+                bilo[(size_t)g * G.nbands + w] = lo;
+                bihi[(size_t)g * G.nbands + w] = hi;
+                max_rows = std::max(max_rows, hi - lo);
+            }
+        if ((st = up(bl, &G.band_layer)) || (st = up(br0, &G.band_row0)) || (st = up(brs, &G.band_rows)) ||
+            (st = up(bilo, &G.band_ilo)) || (st = up(bihi, &G.band_ihi)))
+            return st;
+        if ((st = alloc((size_t)P.n, &base.nodal)) || (st = alloc((size_t)P.n, &base.u)) ||
+            (st = alloc((size_t)P.G * P.m * P.m, &base.psi)) ||
             (st = alloc((size_t)kSlots * kMaxCtas, &base.part)) || (st = alloc((size_t)1, &base.rec)))
             return st;
         // launch geometry: dynamic shared memory = max over phases
@@ -284,6 +339,13 @@ struct Impl : ImplBase {
         int H = tile + 2, SB = tile + 1;
         size_t sm_wfs = ((size_t)P.L * H * H + 2 * SB * SB) * sizeof(T);
         smem = std::max(sm_layer, sm_wfs);
+        // band_gather stages rows_chunk psi rows and their x-contraction
+        const size_t row_bytes = (size_t)(P.m + nmax) * sizeof(T);
+        const size_t smem_cap = 227 * 1024;
+        size_t want = (size_t)max_rows * row_bytes;
+        if (want > smem) smem = std::min(want, smem_cap);
+        G.rows_chunk = (int)std::max<size_t>(1, std::min<size_t>(max_rows, smem / row_bytes));
+        if (smem > smem_cap) return FEWHA_ERR_GEOMETRY;
         int dev, nsm;
         CK(cudaGetDevice(&dev));
         CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
@@ -293,15 +355,17 @@ struct Impl : ImplBase {
         CK(setattr((const void *)k_apply_idwt<T, S>));
         CK(setattr((const void *)k_wfs<T, S, false>));
         CK(setattr((const void *)k_wfs<T, S, true>));
-        CK(setattr((const void *)k_adj<T, S, false>));
-        CK(setattr((const void *)k_adj<T, S, true>));
+        CK(setattr((const void *)k_gather<T, S>));
+        CK(setattr((const void *)k_fdwt<T, S, false>));
+        CK(setattr((const void *)k_fdwt<T, S, true>));
         CK(setattr((const void *)k_rhs_wfs<T, S>));
-        CK(setattr((const void *)k_rhs_adj<T, S>));
+        CK(setattr((const void *)k_rhs_fdwt<T, S>));
         CK(setattr((const void *)k_gram<T, S>));
         CK(setattr((const void *)k_init<T, S>));
         CK(setattr((const void *)k_A<T, S>));
         CK(setattr((const void *)k_B<T, S>));
-        CK(setattr((const void *)k_CD<T, S>));
+        CK(setattr((const void *)k_C<T, S>));
+        CK(setattr((const void *)k_D<T, S>));
         CK(setattr((const void *)k_E<T, S>));
         CK(setattr((const void *)k_finish<T, S>));
         CK(setattr((const void *)k_solve_persistent<T, S>));
@@ -341,7 +405,8 @@ struct Impl : ImplBase {
         CK(cudaMemsetAsync(A.rec, 0, offsetof(Record, rz), s));
         k_apply_idwt<T, S><<<ncta, kThreads, smem, s>>>(A);
         k_wfs<T, S, false><<<ncta, kThreads, smem, s>>>(A);
-        k_adj<T, S, false><<<ncta, kThreads, smem, s>>>(A);
+        k_gather<T, S><<<ncta, kThreads, smem, s>>>(A);
+        k_fdwt<T, S, false><<<ncta, kThreads, smem, s>>>(A);
         return launch_check();
     }
 
@@ -352,7 +417,8 @@ struct Impl : ImplBase {
         A.y = static_cast<T *>(b);
         CK(cudaMemsetAsync(A.rec, 0, offsetof(Record, rz), s));
         k_wfs<T, S, true><<<ncta, kThreads, smem, s>>>(A);
-        k_adj<T, S, true><<<ncta, kThreads, smem, s>>>(A);
+        k_gather<T, S><<<ncta, kThreads, smem, s>>>(A);
+        k_fdwt<T, S, true><<<ncta, kThreads, smem, s>>>(A);
         return launch_check();
     }
 
@@ -391,13 +457,15 @@ struct Impl : ImplBase {
             return launch_check();
         }
         k_rhs_wfs<T, S><<<ncta, kThreads, smem, s>>>(A);
-        k_rhs_adj<T, S><<<ncta, kThreads, smem, s>>>(A);
+        k_gather<T, S><<<ncta, kThreads, smem, s>>>(A);
+        k_rhs_fdwt<T, S><<<ncta, kThreads, smem, s>>>(A);
         k_gram<T, S><<<ncta, kThreads, smem, s>>>(A);
         k_init<T, S><<<ncta, kThreads, smem, s>>>(A);
         for (int k = 0; k < A.max_iter; k++) {
             k_A<T, S><<<ncta, kThreads, smem, s>>>(A, k);
             k_B<T, S><<<ncta, kThreads, smem, s>>>(A, k);
-            k_CD<T, S><<<ncta, kThreads, smem, s>>>(A, k);
+            k_C<T, S><<<ncta, kThreads, smem, s>>>(A, k);
+            k_D<T, S><<<ncta, kThreads, smem, s>>>(A, k);
             k_E<T, S><<<ncta, kThreads, smem, s>>>(A, k);
         }
         k_finish<T, S><<<1, kThreads, smem, s>>>(A);

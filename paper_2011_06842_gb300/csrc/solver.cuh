@@ -107,18 +107,21 @@ __device__ bool iter_scalars(const Args<T, S> &A, const Basis &b, int k, Scal &s
 }
 
 // ---------------------------------------------------------------------------
-// R1/R2: right-hand side b = W^{-T} A^T C s, r0 = (b - b_prev) + r_prev
+// R3: right-hand side b = W^{-T} u / delta (u = P^T Gamma^T C s from the
+// preceding phases) and the warm-restart residual of Algorithm 3,
+// r0 = (b - b_prev) + r_prev;  b_prev <- b.
 // ---------------------------------------------------------------------------
 template <typename T, typename S>
-__device__ void phase_rhs_adj(const Args<T, S> &A, T *sm, double *sred)
+__device__ void phase_rhs_fdwt(const Args<T, S> &A, T *sm, double *sred)
 {
-    double acc[2] = {0.0, 0.0};
-    layer_adj<T, S>(A, sm, [&](long e, T b) {
+    typedef typename AccT<T>::type Acc;
+    Acc acc[2] = {0, 0};
+    layer_fdwt<T, S>(A, sm, [&](long e, T b) {
         T r0 = (b - A.b_prev[e]) + ldcg(A.r + e);
         A.b_prev[e] = b;
         A.r[e] = r0;
-        acc[0] += (double)b * (double)b;
-        acc[1] += (double)r0 * (double)r0;
+        acc[0] += (Acc)b * (Acc)b;
+        acc[1] += (Acc)r0 * (Acc)r0;
     });
     const int slots[2] = {kSlotR2, kSlotR2 + 1};
     block_partials<2>(acc, A.part, slots, sred);
@@ -136,18 +139,18 @@ __device__ void phase_gram(const Args<T, S> &A, const Basis &b)
         const T *X, *Y;
         int slot;
         if (s < kv * kv) {
-            X = oldP(A, b, s / kv);
-            Y = oldQ(A, b, s % kv);
+            X = oldQ(A, b, s % kv);
+            Y = oldP(A, b, s / kv);
             slot = kSlotGram + (s / kv) * kK + (s % kv);
         } else {
             X = oldP(A, b, s - kv * kv);
-            Y = A.r;
+            Y = A.r;  // written by another CTA in R3
             slot = kSlotGram + kK * kK + (s - kv * kv);
         }
-        double acc = 0.0;
-        for (long e = lo + lane; e < hi; e += 32) acc += (double)ldcg(X + e) * (double)ldcg(Y + e);
-        acc = warp_sum(acc);
-        if (lane == 0) A.part[(size_t)slot * kMaxCtas + blockIdx.x] = acc;
+        typename AccT<T>::type acc = 0;
+        for (long e = lo + lane; e < hi; e += 32) acc += __ldg(X + e) * ldcg(Y + e);
+        acc = warp_sum_t(acc);
+        if (lane == 0) A.part[(size_t)slot * kMaxCtas + blockIdx.x] = (double)acc;
     }
 }
 
@@ -170,8 +173,8 @@ __device__ bool phase_init(const Args<T, S> &A, const Basis &b, Scal &sc)
         T cv = A.c[e], rv = ldcg(A.r + e);
         for (int j = 0; j < kv; j++) {
             const T sj = (T)sc.tau[j];
-            cv += sj * ldcg(oldP(A, b, j) + e);
-            rv -= sj * ldcg(oldQ(A, b, j) + e);
+            cv += sj * __ldg(oldP(A, b, j) + e);
+            rv -= sj * __ldg(oldQ(A, b, j) + e);
         }
         A.c[e] = cv;
         A.r[e] = rv;
@@ -179,19 +182,19 @@ __device__ bool phase_init(const Args<T, S> &A, const Basis &b, Scal &sc)
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int s = warp; s < kv + 2; s += nw) {
-        double acc = 0.0;
+        typename AccT<T>::type acc = 0;
         for (long e = lo + lane; e < hi; e += 32) {
-            const T rv = ldcg(A.r + e), z = A.geo.invJ[e] * rv;
+            const T rv = ldcg(A.r + e), z = __ldg(A.geo.invJ + e) * rv;
             if (s < kv)
-                acc += (double)ldcg(oldQ(A, b, s) + e) * (double)z;
+                acc += __ldg(oldQ(A, b, s) + e) * z;
             else if (s == kv)
-                acc += (double)rv * (double)z;
+                acc += rv * z;
             else
-                acc += (double)rv * (double)rv;
+                acc += rv * rv;
         }
-        acc = warp_sum(acc);
+        acc = warp_sum_t(acc);
         int slot = s < kv ? kSlotInit + s : (s == kv ? kSlotInit + kK : kSlotInit + kK + 1);
-        if (lane == 0) A.part[(size_t)slot * kMaxCtas + blockIdx.x] = acc;
+        if (lane == 0) A.part[(size_t)slot * kMaxCtas + blockIdx.x] = (double)acc;
     }
     return true;
 }
@@ -256,21 +259,22 @@ __device__ bool phase_A(const Args<T, S> &A, const Basis &b, int k, T *sm, Scal 
     T tau[kK];
     for (int j = 0; j < kK; j++) tau[j] = j < kv ? (T)sc.tau[j] : T(0);
     const bool proj_all = (k == 0) || A.recycle_all;
-    double acc[2] = {0.0, 0.0};
+    typedef typename AccT<T>::type Acc;
+    Acc acc[2] = {0, 0};
     layer_idwt<T, S>(A, sm, [&](long e) -> T {
         const T rv = ldcg(A.r + e);
-        T z = A.geo.invJ[e] * rv;
+        T z = __ldg(A.geo.invJ + e) * rv;
         if (kv > 0) {
             if (proj_all) {
-                for (int j = 0; j < kv; j++) z -= tau[j] * oldP(A, b, j)[e];
+                for (int j = 0; j < kv; j++) z -= tau[j] * __ldg(oldP(A, b, j) + e);
             } else {
-                z -= mu * pm[e];
+                z -= mu * __ldg(pm + e);
             }
         }
         const T p = k > 0 ? z + beta * pprev[e] : z;
         pk[e] = p;
-        acc[0] += (double)A.geo.alpha_d[e] * (double)p * (double)p;
-        acc[1] += (double)rv * (double)p;
+        acc[0] += (Acc)__ldg(A.geo.alpha_d + e) * (Acc)p * (Acc)p;
+        acc[1] += (Acc)rv * (Acc)p;
         return p;
     });
     const int slots[2] = {kSlotA + (k & 1) * 2, kSlotA + (k & 1) * 2 + 1};
@@ -292,12 +296,13 @@ __device__ bool rz_of_iter(const Args<T, S> &A, const Basis &b, int k, Scal &sc)
 }
 
 // ---------------------------------------------------------------------------
-// CD_k: q_k = M p_k = W^{-T} P^T psi / delta + alpha D p_k, with
-// (p_k, q_k) = sum w s^2 + sum alpha d p^2 from the forward pass.
-// Returns false (uniformly) on rz == 0 (converged) or breakdown.
+// C_k: scalars of iteration k and u = P^T psi.  (p_k, q_k) comes from the
+// forward pass: sum w s^2 (WFS phase) + sum alpha d p^2 (A phase), equal to
+// (p_k, M p_k) by Eq. M.  Returns false (uniformly) on rz == 0 (converged)
+// or breakdown; CTA 0 records rz_k, alpha_k and (p_k, q_k).
 // ---------------------------------------------------------------------------
 template <typename T, typename S>
-__device__ bool phase_CD(const Args<T, S> &A, const Basis &b, int k, T *sm, Scal &sc)
+__device__ bool phase_C(const Args<T, S> &A, const Basis &b, int k, T *sm, Scal &sc)
 {
     if (!rz_of_iter(A, b, k, sc)) return false;
     reduce_slots(A.part, A.ncta, kSlotB + (k & 1), 1, sc.red + 1);
@@ -325,10 +330,17 @@ __device__ bool phase_CD(const Args<T, S> &A, const Basis &b, int k, T *sm, Scal
     }
     __syncthreads();
     if (sc.stop) return false;
+    band_gather<T, S>(A, sm);
+    return true;
+}
+
+// D_k: q_k = W^{-T} u / delta + alpha D p_k, stored in the basis slot.
+template <typename T, typename S>
+__device__ void phase_D(const Args<T, S> &A, const Basis &b, int k, T *sm)
+{
     const T *pk = newP(A, b, k);
     T *qk = newQ(A, b, k);
-    layer_adj<T, S>(A, sm, [&](long e, T v) { qk[e] = v + A.geo.alpha_d[e] * pk[e]; });
-    return true;
+    layer_fdwt<T, S>(A, sm, [&](long e, T v) { qk[e] = v + __ldg(A.geo.alpha_d + e) * pk[e]; });
 }
 
 // E_k: c += alpha p, r -= alpha q, and the inner products of the next step.
@@ -342,20 +354,21 @@ __device__ void phase_E(const Args<T, S> &A, const Basis &b, int k, double *sred
     const T *qm = kv > 0 ? oldQ(A, b, kv - 1) : nullptr;
     long lo, hi;
     cta_range(A.geo.n, lo, hi);
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    typedef typename AccT<T>::type Acc;
+    Acc acc[4] = {0, 0, 0, 0};
     for (long e = lo + threadIdx.x; e < hi; e += blockDim.x) {
         const T p = ldcg(pk + e), q = ldcg(qk + e);
         const T cv = A.c[e] + alpha * p;
         const T rv = ldcg(A.r + e) - alpha * q;
         A.c[e] = cv;
         A.r[e] = rv;
-        const T z = A.geo.invJ[e] * rv;
-        acc[0] += (double)rv * (double)z;
+        const T z = __ldg(A.geo.invJ + e) * rv;
+        acc[0] += (Acc)rv * (Acc)z;
         if (kv > 0 && !A.recycle_all) {
-            acc[1] += (double)z * (double)qm[e];
-            acc[2] += (double)rv * (double)pm[e];
+            acc[1] += (Acc)z * (Acc)__ldg(qm + e);
+            acc[2] += (Acc)rv * (Acc)__ldg(pm + e);
         }
-        acc[3] += (double)rv * (double)rv;
+        acc[3] += (Acc)rv * (Acc)rv;
     }
     const int e0 = kSlotE + (k & 1) * kSlotEStride;
     const int slots[4] = {e0, e0 + 1, e0 + 2, e0 + 3};
@@ -364,17 +377,17 @@ __device__ void phase_E(const Args<T, S> &A, const Basis &b, int k, double *sred
         __syncthreads();
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
         for (int s = warp; s < 2 * kv; s += nw) {
-            double a = 0.0;
+            Acc a = 0;
             for (long e = lo + lane; e < hi; e += 32) {
                 const T rv = ldcg(A.r + e);
                 if (s < kv)
-                    a += (double)(A.geo.invJ[e] * rv) * (double)oldQ(A, b, s)[e];
+                    a += (Acc)(__ldg(A.geo.invJ + e) * rv) * (Acc)__ldg(oldQ(A, b, s) + e);
                 else
-                    a += (double)rv * (double)oldP(A, b, s - kv)[e];
+                    a += (Acc)rv * (Acc)__ldg(oldP(A, b, s - kv) + e);
             }
-            a = warp_sum(a);
+            a = warp_sum_t(a);
             int slot = s < kv ? e0 + 4 + s : e0 + 4 + kK + (s - kv);
-            if (lane == 0) A.part[(size_t)slot * kMaxCtas + blockIdx.x] = a;
+            if (lane == 0) A.part[(size_t)slot * kMaxCtas + blockIdx.x] = (double)a;
         }
     }
 }

@@ -56,3 +56,20 @@ def bytes_per_iter(geom, word=4, augmented=True):
     vec_reads = 6 + (2 if augmented else 0)
     vec_writes = 4
     return word * (op + (vec_reads + vec_writes) * n)
+
+
+def solve_bytes(geom, iters, kv, word=4):
+    """Algorithmic bytes of one time step of the solver: right-hand side and
+    warm restart, projection onto kv recycled directions, and iters iterations.
+
+    RHS: slopes read, adjoint wavefronts written and read, b_prev read and
+    written, r read and written.  Projection: the Gram matrix and P^T r read
+    2 kv + 1 vectors; the update reads c, r, kv p and kv q and writes c, r;
+    the dots after it read r and kv q.
+    """
+    n = sum(l.n * l.n for l in geom.layers)
+    G = len(geom.gs)
+    m2 = (geom.n_sub + 1) ** 2
+    rhs = 2 * geom.n_sub ** 2 * G + 2 * G * m2 + 4 * n
+    init = (5 * kv + 6) * n if kv > 0 else 0
+    return word * (rhs + init) + iters * bytes_per_iter(geom, word, augmented=kv > 0)
