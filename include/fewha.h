@@ -15,7 +15,9 @@
  *    (barrier timeout, CG breakdown) are reported in fewha_stats.status,
  *    valid after the stream has been synchronised.
  *  - Memory: all vectors passed to the compute calls are DEVICE pointers owned
- *    by the caller, allocated on the device the handle was created on.  The
+ *    by the caller, allocated on the device the handle was created on.
+ *    Coefficient vectors (x, y, b, c and the state vectors) must be 16-byte
+ *    aligned (FEWHA_ERR_ARG otherwise); slopes need only element alignment.  The
  *    handle owns its constant tables and its scratch memory.  Nothing is
  *    retained after a call returns except the handle's own state.
  *  - Element type of the vectors: double for FEWHA_F64 handles, float for
@@ -161,6 +163,16 @@ int fewha_rhs(void *handle, const void *s, void *b, cudaStream_t stream);
  * stats_dev: device pointer to a fewha_stats, written at the end. */
 int fewha_solve(void *handle, const void *s, void *c, const fewha_state *state,
                 const fewha_solve_opts *opts, fewha_stats *stats_dev, cudaStream_t stream);
+
+/* Phase trace of the persistent solver (profiling aid).  trace_dev: device
+ * buffer of capacity x 4 unsigned 64-bit words, owned by the caller, or NULL
+ * to switch tracing off.  Each following fewha_solve (persistent launch)
+ * zeroes it and records, per grid barrier i: [4i] the longest time one CTA
+ * spent in the phase before it [ns] (from its previous barrier), [4i+1] the
+ * %globaltimer when the last CTA finished that phase, [4i+2] when CTA 0
+ * passed the barrier, [4i+3] the phase tag.  Barriers
+ * beyond the capacity are not recorded.  The paper has no counterpart. */
+int fewha_set_trace(void *handle, unsigned long long *trace_dev, int capacity);
 
 /* Text of a status code. */
 const char *fewha_strerror(int status);

@@ -143,15 +143,18 @@ int fewha_get_precond(const void *handle, double *out)
     return h->work ? h->work->get_invJ(out) : h->f64->get_invJ(out);
 }
 
+// Vectors are accessed with 16-byte loads and stores.
+static bool aligned16(const void *p) { return ((size_t)p & 15) == 0; }
+
 int fewha_apply_op(void *handle, const void *x, void *y, cudaStream_t stream)
 {
-    if (!handle || !x || !y || x == y) return FEWHA_ERR_ARG;
+    if (!handle || !x || !y || x == y || !aligned16(x) || !aligned16(y)) return FEWHA_ERR_ARG;
     return static_cast<Handle *>(handle)->w()->apply(x, y, stream);
 }
 
 int fewha_rhs(void *handle, const void *s, void *b, cudaStream_t stream)
 {
-    if (!handle || !s || !b) return FEWHA_ERR_ARG;
+    if (!handle || !s || !b || !aligned16(b)) return FEWHA_ERR_ARG;
     return static_cast<Handle *>(handle)->w()->rhs(s, b, stream);
 }
 
@@ -161,11 +164,21 @@ int fewha_solve(void *handle, const void *s, void *c, const fewha_state *st, con
     if (!handle || !s || !c || !st || !o) return FEWHA_ERR_ARG;
     if (!st->b_prev || !st->r_prev || !st->basis_P || !st->basis_Q || !st->basis_pq || !st->meta)
         return FEWHA_ERR_ARG;
+    if (!aligned16(c) || !aligned16(st->b_prev) || !aligned16(st->r_prev) || !aligned16(st->basis_P) ||
+        !aligned16(st->basis_Q))
+        return FEWHA_ERR_ARG;
     if (st->k_cap < 1 || st->k_cap > FEWHA_MAX_K) return FEWHA_ERR_ARG;
     if (o->max_iter < 1 || o->max_iter > FEWHA_MAX_ITER || !(o->rtol >= 0)) return FEWHA_ERR_ARG;
     if (o->launch_mode != FEWHA_LAUNCH_PERSISTENT && o->launch_mode != FEWHA_LAUNCH_PHASES) return FEWHA_ERR_ARG;
     if (o->recycle_mode != FEWHA_RECYCLE_LAST && o->recycle_mode != FEWHA_RECYCLE_ALL) return FEWHA_ERR_ARG;
     return static_cast<Handle *>(handle)->w()->solve(s, c, st, o, stats, stream);
+}
+
+int fewha_set_trace(void *handle, unsigned long long *trace_dev, int capacity)
+{
+    if (!handle || (trace_dev && capacity < 1)) return FEWHA_ERR_ARG;
+    static_cast<Handle *>(handle)->w()->set_trace(trace_dev, capacity);
+    return FEWHA_OK;
 }
 
 const char *fewha_strerror(int status)

@@ -32,10 +32,12 @@
 namespace fewha {
 
 constexpr int kThreads = 1024;     // threads of every CTA
-constexpr int kPairs = 8;          // DWT output pairs per thread: 128 * 64 / 1024
+constexpr int kPairs = 8;          // DWT output pairs per thread: 128 * 64 / 1024 (in place)
 constexpr int kMaxCtas = 1024;
 constexpr int kK = FEWHA_MAX_K;
 constexpr int kMaxT = 8;           // taps
+constexpr int kAdjW = 8;           // most pupil nodes one layer node gathers from, per axis
+constexpr int kSred = (4 + 2 * FEWHA_MAX_K) * 32;  // block_partials scratch (doubles)
 
 // partial-sum slots (slot-major array part[slot * kMaxCtas + cta])
 constexpr int kSlotE = 0;                       // parity p: + p*(4+2K): rz, zq, rp, rr, QTz[K], RP[K]
@@ -53,9 +55,14 @@ struct Bar {
 
 // Device record of one solve (scalars shared between phases).
 struct Record {
-    int status, done, iters, frame_bank;
-    double rz[FEWHA_MAX_ITER + 1];
+    int status, done, iters, chol_ok;
+    double rz[FEWHA_MAX_ITER + 1];      // (r_k, z_k) after the projection of z_k
+    double rinv[FEWHA_MAX_ITER + 1];    // 1 / rz[k]
     double alpha[FEWHA_MAX_ITER + 1];
+    double L[FEWHA_MAX_K * FEWHA_MAX_K];  // Cholesky factor of the old basis' Gram matrix (row-major, kv x kv)
+    double dinv[FEWHA_MAX_K];           // 1 / L_jj
+    double rinv_pqm;                    // 1 / (p_m, q_m) of the newest recycled direction
+    double bb;                          // ||b||^2 of this time step
     Bar bar;
 };
 
@@ -79,6 +86,11 @@ struct Geo {
     const int *band_layer, *band_row0, *band_rows;  // [nbands]
     const int *band_ilo, *band_ihi;  // [G][nbands] pupil rows the band touches
     int rows_chunk;             // pupil rows staged per pass of band_gather
+    int pingpong;               // layer phases have a second n x n shared buffer
+    // P_g^T weights per (g, l, axis, layer node k): pupil nodes adj_lo .. adj_lo +
+    // adj_cnt - 1 with weights adj_w[..][0 .. adj_cnt), index ((g*L + l)*2 + axis)*FEWHA_MAX_GRID + k
+    const int *adj_lo, *adj_cnt;
+    const T *adj_w;             // [..][kAdjW]
 };
 
 enum Mode { kApply = 0, kRhs = 1, kSolve = 2 };
@@ -90,6 +102,7 @@ struct Args {
     S *nodal;        // [n]  W^{-1} p (layer nodal values)
     S *psi;          // [G][m*m] Gamma^T C Gamma P_g (...) per guide star
     T *u;            // [n]  P^T psi (layer nodal adjoint)
+    T *wq;           // [n]  W^{-T} u / delta (operator output before + alpha D p)
     const T *x;      // apply: input
     T *y;            // apply / rhs: output
     const S *slopes; // rhs / solve: measured slopes
@@ -106,6 +119,9 @@ struct Args {
     Record *rec;
     unsigned long long timeout_ns;
     int ncta;        // CTAs that wrote partials (the solver grid)
+    size_t smem_bytes;  // dynamic shared memory of every launch
+    unsigned long long *trace;  // optional phase trace [trace_cap][4]: start, last CTA done, barrier passed, tag
+    int trace_cap;
     // derived per solve (host fills from nothing: phases read meta)
 };
 
@@ -141,6 +157,61 @@ __device__ __forceinline__ __nv_bfloat16 ldcg<__nv_bfloat16>(const __nv_bfloat16
 }
 __device__ __forceinline__ double ldcgd(const double *p) { return __ldcg(p); }
 __device__ __forceinline__ int ldcgi(const int *p) { return __ldcg(p); }
+
+// 16-byte vector access (float4 / double2): W = 16 / sizeof(T) elements at a
+// 16-byte aligned address.  vld_cg bypasses L1 (data written by another CTA
+// of the same launch), vld_nc uses the read-only path (data constant for the
+// launch).
+template <typename T>
+struct VW {
+    static constexpr int W = 16 / sizeof(T);
+};
+__device__ __forceinline__ void vld_cg(const float *p, float (&x)[4])
+{
+    const float4 v = __ldcg(reinterpret_cast<const float4 *>(p));
+    x[0] = v.x, x[1] = v.y, x[2] = v.z, x[3] = v.w;
+}
+__device__ __forceinline__ void vld_cg(const double *p, double (&x)[2])
+{
+    const double2 v = __ldcg(reinterpret_cast<const double2 *>(p));
+    x[0] = v.x, x[1] = v.y;
+}
+__device__ __forceinline__ void vld_nc(const float *p, float (&x)[4])
+{
+    const float4 v = __ldg(reinterpret_cast<const float4 *>(p));
+    x[0] = v.x, x[1] = v.y, x[2] = v.z, x[3] = v.w;
+}
+__device__ __forceinline__ void vld_nc(const double *p, double (&x)[2])
+{
+    const double2 v = __ldg(reinterpret_cast<const double2 *>(p));
+    x[0] = v.x, x[1] = v.y;
+}
+__device__ __forceinline__ void vld(const float *p, float (&x)[4])
+{
+    const float4 v = *reinterpret_cast<const float4 *>(p);
+    x[0] = v.x, x[1] = v.y, x[2] = v.z, x[3] = v.w;
+}
+__device__ __forceinline__ void vld(const double *p, double (&x)[2])
+{
+    const double2 v = *reinterpret_cast<const double2 *>(p);
+    x[0] = v.x, x[1] = v.y;
+}
+__device__ __forceinline__ void vst(float *p, const float (&x)[4])
+{
+    *reinterpret_cast<float4 *>(p) = make_float4(x[0], x[1], x[2], x[3]);
+}
+__device__ __forceinline__ void vst(double *p, const double (&x)[2])
+{
+    *reinterpret_cast<double2 *>(p) = make_double2(x[0], x[1]);
+}
+__device__ __forceinline__ void vst(__nv_bfloat16 *p, const float (&x)[4])
+{
+    __nv_bfloat162 a = __floats2bfloat162_rn(x[0], x[1]), b = __floats2bfloat162_rn(x[2], x[3]);
+    uint2 u;
+    u.x = *reinterpret_cast<unsigned int *>(&a);
+    u.y = *reinterpret_cast<unsigned int *>(&b);
+    *reinterpret_cast<uint2 *>(p) = u;
+}
 
 __device__ __forceinline__ unsigned long long gtimer()
 {
@@ -179,6 +250,7 @@ __device__ __forceinline__ A warp_sum_t(A v)
 // Block-wide sum of NV values per thread, written as partials of this CTA.
 template <int NV, typename A>
 __device__ void block_partials(A (&v)[NV], double *part, const int (&slot)[NV], double *sred)
+// sred: shared scratch of NV * 32 doubles
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
@@ -187,10 +259,10 @@ __device__ void block_partials(A (&v)[NV], double *part, const int (&slot)[NV], 
         if (lane == 0) sred[i * 32 + warp] = (double)s;
     }
     __syncthreads();
-    if (warp < NV) {
-        double s = lane < nw ? sred[warp * 32 + lane] : 0.0;
+    for (int i = warp; i < NV; i += nw) {
+        double s = lane < nw ? sred[i * 32 + lane] : 0.0;
         s = warp_sum(s);
-        if (lane == 0) part[(size_t)slot[warp] * kMaxCtas + blockIdx.x] = s;
+        if (lane == 0) part[(size_t)slot[i] * kMaxCtas + blockIdx.x] = s;
     }
     __syncthreads();
 }
@@ -202,11 +274,99 @@ __device__ inline void reduce_slots(const double *part, int ncta, int slot0, int
     for (int s = warp; s < count; s += nw) {
         const double *p = part + (size_t)(slot0 + s) * kMaxCtas;
         double acc = 0.0;
+#pragma unroll 8
         for (int c = lane; c < ncta; c += 32) acc += __ldcg(p + c);
         acc = warp_sum(acc);
         if (lane == 0) out[s] = acc;
     }
     __syncthreads();
+}
+
+// Up to three contiguous slot ranges reduced in one round (one warp per slot).
+struct SlotRange {
+    int slot0, count;
+    double *out;
+};
+__device__ inline void reduce_ranges(const double *part, int ncta, SlotRange r0, SlotRange r1 = {0, 0, nullptr},
+                                     SlotRange r2 = {0, 0, nullptr})
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int total = r0.count + r1.count + r2.count;
+    for (int s = warp; s < total; s += nw) {
+        int slot;
+        double *dst;
+        if (s < r0.count) {
+            slot = r0.slot0 + s;
+            dst = r0.out + s;
+        } else if (s < r0.count + r1.count) {
+            slot = r1.slot0 + s - r0.count;
+            dst = r1.out + s - r0.count;
+        } else {
+            slot = r2.slot0 + s - r0.count - r1.count;
+            dst = r2.out + s - r0.count - r1.count;
+        }
+        const double *p = part + (size_t)slot * kMaxCtas;
+        double v[8];
+#pragma unroll
+        for (int i = 0; i < 8; i++) v[i] = (lane + 32 * i < ncta) ? __ldcg(p + lane + 32 * i) : 0.0;
+        double acc = ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7]));
+        for (int c = lane + 256; c < ncta; c += 32) acc += __ldcg(p + c);
+        acc = warp_sum(acc);
+        if (lane == 0) *dst = acc;
+    }
+    __syncthreads();
+}
+
+// Warp-parallel Cholesky factorisation (right-looking) of the symmetrised
+// k x k matrix G (row-major): L (row-major, k x k, lower) and dinv_j = 1/L_jj.
+// Run by one full warp; returns false if not positive definite.
+__device__ inline bool warp_cholesky(int k, const double *G, double *L, double *dinv)
+{
+    const int lane = threadIdx.x & 31;
+    for (int e = lane; e < k * k; e += 32) {
+        const int i = e / k, j = e - i * k;
+        L[e] = i >= j ? 0.5 * (G[i * k + j] + G[j * k + i]) : 0.0;
+    }
+    __syncwarp();
+    for (int j = 0; j < k; j++) {
+        const double d = L[j * k + j];
+        if (!(d > 0.0)) return false;
+        const double r = rsqrt(d);
+        __syncwarp();
+        for (int i = j + 1 + lane; i < k; i += 32) L[i * k + j] *= r;
+        if (lane == 0) {
+            L[j * k + j] = d * r;
+            dinv[j] = r;
+        }
+        __syncwarp();
+        const int m = k - j - 1;
+        for (int e = lane; e < m * m; e += 32) {
+            const int i = j + 1 + e / m, t = j + 1 + e % m;
+            if (t <= i) L[i * k + t] -= L[i * k + j] * L[t * k + j];
+        }
+        __syncwarp();
+    }
+    return true;
+}
+
+// Warp-parallel solve of L L^T x = rhs (factor from warp_cholesky); x may alias rhs.
+__device__ inline void warp_chol_solve(int k, const double *L, const double *dinv, const double *rhs, double *x)
+{
+    const int lane = threadIdx.x & 31;
+    double v = lane < k ? rhs[lane] : 0.0;
+    for (int j = 0; j < k; j++) {  // forward: L y = rhs
+        const double yj = __shfl_sync(0xffffffffu, v, j) * dinv[j];
+        if (lane == j) v = yj;
+        if (lane > j && lane < k) v -= L[lane * k + j] * yj;
+    }
+    for (int j = k - 1; j >= 0; j--) {  // backward: L^T x = y
+        const double xj = __shfl_sync(0xffffffffu, v, j) * dinv[j];
+        if (lane == j) v = xj;
+        if (lane < j) v -= L[j * k + lane] * xj;
+    }
+    __syncwarp();
+    if (lane < k) x[lane] = v;
+    __syncwarp();
 }
 
 // Cholesky solve of the symmetrised k x k Gram matrix (row-major in Graw),
@@ -246,12 +406,19 @@ __device__ __forceinline__ void set_status(Record *rec, int st)
 
 // Grid barrier with a time limit.  Returns false (and the CTA must return)
 // when any CTA has recorded an error or the wait ran past timeout_ns.
-__device__ inline bool grid_sync(Record *rec, unsigned long long timeout_ns)
+__device__ inline bool grid_sync(Record *rec, unsigned long long timeout_ns,
+                                 unsigned long long *trace_slot = nullptr)
 {
     __shared__ int ok;
+    __shared__ unsigned long long t_pass;  // when this CTA passed its previous barrier
     __syncthreads();
     if (threadIdx.x == 0) {
         ok = 1;
+        if (trace_slot) {
+            const unsigned long long now = gtimer();
+            atomicMax(trace_slot + 1, now);
+            if (t_pass) atomicMax(trace_slot, now - t_pass);
+        }
         volatile unsigned int *vgen = &rec->bar.gen;
         volatile int *vst = &rec->status;
         unsigned int g = *vgen;
@@ -277,6 +444,8 @@ __device__ inline bool grid_sync(Record *rec, unsigned long long timeout_ns)
         }
         __threadfence();
         if (*vst != 0) ok = 0;
+        if (trace_slot && blockIdx.x == 0) trace_slot[2] = gtimer();
+        t_pass = trace_slot ? gtimer() : 0ull;
     }
     __syncthreads();
     return ok != 0;
@@ -286,102 +455,217 @@ __device__ inline bool grid_sync(Record *rec, unsigned long long timeout_ns)
 // Periodic orthonormal DWT passes in shared memory (Sec. 3, Eq. fewha)
 //   analysis:  a_k = sum_t h_t x_{(2k+t) mod N},  d_k = sum_t g_t x_{(2k+t) mod N}
 //   synthesis: x_{2m+e} = sum_u h_{e+2u} a_{(m-u) mod N/2} + g_{e+2u} d_{(m-u) mod N/2}
-// In place: every thread first computes its outputs into registers, then the
-// block synchronises and writes them back.
+// The layer sits in shared memory row-major with pitch n + 1 (odd: one thread
+// per row or per column is free of bank conflicts).  N is a power of two, so
+// index reductions are bit masks.  The tap count L is a template parameter
+// and the taps live in registers.  A thread computes kRun consecutive output
+// pairs of one line from a register window (each input loaded once per run).
 // ---------------------------------------------------------------------------
-template <typename T, bool ROWS, bool SYNTH>
-__device__ void dwt_pass(T *buf, int pitch, int lgN, const Geo<T> &G)
+constexpr int kRun = 4;                          // output pairs per run
+constexpr int kRuns = kPairs / kRun;             // runs per thread (128 x 64 pairs / 1024 threads)
+
+template <typename T, int L>
+struct Taps {
+    T h[L], g[L];
+};
+
+template <typename T, int L>
+__device__ __forceinline__ Taps<T, L> load_taps(const Geo<T> &G)
 {
-    const int N = 1 << lgN, half = N >> 1, total = N * half, Lh = G.n_taps >> 1;
-    const int lgh = lgN - 1;
-    const int stride = ROWS ? 1 : pitch;
-    T o0[kPairs], o1[kPairs];
+    Taps<T, L> tp;
 #pragma unroll
-    for (int t = 0; t < kPairs; t++) {
-        const int idx = threadIdx.x + t * blockDim.x;
-        o0[t] = o1[t] = T(0);
-        if (idx < total) {
-            // ROWS: line = row, m along the row; COLS: line = column (consecutive
-            // threads take consecutive columns), m along the column
-            const int line = ROWS ? (idx >> lgh) : (idx & (N - 1));
-            const int m = ROWS ? (idx & (half - 1)) : (idx >> lgN);
-            const T *base = ROWS ? buf + line * pitch : buf + line;
-            T x0 = 0, x1 = 0;
-            if (SYNTH) {
+    for (int u = 0; u < L; u++) {
+        tp.h[u] = G.h[u];
+        tp.g[u] = G.g[u];
+    }
+    return tp;
+}
+
+// One run of `run` output pairs starting at pair m0 of the line at base
+// (element stride es), into out[0 .. 2 kRun).
+template <typename T, int L, bool SYNTH>
+__device__ __forceinline__ void dwt_run(const T *base, int es, int N, int half, int run, int m0,
+                                        const Taps<T, L> &tp, T (&out)[2 * kRun])
+{
+    constexpr int Lh = L / 2;
+    if (SYNTH) {
+        T wa[kRun + Lh - 1], wd[kRun + Lh - 1];  // a_{m0-Lh+1 .. m0+kRun-1}, same for d
 #pragma unroll
-                for (int u = 0; u < kMaxT / 2; u++) {
-                    if (u < Lh) {
-                        const int k = (m - u) & (half - 1);
-                        const T a = base[k * stride], d = base[(half + k) * stride];
-                        x0 += G.h[2 * u] * a + G.g[2 * u] * d;
-                        x1 += G.h[2 * u + 1] * a + G.g[2 * u + 1] * d;
-                    }
-                }
+        for (int i = 0; i < kRun + Lh - 1; i++) {
+            if (i < run + Lh - 1) {
+                const int k = (m0 - Lh + 1 + i) & (half - 1);
+                wa[i] = base[k * es];
+                wd[i] = base[(half + k) * es];
             } else {
-#pragma unroll
-                for (int u = 0; u < kMaxT; u++) {
-                    if (u < 2 * Lh) {
-                        const T v = base[((2 * m + u) & (N - 1)) * stride];
-                        x0 += G.h[u] * v;
-                        x1 += G.g[u] * v;
-                    }
-                }
+                wa[i] = wd[i] = T(0);
             }
-            o0[t] = x0;
-            o1[t] = x1;
         }
-    }
-    __syncthreads();
 #pragma unroll
-    for (int t = 0; t < kPairs; t++) {
-        const int idx = threadIdx.x + t * blockDim.x;
-        if (idx < total) {
-            const int line = ROWS ? (idx >> lgh) : (idx & (N - 1));
-            const int m = ROWS ? (idx & (half - 1)) : (idx >> lgN);
-            T *base = ROWS ? buf + line * pitch : buf + line;
-            const int p0 = SYNTH ? 2 * m : m, p1 = SYNTH ? 2 * m + 1 : half + m;
-            base[p0 * stride] = o0[t];
-            base[p1 * stride] = o1[t];
+        for (int q = 0; q < kRun; q++) {
+            T x0 = 0, x1 = 0;
+#pragma unroll
+            for (int u = 0; u < Lh; u++) {
+                const T a = wa[q + Lh - 1 - u], d = wd[q + Lh - 1 - u];
+                x0 += tp.h[2 * u] * a + tp.g[2 * u] * d;
+                x1 += tp.h[2 * u + 1] * a + tp.g[2 * u + 1] * d;
+            }
+            out[2 * q] = x0;
+            out[2 * q + 1] = x1;
+        }
+    } else {
+        T wx[2 * kRun + L - 2];  // x_{2 m0 .. 2 m0 + 2 kRun + L - 3}
+#pragma unroll
+        for (int i = 0; i < 2 * kRun + L - 2; i++)
+            wx[i] = (i < 2 * run + L - 2) ? base[((2 * m0 + i) & (N - 1)) * es] : T(0);
+#pragma unroll
+        for (int q = 0; q < kRun; q++) {
+            T a = 0, d = 0;
+#pragma unroll
+            for (int u = 0; u < L; u++) {
+                a += tp.h[u] * wx[2 * q + u];
+                d += tp.g[u] * wx[2 * q + u];
+            }
+            out[2 * q] = a;
+            out[2 * q + 1] = d;
         }
     }
-    __syncthreads();
 }
 
-template <typename T>
-__device__ void idwt2(T *buf, int lgn, int J, const Geo<T> &G)
+template <bool SYNTH, typename T>
+__device__ __forceinline__ void dwt_store(T *base, int es, int half, int run, int m0, const T (&out)[2 * kRun])
 {
+#pragma unroll
+    for (int q = 0; q < kRun; q++) {
+        if (q < run) {
+            const int p0 = SYNTH ? 2 * (m0 + q) : m0 + q;
+            const int p1 = SYNTH ? 2 * (m0 + q) + 1 : half + m0 + q;
+            base[p0 * es] = out[2 * q];
+            base[p1 * es] = out[2 * q + 1];
+        }
+    }
+}
+
+// One pass over the top-left N x N block from src to dst (pitch P).  Thread
+// idx takes line idx mod N and run idx / N: consecutive threads work on
+// consecutive rows (ROWS) or columns.  FP32: dst is the ping-pong buffer.
+// FP64 (a 128 x 129 layer fills 132 KB): in place, outputs held in registers
+// across a block barrier (src == dst).
+template <typename T, int L, bool ROWS, bool SYNTH>
+__device__ void dwt_pass(const T *src, T *dst, int P, int lgN, const Taps<T, L> &tp)
+{
+    const int N = 1 << lgN, half = N >> 1;
+    const int run = half < kRun ? half : kRun;       // pairs per run
+    const int total = N * (half / run);              // runs in the pass
+    const int es = ROWS ? 1 : P;                     // element stride along a line
+    const int ls = ROWS ? P : 1;                     // stride between lines
+    if constexpr (sizeof(T) == 4) {
+        for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+            const int line = idx & (N - 1), m0 = (idx >> lgN) * run;
+            T out[2 * kRun];
+            dwt_run<T, L, SYNTH>(src + line * ls, es, N, half, run, m0, tp, out);
+            dwt_store<SYNTH>(dst + line * ls, es, half, run, m0, out);
+        }
+        __syncthreads();
+    } else {
+        T out[kRuns][2 * kRun];
+#pragma unroll
+        for (int t = 0; t < kRuns; t++) {
+            const int idx = threadIdx.x + t * blockDim.x;
+            if (idx < total) {
+                const int line = idx & (N - 1), m0 = (idx >> lgN) * run;
+                dwt_run<T, L, SYNTH>(src + line * ls, es, N, half, run, m0, tp, out[t]);
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int t = 0; t < kRuns; t++) {
+            const int idx = threadIdx.x + t * blockDim.x;
+            if (idx < total) {
+                const int line = idx & (N - 1), m0 = (idx >> lgN) * run;
+                dwt_store<SYNTH>(dst + line * ls, es, half, run, m0, out[t]);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Multi-level transforms of an n x n layer in buf (pitch n + 1); tmp is a
+// second buffer (FP32 ping-pong: both passes of a level return to buf) or buf.
+template <typename T, int L>
+__device__ void idwt2_L(T *buf, T *tmp, int lgn, int J, const Geo<T> &G)
+{
+    const Taps<T, L> tp = load_taps<T, L>(G);
+    const int P = (1 << lgn) + 1;
     for (int t = J - 1; t >= 0; t--) {
-        dwt_pass<T, false, true>(buf, 1 << lgn, lgn - t, G);
-        dwt_pass<T, true, true>(buf, 1 << lgn, lgn - t, G);
+        dwt_pass<T, L, false, true>(buf, tmp, P, lgn - t, tp);
+        dwt_pass<T, L, true, true>(tmp, buf, P, lgn - t, tp);
+    }
+}
+
+template <typename T, int L>
+__device__ void fdwt2_L(T *buf, T *tmp, int lgn, int J, const Geo<T> &G)
+{
+    const Taps<T, L> tp = load_taps<T, L>(G);
+    const int P = (1 << lgn) + 1;
+    for (int t = 0; t < J; t++) {
+        dwt_pass<T, L, true, false>(buf, tmp, P, lgn - t, tp);
+        dwt_pass<T, L, false, false>(tmp, buf, P, lgn - t, tp);
+    }
+}
+
+// Daubechies-1..4 (2..8 taps)
+template <typename T>
+__device__ void idwt2(T *buf, T *tmp, int lgn, int J, const Geo<T> &G)
+{
+    switch (G.n_taps) {
+    case 2: idwt2_L<T, 2>(buf, tmp, lgn, J, G); break;
+    case 4: idwt2_L<T, 4>(buf, tmp, lgn, J, G); break;
+    case 6: idwt2_L<T, 6>(buf, tmp, lgn, J, G); break;
+    default: idwt2_L<T, 8>(buf, tmp, lgn, J, G); break;
     }
 }
 
 template <typename T>
-__device__ void fdwt2(T *buf, int lgn, int J, const Geo<T> &G)
+__device__ void fdwt2(T *buf, T *tmp, int lgn, int J, const Geo<T> &G)
 {
-    for (int t = 0; t < J; t++) {
-        dwt_pass<T, true, false>(buf, 1 << lgn, lgn - t, G);
-        dwt_pass<T, false, false>(buf, 1 << lgn, lgn - t, G);
+    switch (G.n_taps) {
+    case 2: fdwt2_L<T, 2>(buf, tmp, lgn, J, G); break;
+    case 4: fdwt2_L<T, 4>(buf, tmp, lgn, J, G); break;
+    case 6: fdwt2_L<T, 6>(buf, tmp, lgn, J, G); break;
+    default: fdwt2_L<T, 8>(buf, tmp, lgn, J, G); break;
     }
 }
 
-// ---------------------------------------------------------------------------
-// Layer phase 1: coefficients -> nodal values, nodal = W^T coef / delta_l.
-// `load(e)` returns the coefficient of global index e (and may fuse vector
-// updates); runs for the layers owned by this CTA.
-// ---------------------------------------------------------------------------
-template <typename T, typename S, class Load>
-__device__ void layer_idwt(const Args<T, S> &A, T *buf, Load load)
+// Layer element e (row-major, n columns) <-> shared-memory index (pitch n + 1).
+__device__ __forceinline__ int spad(int e, int lgn) { return e + (e >> lgn); }
+
+template <typename T, typename S, class Load, class Post>
+__device__ void layer_idwt(const Args<T, S> &A, T *buf, Load load, Post post)
 {
+    constexpr int W = VW<T>::W;
     const Geo<T> &G = A.geo;
     for (int l = blockIdx.x; l < G.L; l += gridDim.x) {
-        const int n = G.lay_n[l], nn = n * n;
+        const int n = G.lay_n[l], lgn = G.lay_lg[l], nv = n * n / W;
         const long off = G.lay_off[l];
-        for (int e = threadIdx.x; e < nn; e += blockDim.x) buf[e] = load(off + e);
+#pragma unroll 2
+        for (int v = threadIdx.x; v < nv; v += blockDim.x) {
+            T x[W];
+            load(off + (long)v * W, x);
+            const int s0 = spad(v * W, lgn);
+#pragma unroll
+            for (int i = 0; i < W; i++) buf[s0 + i] = x[i];
+        }
         __syncthreads();
-        idwt2<T>(buf, G.lay_lg[l], G.lay_J[l], G);
+        post(l, buf);
+        idwt2<T>(buf, G.pingpong ? buf + n * (n + 1) : buf, lgn, G.lay_J[l], G);
         const T sc = G.inv_delta[l];
-        for (int e = threadIdx.x; e < nn; e += blockDim.x) A.nodal[off + e] = Cv<S>::st(buf[e] * sc);
+        for (int v = threadIdx.x; v < nv; v += blockDim.x) {
+            T x[W];
+            const int s0 = spad(v * W, lgn);
+#pragma unroll
+            for (int i = 0; i < W; i++) x[i] = buf[s0 + i] * sc;
+            vst(A.nodal + off + (long)v * W, x);
+        }
         __syncthreads();
     }
 }
@@ -395,7 +679,7 @@ __device__ void layer_idwt(const Args<T, S> &A, T *buf, Load load)
 //   both    : psi_g = Gamma^T (weighted slopes) on the tile's nodes.
 // ---------------------------------------------------------------------------
 template <typename T, typename S, bool RHS>
-__device__ typename AccT<T>::type wfs_phase(const Args<T, S> &A, T *sm)
+__device__ __noinline__ typename AccT<T>::type wfs_phase(const Args<T, S> &A, T *sm)
 {
     typedef typename AccT<T>::type Acc;
     const Geo<T> &G = A.geo;
@@ -485,53 +769,70 @@ __device__ typename AccT<T>::type wfs_phase(const Args<T, S> &A, T *sm)
 // Thread (a - a0, b) owns output u[a][b]; no atomics, fixed summation order.
 // ---------------------------------------------------------------------------
 template <typename T, typename S>
-__device__ void band_gather(const Args<T, S> &A, T *sm)
+__device__ __noinline__ void band_gather(const Args<T, S> &A, T *sm)
 {
     const Geo<T> &G = A.geo;
-    const int m = G.m, RC = G.rows_chunk;
-    for (int w = blockIdx.x; w < G.nbands; w += gridDim.x) {
+    const int m = G.m, RC = G.rows_chunk, NB = G.nbands;
+    for (int w = blockIdx.x; w < NB; w += gridDim.x) {
         const int l = __ldg(G.band_layer + w), a0 = __ldg(G.band_row0 + w), BR = __ldg(G.band_rows + w);
-        const int n = G.lay_n[l], nout = BR * n;
-        T *ps = sm;               // [RC][m]   staged psi rows
-        T *Tb = sm + RC * m;      // [RC][n]   x-contracted rows
+        const int n = G.lay_n[l], lgn = G.lay_lg[l], nout = BR << lgn;
+        const int oa = threadIdx.x >> lgn, ob = threadIdx.x & (n - 1);  // owned output (a0 + oa, ob)
         T acc = 0;
-        const int oa = threadIdx.x / n, ob = threadIdx.x - oa * n;  // owned output (a0 + oa, ob)
-        for (int g = 0; g < G.G; g++) {
-            const int bx = (g * G.L + l) * 2, by = bx + 1;
-            const int ilo = __ldg(G.band_ilo + g * G.nbands + w), ihi = __ldg(G.band_ihi + g * G.nbands + w);
-            const S *psg = A.psi + (size_t)g * m * m;
-            for (int c0 = ilo; c0 < ihi; c0 += RC) {
-                const int rows = min(RC, ihi - c0);
-                for (int e = threadIdx.x; e < rows * m; e += blockDim.x)
-                    ps[e] = Cv<S>::ld(ldcg(psg + (size_t)c0 * m + e));
-                __syncthreads();
-                for (int e = threadIdx.x; e < rows * n; e += blockDim.x) {
-                    const int i = e / n, b = e - i * n;
-                    const int jlo = __ldg(G.alo + bx * FEWHA_MAX_GRID + b);
-                    const int jhi = __ldg(G.ahi + bx * FEWHA_MAX_GRID + b);
-                    T v = 0;
-                    for (int j = jlo; j < jhi; j++) {
-                        const T w0 = __ldg(G.fw + bx * m + j);
-                        const T wx = (__ldg(G.fk + bx * m + j) == b) ? T(1) - w0 : w0;
-                        v += wx * ps[i * m + j];
-                    }
-                    Tb[e] = v;
-                }
-                __syncthreads();
-                if (oa < BR) {
-                    const int a = a0 + oa;
-                    const int rlo = max(__ldg(G.alo + by * FEWHA_MAX_GRID + a), c0);
-                    const int rhi = min(__ldg(G.ahi + by * FEWHA_MAX_GRID + a), c0 + rows);
-                    for (int i = rlo; i < rhi; i++) {
-                        const T w0 = __ldg(G.fw + by * m + i);
-                        const T wy = (__ldg(G.fk + by * m + i) == a) ? T(1) - w0 : w0;
-                        acc += wy * Tb[(i - c0) * n + ob];
-                    }
-                }
-                __syncthreads();
+        T *ps = sm;           // [RC][m] staged psi rows
+        T *Tb = sm + RC * m;  // [RC][n] their x-contraction
+        // guide stars in groups whose pupil rows fit the RC staged rows
+        for (int g0 = 0, g1; g0 < G.G; g0 = g1) {
+            int rows_tot = 0;
+            for (g1 = g0; g1 < G.G; g1++) {
+                const int r = __ldg(G.band_ihi + g1 * NB + w) - __ldg(G.band_ilo + g1 * NB + w);
+                if (rows_tot + r > RC) break;
+                rows_tot += r;
             }
+            if (g1 == g0) g1 = g0 + 1;  // unreachable: the host sizes RC >= the rows of any one guide star
+            // stage psi rows (one latency round for the group)
+            for (int g = g0, base = 0; g < g1; g++) {
+                const int ilo = __ldg(G.band_ilo + g * NB + w), rows = __ldg(G.band_ihi + g * NB + w) - ilo;
+                const S *src = A.psi + (size_t)g * m * m + (size_t)ilo * m;
+                for (int e = threadIdx.x; e < rows * m; e += blockDim.x) ps[base * m + e] = Cv<S>::ld(ldcg(src + e));
+                base += rows;
+            }
+            __syncthreads();
+            // x-contraction: Tb[i][b] = sum_j Wx[j][b] psi[i][j]
+            for (int g = g0, base = 0; g < g1; g++) {
+                const int rows = __ldg(G.band_ihi + g * NB + w) - __ldg(G.band_ilo + g * NB + w);
+                const int tx = ((g * G.L + l) * 2) * FEWHA_MAX_GRID;
+                for (int e = threadIdx.x; e < (rows << lgn); e += blockDim.x) {
+                    const int i = e >> lgn, b = e & (n - 1);
+                    const int jlo = __ldg(G.adj_lo + tx + b), cnt = __ldg(G.adj_cnt + tx + b);
+                    const T *wt = G.adj_w + (size_t)(tx + b) * kAdjW;
+                    const T *row = ps + (base + i) * m + jlo;
+                    T v = 0;
+#pragma unroll
+                    for (int c = 0; c < kAdjW; c++)
+                        if (c < cnt) v += __ldg(wt + c) * row[c];
+                    Tb[((base + i) << lgn) + b] = v;
+                }
+                base += rows;
+            }
+            __syncthreads();
+            // y-contraction into the owned output
+            if (oa < BR) {
+                const int a = a0 + oa;
+                for (int g = g0, base = 0; g < g1; g++) {
+                    const int ilo = __ldg(G.band_ilo + g * NB + w), rows = __ldg(G.band_ihi + g * NB + w) - ilo;
+                    const int ty = ((g * G.L + l) * 2 + 1) * FEWHA_MAX_GRID + a;
+                    const int ilo_a = __ldg(G.adj_lo + ty), cnt = __ldg(G.adj_cnt + ty);
+                    const T *wt = G.adj_w + (size_t)ty * kAdjW;
+                    const T *col = Tb + ((base + ilo_a - ilo) << lgn) + ob;
+#pragma unroll
+                    for (int c = 0; c < kAdjW; c++)
+                        if (c < cnt) acc += __ldg(wt + c) * col[c << lgn];
+                    base += rows;
+                }
+            }
+            __syncthreads();
         }
-        if (oa < BR && threadIdx.x < nout) A.u[G.lay_off[l] + (long)(a0 + oa) * n + ob] = acc;
+        if (oa < BR && threadIdx.x < nout) A.u[G.lay_off[l] + ((long)(a0 + oa) << lgn) + ob] = acc;
     }
 }
 
@@ -542,17 +843,41 @@ __device__ void band_gather(const Args<T, S> &A, T *sm)
 template <typename T, typename S, class Store>
 __device__ void layer_fdwt(const Args<T, S> &A, T *buf, Store store)
 {
+    constexpr int W = VW<T>::W;
     const Geo<T> &G = A.geo;
     for (int l = blockIdx.x; l < G.L; l += gridDim.x) {
-        const int n = G.lay_n[l], nn = n * n;
+        const int n = G.lay_n[l], lgn = G.lay_lg[l], nv = n * n / W;
         const long off = G.lay_off[l];
-        for (int e = threadIdx.x; e < nn; e += blockDim.x) buf[e] = ldcg(A.u + off + e);
+#pragma unroll 4
+        for (int v = threadIdx.x; v < nv; v += blockDim.x) {
+            T x[W];
+            vld_cg(A.u + off + (long)v * W, x);
+            const int s0 = spad(v * W, lgn);
+#pragma unroll
+            for (int i = 0; i < W; i++) buf[s0 + i] = x[i];
+        }
         __syncthreads();
-        fdwt2<T>(buf, G.lay_lg[l], G.lay_J[l], G);
+        fdwt2<T>(buf, G.pingpong ? buf + n * (n + 1) : buf, lgn, G.lay_J[l], G);
         const T sc = G.inv_delta[l];
-        for (int e = threadIdx.x; e < nn; e += blockDim.x) store(off + e, buf[e] * sc);
+#pragma unroll 2
+        for (int v = threadIdx.x; v < nv; v += blockDim.x) {
+            T x[W];
+            const int s0 = spad(v * W, lgn);
+#pragma unroll
+            for (int i = 0; i < W; i++) x[i] = buf[s0 + i] * sc;
+            store(off + (long)v * W, x);
+        }
         __syncthreads();
     }
+}
+
+// Element range of this CTA for vector phases, aligned to W elements.
+__device__ __forceinline__ void cta_range_vec(long n, int W, long &lo, long &hi)
+{
+    long nv = n / W;
+    long chunk = (nv + gridDim.x - 1) / gridDim.x;
+    lo = (long)blockIdx.x * chunk * W;
+    hi = lo + chunk * W < n ? lo + chunk * W : n;
 }
 
 // Element range of this CTA for vector phases.

@@ -27,14 +27,15 @@ __device__ __forceinline__ T *dyn_smem()
 template <typename T, typename S>
 __global__ void __launch_bounds__(kThreads, 1) k_apply_idwt(Args<T, S> A)
 {
-    layer_idwt<T, S>(A, dyn_smem<T>(), [&](long e) -> T { return A.x[e]; });
+    constexpr int W = VW<T>::W;
+    layer_idwt<T, S>(A, dyn_smem<T>(), [&](long e, T (&x)[W]) { vld(A.x + e, x); }, [](int, const T *) {});
 }
 
 // psi = Gamma^T C Gamma P nodal (RHS = false) or Gamma^T C s (RHS = true)
 template <typename T, typename S, bool RHS>
 __global__ void __launch_bounds__(kThreads, 1) k_wfs(Args<T, S> A)
 {
-    __shared__ double sred[8 * 32];
+    __shared__ double sred[kSred];
     typename AccT<T>::type acc[1] = {wfs_phase<T, S, RHS>(A, dyn_smem<T>())};
     const int slots[1] = {kSlotB};
     block_partials<1>(acc, A.part, slots, sred);
@@ -52,24 +53,44 @@ __global__ void __launch_bounds__(kThreads, 1) k_gather(Args<T, S> A)
 template <typename T, typename S, bool RHS>
 __global__ void __launch_bounds__(kThreads, 1) k_fdwt(Args<T, S> A)
 {
-    layer_fdwt<T, S>(A, dyn_smem<T>(), [&](long e, T v) {
-        A.y[e] = RHS ? v : v + A.geo.alpha_d[e] * A.x[e];
+    constexpr int W = VW<T>::W;
+    layer_fdwt<T, S>(A, dyn_smem<T>(), [&](long e, const T (&v)[W]) {
+        T y[W], x[W], ad[W];
+        if (!RHS) {
+            vld(A.x + e, x);
+            vld_nc(A.geo.alpha_d + e, ad);
+        }
+#pragma unroll
+        for (int i = 0; i < W; i++) y[i] = RHS ? v[i] : v[i] + ad[i] * x[i];
+        vst(A.y + e, y);
     });
 }
 
 // --- solver phases, one kernel each (FEWHA_LAUNCH_PHASES) -------------------
 #define FEWHA_PHASE_GUARD                                             \
     __shared__ Scal sc;                                               \
-    __shared__ double sred[8 * 32];                                   \
+    __shared__ double sred[kSred];                                   \
     (void)sred;                                                       \
     if (ldcgi(&A.rec->done) || ldcgi(&A.rec->status)) return;         \
     const Basis b = basis_info(A);                                    \
     (void)b;
 
+// R1: weighted slopes -> psi, and the Gram matrix of the old basis
 template <typename T, typename S>
 __global__ void __launch_bounds__(kThreads, 1) k_rhs_wfs(Args<T, S> A)
 {
     wfs_phase<T, S, true>(A, dyn_smem<T>());
+    const Basis b = basis_info(A);
+    if (b.kv > 0) phase_gram<T, S>(A, b, dyn_smem<T>(), (int)(A.smem_bytes / sizeof(T)));
+}
+
+// R2: u = P^T psi; the last CTA also factorises the Gram matrix
+template <typename T, typename S>
+__global__ void __launch_bounds__(kThreads, 1) k_rhs_gather(Args<T, S> A)
+{
+    FEWHA_PHASE_GUARD
+    band_gather<T, S>(A, dyn_smem<T>());
+    if (b.kv > 0 && blockIdx.x == gridDim.x - 1) phase_factor<T, S>(A, b, sc);
 }
 
 template <typename T, typename S>
@@ -81,18 +102,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_rhs_fdwt(Args<T, S> A)
 }
 
 template <typename T, typename S>
-__global__ void __launch_bounds__(kThreads, 1) k_gram(Args<T, S> A)
+__global__ void __launch_bounds__(kThreads, 1) k_ptr(Args<T, S> A)
 {
     FEWHA_PHASE_GUARD
     (void)sc;
-    if (b.kv > 0) phase_gram<T, S>(A, b);
+    if (b.kv > 0) phase_ptr<T, S>(A, b, sred);
 }
 
 template <typename T, typename S>
 __global__ void __launch_bounds__(kThreads, 1) k_init(Args<T, S> A)
 {
     FEWHA_PHASE_GUARD
-    if (b.kv > 0) phase_init<T, S>(A, b, sc);
+    if (b.kv > 0) phase_init<T, S>(A, b, sc, sred);
 }
 
 template <typename T, typename S>
@@ -124,7 +145,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_D(Args<T, S> A, int k)
 {
     FEWHA_PHASE_GUARD
     (void)sc;
-    phase_D<T, S>(A, b, k, dyn_smem<T>());
+    phase_D<T, S>(A, dyn_smem<T>());
 }
 
 template <typename T, typename S>
@@ -150,45 +171,56 @@ template <typename T, typename S>
 __global__ void __launch_bounds__(kThreads, 1) k_solve_persistent(Args<T, S> A)
 {
     __shared__ Scal sc;
-    __shared__ double sred[8 * 32];
+    __shared__ double sred[kSred];
     T *sm = dyn_smem<T>();
     const unsigned long long to = A.timeout_ns;
     const Basis b = basis_info(A);
+    int ti = 0;  // trace slot of the next barrier
+    // barrier with the optional phase trace (tag = phase id)
+    auto sync = [&](int tag) -> bool {
+        unsigned long long *slot = (A.trace && ti < A.trace_cap) ? A.trace + 4 * ti : nullptr;
+        if (slot && blockIdx.x == 0 && threadIdx.x == 0) slot[3] = (unsigned long long)tag;
+        bool ok = grid_sync(A.rec, to, slot);
+        ti++;
+        return ok;
+    };
     int K = A.max_iter;
     do {
         wfs_phase<T, S, true>(A, sm);
-        if (!grid_sync(A.rec, to)) break;
+        if (b.kv > 0) phase_gram<T, S>(A, b, sm, (int)(A.smem_bytes / sizeof(T)));
+        if (!sync(1)) break;
         band_gather<T, S>(A, sm);
-        if (!grid_sync(A.rec, to)) break;
+        if (b.kv > 0 && blockIdx.x == gridDim.x - 1) phase_factor<T, S>(A, b, sc);
+        if (!sync(2)) break;
         phase_rhs_fdwt<T, S>(A, sm, sred);
-        if (!grid_sync(A.rec, to)) break;
+        if (!sync(3)) break;
         if (b.kv > 0) {
-            phase_gram<T, S>(A, b);
-            if (!grid_sync(A.rec, to)) break;
-            bool ok = phase_init<T, S>(A, b, sc);
-            if (!grid_sync(A.rec, to) || !ok) break;
+            phase_ptr<T, S>(A, b, sred);
+            if (!sync(4)) break;
+            phase_init<T, S>(A, b, sc, sred);
+            if (!sync(5)) break;
         }
         for (int k = 0; k < A.max_iter; k++) {
             if (!phase_A<T, S>(A, b, k, sm, sc, sred)) {
                 K = k;
                 break;
             }
-            if (!grid_sync(A.rec, to)) break;
+            if (!sync(11)) break;
             {
                 typename AccT<T>::type acc[1] = {wfs_phase<T, S, false>(A, sm)};
                 const int slots[1] = {kSlotB + (k & 1)};
                 block_partials<1>(acc, A.part, slots, sred);
             }
-            if (!grid_sync(A.rec, to)) break;
+            if (!sync(12)) break;
             if (!phase_C<T, S>(A, b, k, sm, sc)) {
                 K = k;
                 break;
             }
-            if (!grid_sync(A.rec, to)) break;
-            phase_D<T, S>(A, b, k, sm);
-            if (!grid_sync(A.rec, to)) break;
+            if (!sync(13)) break;
+            phase_D<T, S>(A, sm);
+            if (!sync(14)) break;
             phase_E<T, S>(A, b, k, sred);
-            if (!grid_sync(A.rec, to)) break;
+            if (!sync(15)) break;
         }
     } while (0);
     // on a device-side error the stats carry the status; the other fields are
@@ -224,6 +256,7 @@ struct ImplBase {
     virtual int solve(const void *sl, void *c, const fewha_state *st, const fewha_solve_opts *o,
                       fewha_stats *stats, cudaStream_t s) = 0;
     virtual int set_invJ(const std::vector<double> &invJ) = 0;
+    virtual void set_trace(unsigned long long *buf, int cap) = 0;
 };
 
 template <typename T, typename S>
@@ -308,7 +341,8 @@ struct Impl : ImplBase {
         }
         G.nbands = (int)bl.size();
         std::vector<int> bilo((size_t)P.G * G.nbands), bihi((size_t)P.G * G.nbands);
-        int max_rows = 1;
+        int max_rows = 1, max_rows_sum = 1;
+        std::vector<int> rows_sum(G.nbands, 0);
         for (int g = 0; g < P.G; g++)
             for (int w = 0; w < G.nbands; w++) {
                 int lo = P.m, hi = 0;
@@ -324,28 +358,53 @@ struct Impl : ImplBase {
                 bilo[(size_t)g * G.nbands + w] = lo;
                 bihi[(size_t)g * G.nbands + w] = hi;
                 max_rows = std::max(max_rows, hi - lo);
+                rows_sum[w] += hi - lo;
+                max_rows_sum = std::max(max_rows_sum, rows_sum[w]);
             }
+        // compact P_g^T weights: per layer node, its pupil-node range and weights
+        {
+            size_t nt = (size_t)P.G * P.L * 2 * FEWHA_MAX_GRID;
+            std::vector<int> alo(nt, 0), acnt(nt, 0);
+            std::vector<T> aw(nt * kAdjW, T(0));
+            for (size_t t = 0; t < (size_t)P.G * P.L * 2; t++)
+                for (int k = 0; k < FEWHA_MAX_GRID; k++) {
+                    int lo = P.alo[t * FEWHA_MAX_GRID + k], hi = P.ahi[t * FEWHA_MAX_GRID + k];
+                    if (hi - lo > kAdjW) return FEWHA_ERR_GEOMETRY;
+                    alo[t * FEWHA_MAX_GRID + k] = lo;
+                    acnt[t * FEWHA_MAX_GRID + k] = hi - lo;
+                    for (int j = lo; j < hi; j++) {
+                        double w0 = P.fw[t * P.m + j];
+                        aw[(t * FEWHA_MAX_GRID + k) * kAdjW + (j - lo)] =
+                            (T)(P.fk[t * P.m + j] == k ? 1.0 - w0 : w0);
+                    }
+                }
+            if ((st = up(alo, &G.adj_lo)) || (st = up(acnt, &G.adj_cnt)) || (st = up(aw, &G.adj_w))) return st;
+        }
         if ((st = up(bl, &G.band_layer)) || (st = up(br0, &G.band_row0)) || (st = up(brs, &G.band_rows)) ||
             (st = up(bilo, &G.band_ilo)) || (st = up(bihi, &G.band_ihi)))
             return st;
         if ((st = alloc((size_t)P.n, &base.nodal)) || (st = alloc((size_t)P.n, &base.u)) ||
+            (st = alloc((size_t)P.n, &base.wq)) ||
             (st = alloc((size_t)P.G * P.m * P.m, &base.psi)) ||
             (st = alloc((size_t)kSlots * kMaxCtas, &base.part)) || (st = alloc((size_t)1, &base.rec)))
             return st;
         // launch geometry: dynamic shared memory = max over phases
         int nmax = 0;
         for (int l = 0; l < P.L; l++) nmax = std::max(nmax, P.geom.layers[l].n);
-        size_t sm_layer = (size_t)nmax * nmax * sizeof(T);
+        size_t sm_layer = (size_t)nmax * (nmax + 1) * sizeof(T);  // pitch n + 1
+        G.pingpong = sizeof(T) == 4 ? 1 : 0;  // FP32: second buffer for out-of-place DWT passes
+        if (G.pingpong) sm_layer *= 2;
         int H = tile + 2, SB = tile + 1;
         size_t sm_wfs = ((size_t)P.L * H * H + 2 * SB * SB) * sizeof(T);
         smem = std::max(sm_layer, sm_wfs);
         // band_gather stages rows_chunk psi rows and their x-contraction
+        // (all guide stars of a band at once when they fit, else in groups)
         const size_t row_bytes = (size_t)(P.m + nmax) * sizeof(T);
-        const size_t smem_cap = 227 * 1024;
-        size_t want = (size_t)max_rows * row_bytes;
+        const size_t smem_cap = 200 * 1024;  // 227 KB per CTA minus the static shared memory
+        size_t want = (size_t)max_rows_sum * row_bytes;
         if (want > smem) smem = std::min(want, smem_cap);
-        G.rows_chunk = (int)std::max<size_t>(1, std::min<size_t>(max_rows, smem / row_bytes));
-        if (smem > smem_cap) return FEWHA_ERR_GEOMETRY;
+        G.rows_chunk = (int)std::min<size_t>(max_rows_sum, smem / row_bytes);
+        if (smem > smem_cap || G.rows_chunk < max_rows) return FEWHA_ERR_GEOMETRY;
         int dev, nsm;
         CK(cudaGetDevice(&dev));
         CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
@@ -360,7 +419,8 @@ struct Impl : ImplBase {
         CK(setattr((const void *)k_fdwt<T, S, true>));
         CK(setattr((const void *)k_rhs_wfs<T, S>));
         CK(setattr((const void *)k_rhs_fdwt<T, S>));
-        CK(setattr((const void *)k_gram<T, S>));
+        CK(setattr((const void *)k_rhs_gather<T, S>));
+        CK(setattr((const void *)k_ptr<T, S>));
         CK(setattr((const void *)k_init<T, S>));
         CK(setattr((const void *)k_A<T, S>));
         CK(setattr((const void *)k_B<T, S>));
@@ -377,6 +437,7 @@ struct Impl : ImplBase {
         if (ncta > kMaxCtas) ncta = kMaxCtas;
         base.timeout_ns = 1000000000ull;
         base.ncta = ncta;
+        base.smem_bytes = smem;
         return FEWHA_OK;
     }
 
@@ -393,6 +454,12 @@ struct Impl : ImplBase {
         std::vector<T> v(invJ.begin(), invJ.end());
         CK(cudaMemcpy(const_cast<T *>(base.geo.invJ), v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
         return FEWHA_OK;
+    }
+
+    void set_trace(unsigned long long *buf, int cap) override
+    {
+        base.trace = buf;
+        base.trace_cap = buf ? cap : 0;
     }
 
     int launch_check() { return cudaGetLastError() == cudaSuccess ? FEWHA_OK : FEWHA_ERR_CUDA; }
@@ -442,6 +509,7 @@ struct Impl : ImplBase {
         A.stats = stats;
         CK(cudaMemsetAsync(A.rec, 0, offsetof(Record, rz), s));
         CK(cudaMemsetAsync(&A.rec->bar, 0, sizeof(Bar), s));
+        if (A.trace) CK(cudaMemsetAsync(A.trace, 0, (size_t)A.trace_cap * 4 * sizeof(unsigned long long), s));
         if (o->launch_mode == FEWHA_LAUNCH_PERSISTENT) {
             cudaLaunchConfig_t cfg = {};
             cfg.gridDim = dim3(ncta);
@@ -457,9 +525,9 @@ struct Impl : ImplBase {
             return launch_check();
         }
         k_rhs_wfs<T, S><<<ncta, kThreads, smem, s>>>(A);
-        k_gather<T, S><<<ncta, kThreads, smem, s>>>(A);
+        k_rhs_gather<T, S><<<ncta, kThreads, smem, s>>>(A);
         k_rhs_fdwt<T, S><<<ncta, kThreads, smem, s>>>(A);
-        k_gram<T, S><<<ncta, kThreads, smem, s>>>(A);
+        k_ptr<T, S><<<ncta, kThreads, smem, s>>>(A);
         k_init<T, S><<<ncta, kThreads, smem, s>>>(A);
         for (int k = 0; k < A.max_iter; k++) {
             k_A<T, S><<<ncta, kThreads, smem, s>>>(A, k);

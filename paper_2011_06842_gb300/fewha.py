@@ -92,6 +92,8 @@ def load_library(path=LIB_PATH):
     lib.fewha_apply_op.argtypes = [vp, vp, vp, vp]
     lib.fewha_rhs.argtypes = [vp, vp, vp, vp]
     lib.fewha_solve.argtypes = [vp, vp, vp, C.POINTER(STATE), C.POINTER(OPTS), vp, vp]
+    lib.fewha_set_trace.argtypes = [vp, vp, C.c_int]
+    lib.fewha_set_trace.restype = C.c_int
     lib.fewha_strerror.argtypes = [C.c_int]
     lib.fewha_strerror.restype = C.c_char_p
     for name in ("fewha_create", "fewha_get_prior", "fewha_get_precond", "fewha_apply_op",
@@ -105,7 +107,7 @@ def exported_symbols():
     """Entry points declared in include/fewha.h."""
     return ["fewha_create", "fewha_destroy", "fewha_n_unknowns", "fewha_n_slopes",
             "fewha_layer_spacing", "fewha_get_prior", "fewha_get_precond", "fewha_apply_op",
-            "fewha_rhs", "fewha_solve", "fewha_strerror"]
+            "fewha_rhs", "fewha_solve", "fewha_set_trace", "fewha_strerror"]
 
 
 def make_geometry(geom, noise_w, precision="f64", tile=0, grid=0) -> GEOMETRY:
@@ -250,6 +252,35 @@ class Fewha:
                                          C.byref(o), C.c_void_p(stats.data_ptr()),
                                          _stream_ptr(self._torch)), "fewha_solve")
         return stats
+
+    TRACE_TAGS = {1: "R1 wfs(rhs)", 2: "R2 gather(rhs)", 3: "R3 fdwt(rhs)", 4: "gram", 5: "init",
+                  11: "A update+idwt", 12: "B wfs", 13: "C gather", 14: "D fdwt", 15: "E axpy"}
+
+    def set_trace(self, buf):
+        """Enables the phase trace into a CUDA uint64/int64 tensor of shape (cap, 4), or None."""
+        if buf is None:
+            self._check(self.lib.fewha_set_trace(self._h, None, 0), "fewha_set_trace")
+            self._trace = None
+            return
+        self._check(self.lib.fewha_set_trace(self._h, C.c_void_p(buf.data_ptr()), buf.shape[0]),
+                    "fewha_set_trace")
+        self._trace = buf
+
+    def read_trace(self):
+        """Per-phase (tag, span_ns, barrier_ns, max_cta_ns) of the last traced solve
+        (synchronises): span from CTA 0 leaving the previous barrier to the last
+        CTA arriving, barrier wait after that, and the longest single-CTA phase."""
+        t = self._trace.cpu().numpy().astype("int64")
+        out = []
+        prev = None
+        for i in range(t.shape[0]):
+            maxcta, end, passed, tag = t[i, 0], t[i, 1], t[i, 2], t[i, 3]
+            if passed == 0:
+                break
+            span = int(end - prev) if prev is not None else 0
+            out.append((self.TRACE_TAGS.get(int(tag), str(tag)), span, int(passed - end), int(maxcta)))
+            prev = passed
+        return out
 
     @staticmethod
     def read_stats(stats):
