@@ -75,7 +75,8 @@ struct Geo {
     T inv_delta[FEWHA_MAX_LAYERS];
     int n_taps;
     T h[kMaxT], g[kMaxT];
-    int tile, tiles_x;          // WFS tiles: tile x tile output nodes, tiles_x per axis
+    int tile_y, tile_x;         // WFS tiles: tile_y x tile_x output nodes
+    int tiles_y, tiles_x;       // tiles per axis
     const int *fk, *alo, *ahi;  // interpolation tables
     const T *fw;
     const T *wmask;             // [G][ns*ns] weight on lit subapertures, 0 elsewhere
@@ -406,6 +407,27 @@ __device__ __forceinline__ void set_status(Record *rec, int st)
 
 // Grid barrier with a time limit.  Returns false (and the CTA must return)
 // when any CTA has recorded an error or the wait ran past timeout_ns.
+__device__ __forceinline__ unsigned int atom_add_release_gpu(unsigned int *p, unsigned int v)
+{
+    unsigned int r;
+    asm volatile("atom.add.release.gpu.u32 %0, [%1], %2;" : "=r"(r) : "l"(p), "r"(v) : "memory");
+    return r;
+}
+__device__ __forceinline__ unsigned int ld_acquire_gpu(const unsigned int *p)
+{
+    unsigned int r;
+    asm volatile("ld.acquire.gpu.u32 %0, [%1];" : "=r"(r) : "l"(p) : "memory");
+    return r;
+}
+__device__ __forceinline__ void st_release_gpu(unsigned int *p, unsigned int v)
+{
+    asm volatile("st.release.gpu.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Grid barrier with a time limit (sense by generation counter).  Thread 0
+// arrives with a release add after the block barrier (publishing the CTA's
+// writes) and waits with acquire loads.  Returns false (and the CTA must
+// return) when any CTA has recorded an error or the wait ran past timeout_ns.
 __device__ inline bool grid_sync(Record *rec, unsigned long long timeout_ns,
                                  unsigned long long *trace_slot = nullptr)
 {
@@ -419,18 +441,15 @@ __device__ inline bool grid_sync(Record *rec, unsigned long long timeout_ns,
             atomicMax(trace_slot + 1, now);
             if (t_pass) atomicMax(trace_slot, now - t_pass);
         }
-        volatile unsigned int *vgen = &rec->bar.gen;
         volatile int *vst = &rec->status;
-        unsigned int g = *vgen;
-        __threadfence();
-        unsigned int prev = atomicAdd(&rec->bar.count, 1u);
+        const unsigned int g = ld_acquire_gpu(&rec->bar.gen);
+        const unsigned int prev = atom_add_release_gpu(&rec->bar.count, 1u);
         if (prev == gridDim.x - 1) {
-            atomicExch(&rec->bar.count, 0u);
-            __threadfence();
-            atomicAdd(&rec->bar.gen, 1u);
+            rec->bar.count = 0;  // ordered before the release of the new generation
+            st_release_gpu(&rec->bar.gen, g + 1);
         } else {
-            unsigned long long t0 = gtimer();
-            while (*vgen == g) {
+            const unsigned long long t0 = gtimer();
+            while (ld_acquire_gpu(&rec->bar.gen) == g) {
                 if (*vst != 0) {
                     ok = 0;
                     break;
@@ -442,7 +461,6 @@ __device__ inline bool grid_sync(Record *rec, unsigned long long timeout_ns,
                 }
             }
         }
-        __threadfence();
         if (*vst != 0) ok = 0;
         if (trace_slot && blockIdx.x == 0) trace_slot[2] = gtimer();
         t_pass = trace_slot ? gtimer() : 0ull;
@@ -683,20 +701,21 @@ __device__ __noinline__ typename AccT<T>::type wfs_phase(const Args<T, S> &A, T 
 {
     typedef typename AccT<T>::type Acc;
     const Geo<T> &G = A.geo;
-    const int TS = G.tile, H = TS + 2, SB = TS + 1, m = G.m, ns = G.ns;
-    const int per_g = G.tiles_x * G.tiles_x, total = G.G * per_g;
-    T *phi = sm;                         // [L][H*H] per-layer contributions (OP)
-    T *sx = sm + (size_t)G.L * H * H;    // [SB*SB]
-    T *sy = sx + SB * SB;
+    const int TY = G.tile_y, TX = G.tile_x, HY = TY + 2, HX = TX + 2, SY = TY + 1, SX = TX + 1;
+    const int m = G.m, ns = G.ns;
+    const int per_g = G.tiles_y * G.tiles_x, total = G.G * per_g;
+    T *phi = sm;                          // [L][HY*HX] per-layer contributions (OP)
+    T *sx = sm + (size_t)G.L * HY * HX;   // [SY*SX]
+    T *sy = sx + SY * SX;
     Acc ws = 0;
     for (int w = blockIdx.x; w < total; w += gridDim.x) {
         const int g = w / per_g, tt = w - g * per_g;
-        const int i0 = (tt / G.tiles_x) * TS, j0 = (tt % G.tiles_x) * TS;
+        const int i0 = (tt / G.tiles_x) * TY, j0 = (tt % G.tiles_x) * TX;
         if (!RHS) {
             // per (layer, halo node) bilinear value
-            for (int e = threadIdx.x; e < G.L * H * H; e += blockDim.x) {
-                const int l = e / (H * H), loc = e - l * H * H;
-                const int i = i0 - 1 + loc / H, j = j0 - 1 + loc % H;
+            for (int e = threadIdx.x; e < G.L * HY * HX; e += blockDim.x) {
+                const int l = e / (HY * HX), loc = e - l * HY * HX;
+                const int i = i0 - 1 + loc / HX, j = j0 - 1 + loc % HX;
                 T v = 0;
                 if (i >= 0 && i < m && j >= 0 && j < m) {
                     const int bx = ((g * G.L + l) * 2 + 0) * m, by = ((g * G.L + l) * 2 + 1) * m;
@@ -711,16 +730,16 @@ __device__ __noinline__ typename AccT<T>::type wfs_phase(const Args<T, S> &A, T 
                 phi[e] = v;
             }
             __syncthreads();
-            for (int loc = threadIdx.x; loc < H * H; loc += blockDim.x) {
+            for (int loc = threadIdx.x; loc < HY * HX; loc += blockDim.x) {
                 T s = 0;
-                for (int l = 0; l < G.L; l++) s += phi[l * H * H + loc];
+                for (int l = 0; l < G.L; l++) s += phi[l * HY * HX + loc];
                 phi[loc] = s;
             }
             __syncthreads();
         }
-        // weighted slopes of subapertures (i0-1 .. i0+TS-1) x (j0-1 .. j0+TS-1)
-        for (int e = threadIdx.x; e < SB * SB; e += blockDim.x) {
-            const int a = e / SB, b = e - a * SB;
+        // weighted slopes of subapertures (i0-1 .. i0+TY-1) x (j0-1 .. j0+TX-1)
+        for (int e = threadIdx.x; e < SY * SX; e += blockDim.x) {
+            const int a = e / SX, b = e - a * SX;
             const int i = i0 - 1 + a, j = j0 - 1 + b;
             T vx = 0, vy = 0;
             if (i >= 0 && i < ns && j >= 0 && j < ns) {
@@ -730,8 +749,8 @@ __device__ __noinline__ typename AccT<T>::type wfs_phase(const Args<T, S> &A, T 
                     vx = wgt * Cv<S>::ld(sg[i * ns + j]);
                     vy = wgt * Cv<S>::ld(sg[ns * ns + i * ns + j]);
                 } else {
-                    const T p00 = phi[a * H + b], p01 = phi[a * H + b + 1];
-                    const T p10 = phi[(a + 1) * H + b], p11 = phi[(a + 1) * H + b + 1];
+                    const T p00 = phi[a * HX + b], p01 = phi[a * HX + b + 1];
+                    const T p10 = phi[(a + 1) * HX + b], p11 = phi[(a + 1) * HX + b + 1];
                     const T gx = T(0.5) * ((p01 - p00) + (p11 - p10));
                     const T gy = T(0.5) * ((p10 - p00) + (p11 - p01));
                     vx = wgt * gx;
@@ -744,13 +763,13 @@ __device__ __noinline__ typename AccT<T>::type wfs_phase(const Args<T, S> &A, T 
         }
         __syncthreads();
         // Gamma^T on the tile's own nodes
-        for (int e = threadIdx.x; e < TS * TS; e += blockDim.x) {
-            const int a = e / TS + 1, b = e % TS + 1;  // subaperture-local (i, j) of node (i0+a-1, j0+b-1)
+        for (int e = threadIdx.x; e < TY * TX; e += blockDim.x) {
+            const int a = e / TX + 1, b = e % TX + 1;  // subaperture-local (i, j) of node (i0+a-1, j0+b-1)
             const int i = i0 + a - 1, j = j0 + b - 1;
             if (i < m && j < m) {
-                const T v = T(0.5) * (sx[a * SB + b - 1] - sx[a * SB + b] + sx[(a - 1) * SB + b - 1] -
-                                      sx[(a - 1) * SB + b] + sy[(a - 1) * SB + b] - sy[a * SB + b] +
-                                      sy[(a - 1) * SB + b - 1] - sy[a * SB + b - 1]);
+                const T v = T(0.5) * (sx[a * SX + b - 1] - sx[a * SX + b] + sx[(a - 1) * SX + b - 1] -
+                                      sx[(a - 1) * SX + b] + sy[(a - 1) * SX + b] - sy[a * SX + b] +
+                                      sy[(a - 1) * SX + b - 1] - sy[a * SX + b - 1]);
                 A.psi[(size_t)g * m * m + i * m + j] = Cv<S>::st(v);
             }
         }

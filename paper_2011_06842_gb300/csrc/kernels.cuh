@@ -311,9 +311,31 @@ struct Impl : ImplBase {
             G.h[t] = t < G.n_taps ? (T)P.taps[t] : T(0);
             G.g[t] = t < G.n_taps ? (T)(((t & 1) ? -1.0 : 1.0) * P.taps[G.n_taps - 1 - t]) : T(0);
         }
-        int tile = P.geom.tile ? P.geom.tile : 16;
-        G.tile = tile;
-        G.tiles_x = (P.m + tile - 1) / tile;
+        // WFS tiles: a square tile if the caller fixed one, else the shape
+        // (8..32 nodes per side) whose work per round of CTAs is least
+        {
+            int dev0, nsm0;
+            CK(cudaGetDevice(&dev0));
+            CK(cudaDeviceGetAttribute(&nsm0, cudaDevAttrMultiProcessorCount, dev0));
+            const int ctas = grid > 0 ? grid : nsm0;
+            double best = 1e300;
+            const int cand[4] = {8, 16, 24, 32};
+            for (int a = 0; a < 4; a++)
+                for (int c = 0; c < 4; c++) {
+                    int ty = cand[a], tx = cand[c];
+                    if (P.geom.tile) ty = tx = P.geom.tile;
+                    const int tiles = P.G * ((P.m + ty - 1) / ty) * ((P.m + tx - 1) / tx);
+                    const int rounds = (tiles + ctas - 1) / ctas;
+                    const double cost = rounds * ((double)(ty + 2) * (tx + 2) + 64.0);
+                    if (cost < best - 1e-9) {
+                        best = cost;
+                        G.tile_y = ty;
+                        G.tile_x = tx;
+                    }
+                }
+            G.tiles_y = (P.m + G.tile_y - 1) / G.tile_y;
+            G.tiles_x = (P.m + G.tile_x - 1) / G.tile_x;
+        }
         int st;
         if ((st = up(P.fk, &G.fk)) || (st = up(P.alo, &G.alo)) || (st = up(P.ahi, &G.ahi))) return st;
         std::vector<T> fw(P.fw.begin(), P.fw.end());
@@ -332,7 +354,7 @@ struct Impl : ImplBase {
             int n = P.geom.layers[l].n, lg = 0;
             while ((1 << lg) < n) lg++;
             G.lay_lg[l] = lg;
-            int BR = std::max(1, std::min(n, kThreads / n));
+            int BR = std::max(1, std::min(n, std::min(kThreads / n, 8)));  // 8 rows: balanced work items
             for (int a0 = 0; a0 < n; a0 += BR) {
                 bl.push_back(l);
                 br0.push_back(a0);
@@ -394,8 +416,7 @@ struct Impl : ImplBase {
         size_t sm_layer = (size_t)nmax * (nmax + 1) * sizeof(T);  // pitch n + 1
         G.pingpong = sizeof(T) == 4 ? 1 : 0;  // FP32: second buffer for out-of-place DWT passes
         if (G.pingpong) sm_layer *= 2;
-        int H = tile + 2, SB = tile + 1;
-        size_t sm_wfs = ((size_t)P.L * H * H + 2 * SB * SB) * sizeof(T);
+        size_t sm_wfs = ((size_t)P.L * (G.tile_y + 2) * (G.tile_x + 2) + 2 * (G.tile_y + 1) * (G.tile_x + 1)) * sizeof(T);
         smem = std::max(sm_layer, sm_wfs);
         // band_gather stages rows_chunk psi rows and their x-contraction
         // (all guide stars of a band at once when they fit, else in groups)
