@@ -56,7 +56,8 @@ enum {
     FEWHA_ERR_TIMEOUT = -4,   /* a device-side wait gave up (grid barrier) */
     FEWHA_ERR_BREAKDOWN = -5, /* CG breakdown: (p, Mp) <= 0 or not finite */
     FEWHA_ERR_NOT_SPD = -6,   /* recycled Gram matrix not positive definite */
-    FEWHA_ERR_NOMEM = -7      /* device allocation failed */
+    FEWHA_ERR_NOMEM = -7,     /* device allocation failed */
+    FEWHA_ERR_SCRATCH = -8    /* problem too large for fewha_apply_op_noalloc's fixed scratch */
 };
 
 enum { FEWHA_F64 = 0, FEWHA_F32 = 1, FEWHA_BF16S = 2 };
@@ -173,6 +174,30 @@ int fewha_solve(void *handle, const void *s, void *c, const fewha_state *state,
  * passed the barrier, [4i+3] the phase tag.  Barriers
  * beyond the capacity are not recorded.  The paper has no counterpart. */
 int fewha_set_trace(void *handle, unsigned long long *trace_dev, int capacity);
+
+/* y = M x, like fewha_apply_op, but without allocating anything: no
+ * cudaMalloc, no cudaFree, no allocating library call, ever.  Meant for
+ * callers that cannot allocate device memory at the point where they apply
+ * the operator: a hard real-time control loop that must not stall on the
+ * allocator (an allocation can synchronise the device), code issuing work
+ * while a CUDA stream is being captured into a graph (allocation is not a
+ * stream operation), and plug-ins whose host application owns every device
+ * allocation.  The handle itself is still created (and its constant tables
+ * allocated) once, beforehand, by fewha_create.
+ * The intermediate buffers live in one statically reserved device array of
+ * FEWHA_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds until
+ * the process exits.  Problems whose buffers do not fit are rejected with
+ * FEWHA_ERR_SCRATCH (an ELT-size FP64 operator, n = 98304 with 6 sensors of
+ * 84 x 84 subapertures, needs about 4.8 MB).
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls share the one array, which keeps the
+ * last call's contents: calls that overlap on the GPU (different streams,
+ * different handles on the same device) race and must be ordered by the
+ * caller.  The paper has no counterpart; this is a deployment aid.
+ * x, y: device vectors of length n, 16-byte aligned, not overlapping. */
+#define FEWHA_NOALLOC_SCRATCH_BYTES (8u << 20)
+int fewha_apply_op_noalloc(void *handle, const void *x, void *y, cudaStream_t stream);
 
 /* Text of a status code. */
 const char *fewha_strerror(int status);

@@ -20,6 +20,8 @@ struct Handle {
     ImplBase *w() { return work ? work.get() : f64.get(); }
 };
 
+ImplBase *handle_impl(void *handle) { return handle ? static_cast<Handle *>(handle)->w() : nullptr; }
+
 // Modified Jacobi preconditioner (Sec. 4): J = alpha D + t_band, with t_band
 // the mean over sampled coefficients of the data term's diagonal
 // e_i^T M e_i - alpha D_ii, computed with the FP64 operator.
@@ -192,6 +194,7 @@ const char *fewha_strerror(int status)
     case FEWHA_ERR_BREAKDOWN: return "CG breakdown ((p, Mp) <= 0 or not finite)";
     case FEWHA_ERR_NOT_SPD: return "recycled Gram matrix not positive definite";
     case FEWHA_ERR_NOMEM: return "device allocation failed";
+    case FEWHA_ERR_SCRATCH: return "problem too large for the fixed scratch of the allocation-free entry point";
     default: return "unknown status";
     }
 }

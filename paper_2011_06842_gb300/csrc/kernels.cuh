@@ -257,6 +257,9 @@ struct ImplBase {
                       fewha_stats *stats, cudaStream_t s) = 0;
     virtual int set_invJ(const std::vector<double> &invJ) = 0;
     virtual void set_trace(unsigned long long *buf, int cap) = 0;
+    // y = M x with every scratch buffer carved from caller-provided device
+    // memory (no allocation); FEWHA_ERR_SCRATCH if `bytes` is too small.
+    virtual int apply_in_scratch(const void *x, void *y, void *scratch, size_t bytes, cudaStream_t s) = 0;
 };
 
 template <typename T, typename S>
@@ -498,6 +501,38 @@ struct Impl : ImplBase {
         return launch_check();
     }
 
+    int apply_in_scratch(const void *x, void *y, void *scratch, size_t bytes, cudaStream_t s) override
+    {
+        // layout: record | partial sums | nodal layers | adjoint wavefronts | P^T output
+        auto up256 = [](size_t v) { return (v + 255) & ~(size_t)255; };
+        const size_t o_rec = 0;
+        const size_t o_part = up256(o_rec + sizeof(Record));
+        const size_t o_nodal = up256(o_part + (size_t)kSlots * kMaxCtas * sizeof(double));
+        const size_t o_psi = up256(o_nodal + (size_t)P.n * sizeof(S));
+        const size_t o_u = up256(o_psi + (size_t)P.G * P.m * P.m * sizeof(S));
+        const size_t need = up256(o_u + (size_t)P.n * sizeof(T));
+        if (need > bytes) return FEWHA_ERR_SCRATCH;
+        unsigned char *base_p = static_cast<unsigned char *>(scratch);
+        Args<T, S> A = base;
+        A.rec = reinterpret_cast<Record *>(base_p + o_rec);
+        A.part = reinterpret_cast<double *>(base_p + o_part);
+        A.nodal = reinterpret_cast<S *>(base_p + o_nodal);
+        A.psi = reinterpret_cast<S *>(base_p + o_psi);
+        A.u = reinterpret_cast<T *>(base_p + o_u);
+        A.trace = nullptr;
+        A.trace_cap = 0;
+        A.x = static_cast<const T *>(x);
+        A.y = static_cast<T *>(y);
+        // the record's flags must start at zero; the other buffers are fully
+        // overwritten before they are read
+        CK(cudaMemsetAsync(A.rec, 0, offsetof(Record, rz), s));
+        k_apply_idwt<T, S><<<ncta, kThreads, smem, s>>>(A);
+        k_wfs<T, S, false><<<ncta, kThreads, smem, s>>>(A);
+        k_gather<T, S><<<ncta, kThreads, smem, s>>>(A);
+        k_fdwt<T, S, false><<<ncta, kThreads, smem, s>>>(A);
+        return launch_check();
+    }
+
     int rhs(const void *sl, void *b, cudaStream_t s) override
     {
         Args<T, S> A = base;
@@ -564,6 +599,8 @@ struct Impl : ImplBase {
 
 
 ImplBase *make_impl_f64(const Plan &p);
+// Working-precision implementation of a handle (defined with the C ABI).
+ImplBase *handle_impl(void *handle);
 ImplBase *make_impl_f32(const Plan &p);
 ImplBase *make_impl_bf16(const Plan &p);
 

@@ -21,7 +21,7 @@ PRECISIONS = {"f64": F64, "f32": F32, "bf16s": BF16S}
 
 ERRORS = {0: "ok", -1: "FEWHA_ERR_ARG", -2: "FEWHA_ERR_GEOMETRY", -3: "FEWHA_ERR_CUDA",
           -4: "FEWHA_ERR_TIMEOUT", -5: "FEWHA_ERR_BREAKDOWN", -6: "FEWHA_ERR_NOT_SPD",
-          -7: "FEWHA_ERR_NOMEM"}
+          -7: "FEWHA_ERR_NOMEM", -8: "FEWHA_ERR_SCRATCH"}
 
 
 class FewhaError(RuntimeError):
@@ -92,6 +92,8 @@ def load_library(path=LIB_PATH):
     lib.fewha_apply_op.argtypes = [vp, vp, vp, vp]
     lib.fewha_rhs.argtypes = [vp, vp, vp, vp]
     lib.fewha_solve.argtypes = [vp, vp, vp, C.POINTER(STATE), C.POINTER(OPTS), vp, vp]
+    lib.fewha_apply_op_noalloc.argtypes = [vp, vp, vp, vp]
+    lib.fewha_apply_op_noalloc.restype = C.c_int
     lib.fewha_set_trace.argtypes = [vp, vp, C.c_int]
     lib.fewha_set_trace.restype = C.c_int
     lib.fewha_strerror.argtypes = [C.c_int]
@@ -107,7 +109,7 @@ def exported_symbols():
     """Entry points declared in include/fewha.h."""
     return ["fewha_create", "fewha_destroy", "fewha_n_unknowns", "fewha_n_slopes",
             "fewha_layer_spacing", "fewha_get_prior", "fewha_get_precond", "fewha_apply_op",
-            "fewha_rhs", "fewha_solve", "fewha_set_trace", "fewha_strerror"]
+            "fewha_rhs", "fewha_solve", "fewha_set_trace", "fewha_apply_op_noalloc", "fewha_strerror"]
 
 
 def make_geometry(geom, noise_w, precision="f64", tile=0, grid=0) -> GEOMETRY:
@@ -224,6 +226,16 @@ class Fewha:
         self._check(self.lib.fewha_apply_op(self._h, self._vec(x, self.n, self.dtype, "x"),
                                             self._vec(y, self.n, self.dtype, "y"),
                                             _stream_ptr(self._torch)), "fewha_apply_op")
+        return y
+
+    def apply_op_noalloc(self, x, out=None):
+        """y = M x through fewha_apply_op_noalloc: the library allocates
+        nothing (its intermediates live in a statically reserved device array
+        shared by all calls).  `out` lets the caller bring its own output."""
+        y = out if out is not None else self._torch.empty(self.n, dtype=self.dtype, device=self.device)
+        self._check(self.lib.fewha_apply_op_noalloc(self._h, self._vec(x, self.n, self.dtype, "x"),
+                                                    self._vec(y, self.n, self.dtype, "y"),
+                                                    _stream_ptr(self._torch)), "fewha_apply_op_noalloc")
         return y
 
     def rhs(self, s, out=None):
