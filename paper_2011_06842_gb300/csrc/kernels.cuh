@@ -315,18 +315,24 @@ struct Impl : ImplBase {
             G.g[t] = t < G.n_taps ? (T)(((t & 1) ? -1.0 : 1.0) * P.taps[G.n_taps - 1 - t]) : T(0);
         }
         // WFS tiles: a square tile if the caller fixed one, else the shape
-        // (8..32 nodes per side) whose work per round of CTAs is least
+        // (8..32 nodes per side) whose work per round of CTAs is least among
+        // those whose shared memory fits
+        auto wfs_smem = [&](int ty, int tx) -> size_t {
+            return ((size_t)P.L * (ty + 2) * (tx + 2) + 2 * (size_t)(ty + 1) * (tx + 1)) * sizeof(T);
+        };
         {
             int dev0, nsm0;
             CK(cudaGetDevice(&dev0));
             CK(cudaDeviceGetAttribute(&nsm0, cudaDevAttrMultiProcessorCount, dev0));
             const int ctas = grid > 0 ? grid : nsm0;
             double best = 1e300;
+            G.tile_y = G.tile_x = 0;
             const int cand[4] = {8, 16, 24, 32};
             for (int a = 0; a < 4; a++)
                 for (int c = 0; c < 4; c++) {
                     int ty = cand[a], tx = cand[c];
                     if (P.geom.tile) ty = tx = P.geom.tile;
+                    if (wfs_smem(ty, tx) > 200 * 1024) continue;
                     const int tiles = P.G * ((P.m + ty - 1) / ty) * ((P.m + tx - 1) / tx);
                     const int rounds = (tiles + ctas - 1) / ctas;
                     const double cost = rounds * ((double)(ty + 2) * (tx + 2) + 64.0);
@@ -336,6 +342,7 @@ struct Impl : ImplBase {
                         G.tile_x = tx;
                     }
                 }
+            if (!G.tile_y) return FEWHA_ERR_GEOMETRY;
             G.tiles_y = (P.m + G.tile_y - 1) / G.tile_y;
             G.tiles_x = (P.m + G.tile_x - 1) / G.tile_x;
         }
@@ -419,7 +426,7 @@ struct Impl : ImplBase {
         size_t sm_layer = (size_t)nmax * (nmax + 1) * sizeof(T);  // pitch n + 1
         G.pingpong = sizeof(T) == 4 ? 1 : 0;  // FP32: second buffer for out-of-place DWT passes
         if (G.pingpong) sm_layer *= 2;
-        size_t sm_wfs = ((size_t)P.L * (G.tile_y + 2) * (G.tile_x + 2) + 2 * (G.tile_y + 1) * (G.tile_x + 1)) * sizeof(T);
+        const size_t sm_wfs = wfs_smem(G.tile_y, G.tile_x);
         smem = std::max(sm_layer, sm_wfs);
         // band_gather stages rows_chunk psi rows and their x-contraction
         // (all guide stars of a band at once when they fit, else in groups)
