@@ -165,6 +165,13 @@ int fewha_rhs(void *handle, const void *s, void *b, cudaStream_t stream);
 int fewha_solve(void *handle, const void *s, void *c, const fewha_state *state,
                 const fewha_solve_opts *opts, fewha_stats *stats_dev, cudaStream_t stream);
 
+/* Time limit of every device-side wait of the persistent solver (grid
+ * barriers), in ns; default 1 s.  A wait that runs out records
+ * FEWHA_ERR_TIMEOUT in fewha_stats.status and every CTA returns; the context
+ * stays usable.  0 makes any wait time out at once (used to test the error
+ * path).  The paper has no counterpart. */
+int fewha_set_timeout(void *handle, unsigned long long timeout_ns);
+
 /* Phase trace of the persistent solver (profiling aid).  trace_dev: device
  * buffer of capacity x 4 unsigned 64-bit words, owned by the caller, or NULL
  * to switch tracing off.  Each following fewha_solve (persistent launch)

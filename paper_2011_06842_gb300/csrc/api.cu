@@ -176,6 +176,13 @@ int fewha_solve(void *handle, const void *s, void *c, const fewha_state *st, con
     return static_cast<Handle *>(handle)->w()->solve(s, c, st, o, stats, stream);
 }
 
+int fewha_set_timeout(void *handle, unsigned long long timeout_ns)
+{
+    if (!handle) return FEWHA_ERR_ARG;
+    static_cast<Handle *>(handle)->w()->set_timeout(timeout_ns);
+    return FEWHA_OK;
+}
+
 int fewha_set_trace(void *handle, unsigned long long *trace_dev, int capacity)
 {
     if (!handle || (trace_dev && capacity < 1)) return FEWHA_ERR_ARG;

@@ -257,6 +257,7 @@ struct ImplBase {
                       fewha_stats *stats, cudaStream_t s) = 0;
     virtual int set_invJ(const std::vector<double> &invJ) = 0;
     virtual void set_trace(unsigned long long *buf, int cap) = 0;
+    virtual void set_timeout(unsigned long long ns) = 0;
     // y = M x with every scratch buffer carved from caller-provided device
     // memory (no allocation); FEWHA_ERR_SCRATCH if `bytes` is too small.
     virtual int apply_in_scratch(const void *x, void *y, void *scratch, size_t bytes, cudaStream_t s) = 0;
@@ -486,6 +487,8 @@ struct Impl : ImplBase {
         CK(cudaMemcpy(const_cast<T *>(base.geo.invJ), v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
         return FEWHA_OK;
     }
+
+    void set_timeout(unsigned long long ns) override { base.timeout_ns = ns; }
 
     void set_trace(unsigned long long *buf, int cap) override
     {

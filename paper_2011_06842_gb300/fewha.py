@@ -94,6 +94,8 @@ def load_library(path=LIB_PATH):
     lib.fewha_solve.argtypes = [vp, vp, vp, C.POINTER(STATE), C.POINTER(OPTS), vp, vp]
     lib.fewha_apply_op_noalloc.argtypes = [vp, vp, vp, vp]
     lib.fewha_apply_op_noalloc.restype = C.c_int
+    lib.fewha_set_timeout.argtypes = [vp, C.c_ulonglong]
+    lib.fewha_set_timeout.restype = C.c_int
     lib.fewha_set_trace.argtypes = [vp, vp, C.c_int]
     lib.fewha_set_trace.restype = C.c_int
     lib.fewha_strerror.argtypes = [C.c_int]
@@ -109,7 +111,7 @@ def exported_symbols():
     """Entry points declared in include/fewha.h."""
     return ["fewha_create", "fewha_destroy", "fewha_n_unknowns", "fewha_n_slopes",
             "fewha_layer_spacing", "fewha_get_prior", "fewha_get_precond", "fewha_apply_op",
-            "fewha_rhs", "fewha_solve", "fewha_set_trace", "fewha_apply_op_noalloc", "fewha_strerror"]
+            "fewha_rhs", "fewha_solve", "fewha_set_timeout", "fewha_set_trace", "fewha_apply_op_noalloc", "fewha_strerror"]
 
 
 def make_geometry(geom, noise_w, precision="f64", tile=0, grid=0) -> GEOMETRY:
@@ -264,6 +266,10 @@ class Fewha:
                                          C.byref(o), C.c_void_p(stats.data_ptr()),
                                          _stream_ptr(self._torch)), "fewha_solve")
         return stats
+
+    def set_timeout(self, ns):
+        """Time limit of the solver's device-side waits (ns)."""
+        self._check(self.lib.fewha_set_timeout(self._h, int(ns)), "fewha_set_timeout")
 
     TRACE_TAGS = {1: "R1 wfs(rhs)", 2: "R2 gather(rhs)", 3: "R3 fdwt(rhs)", 4: "gram", 5: "init",
                   11: "A update+idwt", 12: "B wfs", 13: "C gather", 14: "D fdwt", 15: "E axpy"}
