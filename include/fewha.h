@@ -165,6 +165,25 @@ int fewha_rhs(void *handle, const void *s, void *b, cudaStream_t stream);
 int fewha_solve(void *handle, const void *s, void *c, const fewha_state *state,
                 const fewha_solve_opts *opts, fewha_stats *stats_dev, cudaStream_t stream);
 
+/* Batched time steps: n instances (handles of one precision, on the current
+ * device, geometries may differ) solved by ONE cooperative launch, each by its
+ * own group of CTAs with its own barrier, reductions and recycled basis.
+ * ctas: CTAs per instance (NULL: proportional to the work of one iteration,
+ * n_l^2 summed over layers plus G (n_s+1)^2, at least one each); the groups
+ * must fit the GPU at once (FEWHA_ERR_ARG otherwise).  The WFS tile shape of
+ * every instance is re-chosen for its group.  fewha_batch_solve takes one
+ * pointer per instance (slopes, c, state; stats_dev: n consecutive records)
+ * and the same options for all; it stages the launch arguments through a
+ * small ring of pinned host buffers, so it can be captured in a CUDA graph
+ * (the graph then replays the captured pointers).  Blocking only when all
+ * four staging buffers are still in flight.  Not in the paper: the paper
+ * solves one system per time step. */
+int fewha_batch_create(void *const *handles, int n, const int *ctas, void **batch_out);
+int fewha_batch_ctas(const void *batch, int *ctas_out);
+int fewha_batch_solve(void *batch, const void *const *slopes, void *const *c, const fewha_state *states,
+                      const fewha_solve_opts *opts, fewha_stats *stats_dev, cudaStream_t stream);
+void fewha_batch_destroy(void *batch);
+
 /* Time limit of every device-side wait of the persistent solver (grid
  * barriers), in ns; default 1 s.  A wait that runs out records
  * FEWHA_ERR_TIMEOUT in fewha_stats.status and every CTA returns; the context

@@ -3,6 +3,7 @@
 // scratch on the current device, and launches the kernels of one precision.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstring>
 #include <memory>
 #include <new>
@@ -20,7 +21,34 @@ struct Handle {
     ImplBase *w() { return work ? work.get() : f64.get(); }
 };
 
+// Vectors are accessed with 16-byte loads and stores.
+static bool aligned16(const void *p) { return ((size_t)p & 15) == 0; }
+
 ImplBase *handle_impl(void *handle) { return handle ? static_cast<Handle *>(handle)->w() : nullptr; }
+
+// A batch: many instances (handles of one precision on one device) run by one
+// cooperative launch, each by its own group of CTAs.
+struct Batch {
+    int n = 0, total = 0;
+    size_t smem = 0, asz = 0;
+    std::vector<ImplBase *> impl;
+    std::vector<int> cta0, ncta, ty, tx;
+    void *d_args = nullptr;
+    int *d_map = nullptr;
+    static constexpr int kRing = 4;  // pinned staging copies of the argument table
+    void *h_args[kRing] = {};
+    cudaEvent_t ev[kRing] = {};
+    int next = 0;
+    ~Batch()
+    {
+        cudaFree(d_args);
+        cudaFree(d_map);
+        for (int i = 0; i < kRing; i++) {
+            if (h_args[i]) cudaFreeHost(h_args[i]);
+            if (ev[i]) cudaEventDestroy(ev[i]);
+        }
+    }
+};
 
 // Modified Jacobi preconditioner (Sec. 4): J = alpha D + t_band, with t_band
 // the mean over sampled coefficients of the data term's diagonal
@@ -145,9 +173,6 @@ int fewha_get_precond(const void *handle, double *out)
     return h->work ? h->work->get_invJ(out) : h->f64->get_invJ(out);
 }
 
-// Vectors are accessed with 16-byte loads and stores.
-static bool aligned16(const void *p) { return ((size_t)p & 15) == 0; }
-
 int fewha_apply_op(void *handle, const void *x, void *y, cudaStream_t stream)
 {
     if (!handle || !x || !y || x == y || !aligned16(x) || !aligned16(y)) return FEWHA_ERR_ARG;
@@ -174,6 +199,121 @@ int fewha_solve(void *handle, const void *s, void *c, const fewha_state *st, con
     if (o->launch_mode != FEWHA_LAUNCH_PERSISTENT && o->launch_mode != FEWHA_LAUNCH_PHASES) return FEWHA_ERR_ARG;
     if (o->recycle_mode != FEWHA_RECYCLE_LAST && o->recycle_mode != FEWHA_RECYCLE_ALL) return FEWHA_ERR_ARG;
     return static_cast<Handle *>(handle)->w()->solve(s, c, st, o, stats, stream);
+}
+
+int fewha_batch_create(void *const *handles, int n, const int *ctas, void **batch_out)
+{
+    if (!handles || n < 1 || !batch_out) return FEWHA_ERR_ARG;
+    *batch_out = nullptr;
+    std::unique_ptr<Batch> b(new (std::nothrow) Batch());
+    if (!b) return FEWHA_ERR_NOMEM;
+    b->n = n;
+    int prec = -1;
+    std::vector<double> weight(n);
+    for (int i = 0; i < n; i++) {
+        if (!handles[i]) return FEWHA_ERR_ARG;
+        Handle *h = static_cast<Handle *>(handles[i]);
+        b->impl.push_back(h->w());
+        if (prec >= 0 && h->w()->precision_id() != prec) return FEWHA_ERR_ARG;
+        prec = h->w()->precision_id();
+        // work of one iteration ~ unknowns + adjoint wavefront nodes
+        weight[i] = (double)h->plan.n + (double)h->plan.G * h->plan.m * h->plan.m;
+    }
+    // CTA groups: given, or proportional to the work (at least one each)
+    int cap = 0;
+    int st = b->impl[0]->batch_capacity(200 * 1024, &cap);
+    if (st) return st;
+    b->ncta.assign(n, 1);
+    if (ctas) {
+        for (int i = 0; i < n; i++) {
+            if (ctas[i] < 1) return FEWHA_ERR_ARG;
+            b->ncta[i] = ctas[i];
+        }
+    } else {
+        if (n > cap) return FEWHA_ERR_ARG;
+        double wsum = 0;
+        for (double w : weight) wsum += w;
+        int used = 0;
+        for (int i = 0; i < n; i++) {
+            b->ncta[i] = std::max(1, (int)((cap - n) * weight[i] / wsum) + 1);
+            used += b->ncta[i];
+        }
+        while (used > cap) {  // trim the largest groups
+            int j = (int)(std::max_element(b->ncta.begin(), b->ncta.end()) - b->ncta.begin());
+            b->ncta[j]--;
+            used--;
+        }
+    }
+    b->cta0.resize(n);
+    b->ty.resize(n);
+    b->tx.resize(n);
+    b->total = 0;
+    for (int i = 0; i < n; i++) {
+        b->cta0[i] = b->total;
+        b->total += b->ncta[i];
+        if ((st = b->impl[i]->tiles_for(b->ncta[i], &b->ty[i], &b->tx[i]))) return st;
+        b->smem = std::max(b->smem, b->impl[i]->smem_for(b->ty[i], b->tx[i]));
+    }
+    if ((st = b->impl[0]->batch_capacity(b->smem, &cap))) return st;
+    if (b->total > cap) return FEWHA_ERR_ARG;  // the groups must be co-resident
+    b->asz = b->impl[0]->args_size();
+    std::vector<int> map(b->total);
+    for (int i = 0; i < n; i++)
+        for (int c = 0; c < b->ncta[i]; c++) map[b->cta0[i] + c] = i;
+    if (cudaMalloc(&b->d_args, b->asz * n) != cudaSuccess || cudaMalloc(&b->d_map, sizeof(int) * b->total) != cudaSuccess)
+        return FEWHA_ERR_NOMEM;
+    if (cudaMemcpy(b->d_map, map.data(), sizeof(int) * b->total, cudaMemcpyHostToDevice) != cudaSuccess)
+        return FEWHA_ERR_CUDA;
+    for (int i = 0; i < Batch::kRing; i++) {
+        if (cudaHostAlloc(&b->h_args[i], b->asz * n, cudaHostAllocDefault) != cudaSuccess) return FEWHA_ERR_NOMEM;
+        if (cudaEventCreateWithFlags(&b->ev[i], cudaEventDisableTiming) != cudaSuccess) return FEWHA_ERR_CUDA;
+    }
+    *batch_out = b.release();
+    return FEWHA_OK;
+}
+
+int fewha_batch_ctas(const void *batch, int *ctas_out)
+{
+    if (!batch || !ctas_out) return FEWHA_ERR_ARG;
+    const Batch *b = static_cast<const Batch *>(batch);
+    for (int i = 0; i < b->n; i++) ctas_out[i] = b->ncta[i];
+    return FEWHA_OK;
+}
+
+int fewha_batch_solve(void *batch, const void *const *slopes, void *const *c, const fewha_state *states,
+                      const fewha_solve_opts *opts, fewha_stats *stats_dev, cudaStream_t stream)
+{
+    if (!batch || !slopes || !c || !states || !opts) return FEWHA_ERR_ARG;
+    Batch *b = static_cast<Batch *>(batch);
+    if (opts->max_iter < 1 || opts->max_iter > FEWHA_MAX_ITER || !(opts->rtol >= 0)) return FEWHA_ERR_ARG;
+    if (opts->recycle_mode != FEWHA_RECYCLE_LAST && opts->recycle_mode != FEWHA_RECYCLE_ALL) return FEWHA_ERR_ARG;
+    const int slot = b->next;
+    b->next = (b->next + 1) % Batch::kRing;
+    if (cudaEventSynchronize(b->ev[slot]) != cudaSuccess) return FEWHA_ERR_CUDA;  // staging copy free again
+    unsigned char *h = static_cast<unsigned char *>(b->h_args[slot]);
+    for (int i = 0; i < b->n; i++) {
+        const fewha_state *st = states + i;
+        if (!slopes[i] || !c[i] || !st->b_prev || !st->r_prev || !st->basis_P || !st->basis_Q || !st->basis_pq ||
+            !st->meta || st->k_cap < 1 || st->k_cap > FEWHA_MAX_K)
+            return FEWHA_ERR_ARG;
+        if (!aligned16(c[i]) || !aligned16(st->b_prev) || !aligned16(st->r_prev) || !aligned16(st->basis_P) ||
+            !aligned16(st->basis_Q))
+            return FEWHA_ERR_ARG;
+        int r = b->impl[i]->batch_args(h + b->asz * i, slopes[i], c[i], st, opts, stats_dev ? stats_dev + i : nullptr,
+                                       b->cta0[i], b->ncta[i], b->ty[i], b->tx[i], b->smem);
+        if (r) return r;
+    }
+    if (cudaMemcpyAsync(b->d_args, h, b->asz * b->n, cudaMemcpyHostToDevice, stream) != cudaSuccess)
+        return FEWHA_ERR_CUDA;
+    if (cudaEventRecord(b->ev[slot], stream) != cudaSuccess) return FEWHA_ERR_CUDA;
+    return b->impl[0]->launch_batched(b->d_args, b->d_map, b->n, b->total, b->smem, stream);
+}
+
+void fewha_batch_destroy(void *batch)
+{
+    if (!batch) return;
+    cudaDeviceSynchronize();
+    delete static_cast<Batch *>(batch);
 }
 
 int fewha_set_timeout(void *handle, unsigned long long timeout_ns)

@@ -1,7 +1,9 @@
 // Device code of the FEWHA operator and the (augmented) PCG solver for sm_103a.
 //
 // Every step of the hot path is a "phase": a __device__ function that one CTA
-// runs over the work items it owns (w = blockIdx.x, blockIdx.x + gridDim.x, ...).
+// runs over the work items it owns (w = rank, rank + ncta, ...), where rank
+// and ncta are the CTA's place in the group running this instance (the whole
+// grid for one instance; a slice of it in the batched launch).
 // The same phases run either as one kernel each (FEWHA_LAUNCH_PHASES) or back
 // to back inside one persistent cooperative kernel separated by a bounded grid
 // barrier (FEWHA_LAUNCH_PERSISTENT).  Reductions are deterministic: each CTA
@@ -97,7 +99,7 @@ struct Geo {
 enum Mode { kApply = 0, kRhs = 1, kSolve = 2 };
 
 template <typename T, typename S>
-struct Args {
+struct __align__(16) Args {
     Geo<T> geo;
     // operator buffers
     S *nodal;        // [n]  W^{-1} p (layer nodal values)
@@ -119,8 +121,10 @@ struct Args {
     double *part;    // kSlots * kMaxCtas
     Record *rec;
     unsigned long long timeout_ns;
-    int ncta;        // CTAs that wrote partials (the solver grid)
+    int ncta;        // CTAs of the group running this instance
+    int cta0;        // first CTA of that group (0 for a single instance)
     size_t smem_bytes;  // dynamic shared memory of every launch
+    __device__ __forceinline__ int vrank() const { return (int)blockIdx.x - cta0; }
     unsigned long long *trace;  // optional phase trace [trace_cap][4]: start, last CTA done, barrier passed, tag
     int trace_cap;
     // derived per solve (host fills from nothing: phases read meta)
@@ -250,8 +254,8 @@ __device__ __forceinline__ A warp_sum_t(A v)
 
 // Block-wide sum of NV values per thread, written as partials of this CTA.
 template <int NV, typename A>
-__device__ void block_partials(A (&v)[NV], double *part, const int (&slot)[NV], double *sred)
-// sred: shared scratch of NV * 32 doubles
+__device__ void block_partials(A (&v)[NV], double *part, const int (&slot)[NV], double *sred, int cta)
+// sred: shared scratch of NV * 32 doubles; cta: this CTA's rank in its group
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
@@ -263,7 +267,7 @@ __device__ void block_partials(A (&v)[NV], double *part, const int (&slot)[NV], 
     for (int i = warp; i < NV; i += nw) {
         double s = lane < nw ? sred[i * 32 + lane] : 0.0;
         s = warp_sum(s);
-        if (lane == 0) part[(size_t)slot[i] * kMaxCtas + blockIdx.x] = s;
+        if (lane == 0) part[(size_t)slot[i] * kMaxCtas + cta] = s;
     }
     __syncthreads();
 }
@@ -424,11 +428,11 @@ __device__ __forceinline__ void st_release_gpu(unsigned int *p, unsigned int v)
     asm volatile("st.release.gpu.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// Grid barrier with a time limit (sense by generation counter).  Thread 0
+// Barrier over the nctas CTAs of a group, with a time limit (generation counter).  Thread 0
 // arrives with a release add after the block barrier (publishing the CTA's
 // writes) and waits with acquire loads.  Returns false (and the CTA must
 // return) when any CTA has recorded an error or the wait ran past timeout_ns.
-__device__ inline bool grid_sync(Record *rec, unsigned long long timeout_ns,
+__device__ inline bool grid_sync(Record *rec, unsigned long long timeout_ns, int nctas, int rank,
                                  unsigned long long *trace_slot = nullptr)
 {
     __shared__ int ok;
@@ -444,7 +448,7 @@ __device__ inline bool grid_sync(Record *rec, unsigned long long timeout_ns,
         volatile int *vst = &rec->status;
         const unsigned int g = ld_acquire_gpu(&rec->bar.gen);
         const unsigned int prev = atom_add_release_gpu(&rec->bar.count, 1u);
-        if (prev == gridDim.x - 1) {
+        if (prev == (unsigned int)nctas - 1) {
             rec->bar.count = 0;  // ordered before the release of the new generation
             st_release_gpu(&rec->bar.gen, g + 1);
         } else {
@@ -462,7 +466,7 @@ __device__ inline bool grid_sync(Record *rec, unsigned long long timeout_ns,
             }
         }
         if (*vst != 0) ok = 0;
-        if (trace_slot && blockIdx.x == 0) trace_slot[2] = gtimer();
+        if (trace_slot && rank == 0) trace_slot[2] = gtimer();
         t_pass = trace_slot ? gtimer() : 0ull;
     }
     __syncthreads();
@@ -662,7 +666,7 @@ __device__ void layer_idwt(const Args<T, S> &A, T *buf, Load load, Post post)
 {
     constexpr int W = VW<T>::W;
     const Geo<T> &G = A.geo;
-    for (int l = blockIdx.x; l < G.L; l += gridDim.x) {
+    for (int l = A.vrank(); l < G.L; l += A.ncta) {
         const int n = G.lay_n[l], lgn = G.lay_lg[l], nv = n * n / W;
         const long off = G.lay_off[l];
 #pragma unroll 2
@@ -708,7 +712,7 @@ __device__ __noinline__ typename AccT<T>::type wfs_phase(const Args<T, S> &A, T 
     T *sx = sm + (size_t)G.L * HY * HX;   // [SY*SX]
     T *sy = sx + SY * SX;
     Acc ws = 0;
-    for (int w = blockIdx.x; w < total; w += gridDim.x) {
+    for (int w = A.vrank(); w < total; w += A.ncta) {
         const int g = w / per_g, tt = w - g * per_g;
         const int i0 = (tt / G.tiles_x) * TY, j0 = (tt % G.tiles_x) * TX;
         if (!RHS) {
@@ -792,7 +796,7 @@ __device__ __noinline__ void band_gather(const Args<T, S> &A, T *sm)
 {
     const Geo<T> &G = A.geo;
     const int m = G.m, RC = G.rows_chunk, NB = G.nbands;
-    for (int w = blockIdx.x; w < NB; w += gridDim.x) {
+    for (int w = A.vrank(); w < NB; w += A.ncta) {
         const int l = __ldg(G.band_layer + w), a0 = __ldg(G.band_row0 + w), BR = __ldg(G.band_rows + w);
         const int n = G.lay_n[l], lgn = G.lay_lg[l], nout = BR << lgn;
         const int oa = threadIdx.x >> lgn, ob = threadIdx.x & (n - 1);  // owned output (a0 + oa, ob)
@@ -864,7 +868,7 @@ __device__ void layer_fdwt(const Args<T, S> &A, T *buf, Store store)
 {
     constexpr int W = VW<T>::W;
     const Geo<T> &G = A.geo;
-    for (int l = blockIdx.x; l < G.L; l += gridDim.x) {
+    for (int l = A.vrank(); l < G.L; l += A.ncta) {
         const int n = G.lay_n[l], lgn = G.lay_lg[l], nv = n * n / W;
         const long off = G.lay_off[l];
 #pragma unroll 4
@@ -891,19 +895,19 @@ __device__ void layer_fdwt(const Args<T, S> &A, T *buf, Store store)
 }
 
 // Element range of this CTA for vector phases, aligned to W elements.
-__device__ __forceinline__ void cta_range_vec(long n, int W, long &lo, long &hi)
+__device__ __forceinline__ void cta_range_vec(long n, int W, int rank, int nctas, long &lo, long &hi)
 {
     long nv = n / W;
-    long chunk = (nv + gridDim.x - 1) / gridDim.x;
-    lo = (long)blockIdx.x * chunk * W;
+    long chunk = (nv + nctas - 1) / nctas;
+    lo = (long)rank * chunk * W;
     hi = lo + chunk * W < n ? lo + chunk * W : n;
 }
 
 // Element range of this CTA for vector phases.
-__device__ __forceinline__ void cta_range(long n, long &lo, long &hi)
+__device__ __forceinline__ void cta_range(long n, int rank, int nctas, long &lo, long &hi)
 {
-    long chunk = (n + gridDim.x - 1) / gridDim.x;
-    lo = (long)blockIdx.x * chunk;
+    long chunk = (n + nctas - 1) / nctas;
+    lo = (long)rank * chunk;
     hi = lo + chunk < n ? lo + chunk : n;
 }
 

@@ -38,7 +38,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_wfs(Args<T, S> A)
     __shared__ double sred[kSred];
     typename AccT<T>::type acc[1] = {wfs_phase<T, S, RHS>(A, dyn_smem<T>())};
     const int slots[1] = {kSlotB};
-    block_partials<1>(acc, A.part, slots, sred);
+    block_partials<1>(acc, A.part, slots, sred, A.vrank());
 }
 
 // u = P^T psi
@@ -90,7 +90,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_rhs_gather(Args<T, S> A)
 {
     FEWHA_PHASE_GUARD
     band_gather<T, S>(A, dyn_smem<T>());
-    if (b.kv > 0 && blockIdx.x == gridDim.x - 1) phase_factor<T, S>(A, b, sc);
+    if (b.kv > 0 && A.vrank() == A.ncta - 1) phase_factor<T, S>(A, b, sc);
 }
 
 template <typename T, typename S>
@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_B(Args<T, S> A, int k)
     (void)sc;
     typename AccT<T>::type acc[1] = {wfs_phase<T, S, false>(A, dyn_smem<T>())};
     const int slots[1] = {kSlotB + (k & 1)};
-    block_partials<1>(acc, A.part, slots, sred);
+    block_partials<1>(acc, A.part, slots, sred, A.vrank());
 }
 
 template <typename T, typename S>
@@ -160,27 +160,26 @@ template <typename T, typename S>
 __global__ void __launch_bounds__(kThreads, 1) k_finish(Args<T, S> A)
 {
     __shared__ Scal sc;
-    if (blockIdx.x != 0) return;
+    if (A.vrank() != 0) return;
     const Basis b = basis_info(A);
     int K = ldcgi(&A.rec->done) ? ldcgi(&A.rec->iters) : A.max_iter;
     phase_finish<T, S>(A, b, K, sc);
 }
 
-// --- the whole time step in one persistent cooperative kernel ---------------
+// --- the whole time step of one instance, run by its group of CTAs ----------
 template <typename T, typename S>
-__global__ void __launch_bounds__(kThreads, 1) k_solve_persistent(Args<T, S> A)
+__device__ void solve_body(const Args<T, S> &A, Scal &sc, double *sred)
 {
-    __shared__ Scal sc;
-    __shared__ double sred[kSred];
     T *sm = dyn_smem<T>();
     const unsigned long long to = A.timeout_ns;
     const Basis b = basis_info(A);
+    const int rank = A.vrank();
     int ti = 0;  // trace slot of the next barrier
-    // barrier with the optional phase trace (tag = phase id)
+    // barrier of the group with the optional phase trace (tag = phase id)
     auto sync = [&](int tag) -> bool {
         unsigned long long *slot = (A.trace && ti < A.trace_cap) ? A.trace + 4 * ti : nullptr;
-        if (slot && blockIdx.x == 0 && threadIdx.x == 0) slot[3] = (unsigned long long)tag;
-        bool ok = grid_sync(A.rec, to, slot);
+        if (slot && rank == 0 && threadIdx.x == 0) slot[3] = (unsigned long long)tag;
+        bool ok = grid_sync(A.rec, to, A.ncta, rank, slot);
         ti++;
         return ok;
     };
@@ -190,7 +189,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_solve_persistent(Args<T, S> A)
         if (b.kv > 0) phase_gram<T, S>(A, b, sm, (int)(A.smem_bytes / sizeof(T)));
         if (!sync(1)) break;
         band_gather<T, S>(A, sm);
-        if (b.kv > 0 && blockIdx.x == gridDim.x - 1) phase_factor<T, S>(A, b, sc);
+        if (b.kv > 0 && rank == A.ncta - 1) phase_factor<T, S>(A, b, sc);
         if (!sync(2)) break;
         phase_rhs_fdwt<T, S>(A, sm, sred);
         if (!sync(3)) break;
@@ -209,7 +208,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_solve_persistent(Args<T, S> A)
             {
                 typename AccT<T>::type acc[1] = {wfs_phase<T, S, false>(A, sm)};
                 const int slots[1] = {kSlotB + (k & 1)};
-                block_partials<1>(acc, A.part, slots, sred);
+                block_partials<1>(acc, A.part, slots, sred, rank);
             }
             if (!sync(12)) break;
             if (!phase_C<T, S>(A, b, k, sm, sc)) {
@@ -225,7 +224,45 @@ __global__ void __launch_bounds__(kThreads, 1) k_solve_persistent(Args<T, S> A)
     } while (0);
     // on a device-side error the stats carry the status; the other fields are
     // then not meaningful
-    if (blockIdx.x == 0) phase_finish<T, S>(A, b, K, sc);
+    if (rank == 0) phase_finish<T, S>(A, b, K, sc);
+}
+
+// One instance on the whole grid (cooperative launch).
+template <typename T, typename S>
+__global__ void __launch_bounds__(kThreads, 1) k_solve_persistent(Args<T, S> A)
+{
+    __shared__ Scal sc;
+    __shared__ double sred[kSred];
+    solve_body<T, S>(A, sc, sred);
+}
+
+// Many instances in one cooperative launch: CTA c runs instance cta_inst[c]
+// with the group of CTAs [inst.cta0, inst.cta0 + inst.ncta).
+template <typename T, typename S>
+__global__ void __launch_bounds__(kThreads, 1) k_solve_batched(const Args<T, S> *inst, const int *cta_inst)
+{
+    __shared__ Scal sc;
+    __shared__ double sred[kSred];
+    __shared__ __align__(16) Args<T, S> A;
+    const int i = cta_inst[blockIdx.x];
+    {
+        const int4 *src = reinterpret_cast<const int4 *>(inst + i);
+        int4 *dst = reinterpret_cast<int4 *>(&A);
+        for (int e = threadIdx.x; e < (int)(sizeof(Args<T, S>) / sizeof(int4)); e += blockDim.x) dst[e] = src[e];
+    }
+    __syncthreads();
+    solve_body<T, S>(A, sc, sred);
+}
+
+// Resets the record flags and the barrier of every instance of a batch.
+template <typename T, typename S>
+__global__ void k_batch_reset(const Args<T, S> *inst, int n)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        Record *r = inst[i].rec;
+        r->status = r->done = r->iters = r->chol_ok = 0;
+        r->bar.count = r->bar.gen = 0;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -258,6 +295,19 @@ struct ImplBase {
     virtual int set_invJ(const std::vector<double> &invJ) = 0;
     virtual void set_trace(unsigned long long *buf, int cap) = 0;
     virtual void set_timeout(unsigned long long ns) = 0;
+    // --- batched launch support (many instances, one cooperative kernel) ---
+    virtual size_t args_size() const = 0;
+    virtual int precision_id() const = 0;
+    // WFS tile shape for a group of `ctas` CTAs, and the dynamic shared memory it needs
+    virtual int tiles_for(int ctas, int *ty, int *tx) const = 0;
+    virtual size_t smem_for(int ty, int tx) const = 0;
+    // host copy of this instance's kernel arguments for one time step
+    virtual int batch_args(void *out, const void *sl, void *c, const fewha_state *st, const fewha_solve_opts *o,
+                           fewha_stats *stats, int cta0, int ncta, int ty, int tx, size_t smem) const = 0;
+    // CTAs that can be co-resident for the batched kernel with `smem` bytes
+    virtual int batch_capacity(size_t smem, int *max_ctas) const = 0;
+    virtual int launch_batched(const void *d_args, const int *d_map, int n, int total, size_t smem,
+                               cudaStream_t s) const = 0;
     // y = M x with every scratch buffer carved from caller-provided device
     // memory (no allocation); FEWHA_ERR_SCRATCH if `bytes` is too small.
     virtual int apply_in_scratch(const void *x, void *y, void *scratch, size_t bytes, cudaStream_t s) = 0;
@@ -271,7 +321,47 @@ struct Impl : ImplBase {
     size_t smem = 0;
     std::vector<void *> owned;
 
+    size_t sm_fixed = 0;  // dynamic shared memory of every phase but the WFS tiles
+
     explicit Impl(const Plan &p) : P(p) {}
+
+    // WFS tile bytes: per-layer halo values and the weighted slopes
+    size_t wfs_bytes(int ty, int tx) const
+    {
+        return ((size_t)P.L * (ty + 2) * (tx + 2) + 2 * (size_t)(ty + 1) * (tx + 1)) * sizeof(T);
+    }
+
+    // WFS tile shape: a square tile if the caller fixed one, else the shape
+    // (8..32 nodes per side) whose work per round of `ctas` CTAs is least
+    // among those whose shared memory fits
+    int tiles_for(int ctas, int *ty_out, int *tx_out) const override
+    {
+        double best = 1e300;
+        *ty_out = *tx_out = 0;
+        const int cand[4] = {8, 16, 24, 32};
+        for (int a = 0; a < 4; a++)
+            for (int c = 0; c < 4; c++) {
+                int ty = cand[a], tx = cand[c];
+                if (P.geom.tile) ty = tx = P.geom.tile;
+                if (wfs_bytes(ty, tx) > 200 * 1024) continue;
+                const int tiles = P.G * ((P.m + ty - 1) / ty) * ((P.m + tx - 1) / tx);
+                const int rounds = (tiles + ctas - 1) / ctas;
+                const double cost = rounds * ((double)(ty + 2) * (tx + 2) + 64.0);
+                if (cost < best - 1e-9) {
+                    best = cost;
+                    *ty_out = ty;
+                    *tx_out = tx;
+                }
+            }
+        return *ty_out ? FEWHA_OK : FEWHA_ERR_GEOMETRY;
+    }
+
+    size_t smem_for(int ty, int tx) const override { return std::max(sm_fixed, wfs_bytes(ty, tx)); }
+    size_t args_size() const override { return sizeof(Args<T, S>); }
+    int precision_id() const override
+    {
+        return sizeof(T) == 8 ? FEWHA_F64 : (sizeof(S) == 2 ? FEWHA_BF16S : FEWHA_F32);
+    }
     ~Impl() override
     {
         for (void *q : owned) cudaFree(q);
@@ -315,35 +405,12 @@ struct Impl : ImplBase {
             G.h[t] = t < G.n_taps ? (T)P.taps[t] : T(0);
             G.g[t] = t < G.n_taps ? (T)(((t & 1) ? -1.0 : 1.0) * P.taps[G.n_taps - 1 - t]) : T(0);
         }
-        // WFS tiles: a square tile if the caller fixed one, else the shape
-        // (8..32 nodes per side) whose work per round of CTAs is least among
-        // those whose shared memory fits
-        auto wfs_smem = [&](int ty, int tx) -> size_t {
-            return ((size_t)P.L * (ty + 2) * (tx + 2) + 2 * (size_t)(ty + 1) * (tx + 1)) * sizeof(T);
-        };
+        // WFS tiles for the whole grid
         {
             int dev0, nsm0;
             CK(cudaGetDevice(&dev0));
             CK(cudaDeviceGetAttribute(&nsm0, cudaDevAttrMultiProcessorCount, dev0));
-            const int ctas = grid > 0 ? grid : nsm0;
-            double best = 1e300;
-            G.tile_y = G.tile_x = 0;
-            const int cand[4] = {8, 16, 24, 32};
-            for (int a = 0; a < 4; a++)
-                for (int c = 0; c < 4; c++) {
-                    int ty = cand[a], tx = cand[c];
-                    if (P.geom.tile) ty = tx = P.geom.tile;
-                    if (wfs_smem(ty, tx) > 200 * 1024) continue;
-                    const int tiles = P.G * ((P.m + ty - 1) / ty) * ((P.m + tx - 1) / tx);
-                    const int rounds = (tiles + ctas - 1) / ctas;
-                    const double cost = rounds * ((double)(ty + 2) * (tx + 2) + 64.0);
-                    if (cost < best - 1e-9) {
-                        best = cost;
-                        G.tile_y = ty;
-                        G.tile_x = tx;
-                    }
-                }
-            if (!G.tile_y) return FEWHA_ERR_GEOMETRY;
+            if (tiles_for(grid > 0 ? grid : nsm0, &G.tile_y, &G.tile_x)) return FEWHA_ERR_GEOMETRY;
             G.tiles_y = (P.m + G.tile_y - 1) / G.tile_y;
             G.tiles_x = (P.m + G.tile_x - 1) / G.tile_x;
         }
@@ -427,7 +494,7 @@ struct Impl : ImplBase {
         size_t sm_layer = (size_t)nmax * (nmax + 1) * sizeof(T);  // pitch n + 1
         G.pingpong = sizeof(T) == 4 ? 1 : 0;  // FP32: second buffer for out-of-place DWT passes
         if (G.pingpong) sm_layer *= 2;
-        const size_t sm_wfs = wfs_smem(G.tile_y, G.tile_x);
+        const size_t sm_wfs = wfs_bytes(G.tile_y, G.tile_x);
         smem = std::max(sm_layer, sm_wfs);
         // band_gather stages rows_chunk psi rows and their x-contraction
         // (all guide stars of a band at once when they fit, else in groups)
@@ -437,6 +504,7 @@ struct Impl : ImplBase {
         if (want > smem) smem = std::min(want, smem_cap);
         G.rows_chunk = (int)std::min<size_t>(max_rows_sum, smem / row_bytes);
         if (smem > smem_cap || G.rows_chunk < max_rows) return FEWHA_ERR_GEOMETRY;
+        sm_fixed = std::max(sm_layer, std::min(want, smem_cap));
         int dev, nsm;
         CK(cudaGetDevice(&dev));
         CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
@@ -461,6 +529,8 @@ struct Impl : ImplBase {
         CK(setattr((const void *)k_E<T, S>));
         CK(setattr((const void *)k_finish<T, S>));
         CK(setattr((const void *)k_solve_persistent<T, S>));
+        CK(cudaFuncSetAttribute((const void *)k_solve_batched<T, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                200 * 1024));
         int per_sm = 0;
         CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve_persistent<T, S>, kThreads, smem));
         if (per_sm < 1) return FEWHA_ERR_CUDA;
@@ -469,6 +539,7 @@ struct Impl : ImplBase {
         if (ncta > kMaxCtas) ncta = kMaxCtas;
         base.timeout_ns = 1000000000ull;
         base.ncta = ncta;
+        base.cta0 = 0;
         base.smem_bytes = smem;
         return FEWHA_OK;
     }
@@ -555,8 +626,8 @@ struct Impl : ImplBase {
         return launch_check();
     }
 
-    int solve(const void *sl, void *c, const fewha_state *st, const fewha_solve_opts *o,
-              fewha_stats *stats, cudaStream_t s) override
+    Args<T, S> solve_args(const void *sl, void *c, const fewha_state *st, const fewha_solve_opts *o,
+                          fewha_stats *stats) const
     {
         Args<T, S> A = base;
         A.slopes = static_cast<const S *>(sl);
@@ -573,6 +644,59 @@ struct Impl : ImplBase {
         A.augmented = o->augmented ? 1 : 0;
         A.recycle_all = o->recycle_mode == FEWHA_RECYCLE_ALL ? 1 : 0;
         A.stats = stats;
+        return A;
+    }
+
+    int batch_args(void *out, const void *sl, void *c, const fewha_state *st, const fewha_solve_opts *o,
+                   fewha_stats *stats, int cta0, int nct, int ty, int tx, size_t sm) const override
+    {
+        Args<T, S> A = solve_args(sl, c, st, o, stats);
+        A.cta0 = cta0;
+        A.ncta = nct;
+        A.geo.tile_y = ty;
+        A.geo.tile_x = tx;
+        A.geo.tiles_y = (P.m + ty - 1) / ty;
+        A.geo.tiles_x = (P.m + tx - 1) / tx;
+        A.smem_bytes = sm;
+        A.trace = nullptr;
+        A.trace_cap = 0;
+        std::memcpy(out, &A, sizeof(A));
+        return FEWHA_OK;
+    }
+
+    int batch_capacity(size_t sm, int *max_ctas) const override
+    {
+        int dev, nsm, per_sm = 0;
+        CK(cudaGetDevice(&dev));
+        CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve_batched<T, S>, kThreads, sm));
+        *max_ctas = std::min(nsm * per_sm, kMaxCtas);
+        return FEWHA_OK;
+    }
+
+    int launch_batched(const void *d_args, const int *d_map, int n, int total, size_t sm,
+                       cudaStream_t s) const override
+    {
+        const Args<T, S> *args = static_cast<const Args<T, S> *>(d_args);
+        k_batch_reset<T, S><<<(n + 255) / 256, 256, 0, s>>>(args, n);
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(total);
+        cfg.blockDim = dim3(kThreads);
+        cfg.dynamicSmemBytes = sm;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        CK(cudaLaunchKernelEx(&cfg, k_solve_batched<T, S>, args, d_map));
+        return cudaGetLastError() == cudaSuccess ? FEWHA_OK : FEWHA_ERR_CUDA;
+    }
+
+    int solve(const void *sl, void *c, const fewha_state *st, const fewha_solve_opts *o,
+              fewha_stats *stats, cudaStream_t s) override
+    {
+        Args<T, S> A = solve_args(sl, c, st, o, stats);
         CK(cudaMemsetAsync(A.rec, 0, offsetof(Record, rz), s));
         CK(cudaMemsetAsync(&A.rec->bar, 0, sizeof(Bar), s));
         if (A.trace) CK(cudaMemsetAsync(A.trace, 0, (size_t)A.trace_cap * 4 * sizeof(unsigned long long), s));

@@ -90,7 +90,7 @@ __device__ __noinline__ void phase_gram(const Args<T, S> &A, const Basis &b, T *
     typedef typename AccT<T>::type Acc;
     constexpr int W = VW<T>::W;
     long lo, hi;
-    cta_range_vec(A.geo.n, W, lo, hi);
+    cta_range_vec(A.geo.n, W, A.vrank(), A.ncta, lo, hi);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int kv = b.kv, nslot = kv * kv, nvec = 2 * kv;
     const int CH = (sm_elems / nvec) / W * W;  // elements of the slice staged at once
@@ -116,7 +116,7 @@ __device__ __noinline__ void phase_gram(const Args<T, S> &A, const Basis &b, T *
     }
     for (int s2 = warp, t = 0; s2 < nslot; s2 += nw, t++) {
         const Acc a = warp_sum_t(acc[t]);
-        if (lane == 0) A.part[(size_t)(kSlotGram + s2) * kMaxCtas + blockIdx.x] = (double)a;
+        if (lane == 0) A.part[(size_t)(kSlotGram + s2) * kMaxCtas + A.vrank()] = (double)a;
     }
     __syncthreads();
 }
@@ -165,7 +165,7 @@ __device__ __noinline__ void phase_rhs_fdwt(const Args<T, S> &A, T *sm, double *
         vst(A.r + e, r0);
     });
     const int slots[2] = {kSlotR2, kSlotR2 + 1};
-    block_partials<2>(acc, A.part, slots, sred);
+    block_partials<2>(acc, A.part, slots, sred, A.vrank());
 }
 
 // INIT1: P^T r0 (Algorithm 2 initial projection), per CTA slice.
@@ -175,7 +175,7 @@ __device__ __noinline__ void phase_ptr(const Args<T, S> &A, const Basis &b, doub
     typedef typename AccT<T>::type Acc;
     constexpr int W = VW<T>::W;
     long lo, hi;
-    cta_range_vec(A.geo.n, W, lo, hi);
+    cta_range_vec(A.geo.n, W, A.vrank(), A.ncta, lo, hi);
     Acc acc[kK];
     for (int j = 0; j < kK; j++) acc[j] = 0;
     for (long e = lo + (long)threadIdx.x * W; e < hi; e += (long)blockDim.x * W) {
@@ -190,7 +190,7 @@ __device__ __noinline__ void phase_ptr(const Args<T, S> &A, const Basis &b, doub
     }
     int slots[kK];
     for (int j = 0; j < kK; j++) slots[j] = kSlotGram + kK * kK + j;
-    block_partials<kK>(acc, A.part, slots, sred);
+    block_partials<kK>(acc, A.part, slots, sred, A.vrank());
 }
 
 // INIT2: c += P sigma, r -= Q sigma with sigma = G^{-1} P^T r0; then the
@@ -206,7 +206,7 @@ __device__ __noinline__ void phase_init(const Args<T, S> &A, const Basis &b, Sca
     typedef typename AccT<T>::type Acc;
     constexpr int W = VW<T>::W;
     long lo, hi;
-    cta_range_vec(A.geo.n, W, lo, hi);
+    cta_range_vec(A.geo.n, W, A.vrank(), A.ncta, lo, hi);
     Acc acc[kK + 2];
     for (int j = 0; j < kK + 2; j++) acc[j] = 0;
     for (long e = lo + (long)threadIdx.x * W; e < hi; e += (long)blockDim.x * W) {
@@ -245,7 +245,7 @@ __device__ __noinline__ void phase_init(const Args<T, S> &A, const Basis &b, Sca
     for (int j = 0; j < kK; j++) slots[j] = kSlotInit + j;
     slots[kK] = kSlotInit + kK;
     slots[kK + 1] = kSlotInit + kK + 1;
-    block_partials<kK + 2>(acc, A.part, slots, sred);
+    block_partials<kK + 2>(acc, A.part, slots, sred, A.vrank());
 }
 
 // ---------------------------------------------------------------------------
@@ -278,7 +278,7 @@ __device__ __noinline__ bool phase_A(const Args<T, S> &A, const Basis &b, int k,
             sc.rr = kv > 0 ? red[3 + kv] : red[1];
             sc.beta = 0.0;
             sc.mu = 0.0;
-            if (blockIdx.x == 0) A.rec->bb = sc.bb;
+            if (A.vrank() == 0) A.rec->bb = sc.bb;
         }
     } else {
         // red: [0] rz, [1] zq, [2] rp, [3] rr (E_{k-1}); [4..4+kv) Q^T z, [4+kK..) P^T r
@@ -307,13 +307,13 @@ __device__ __noinline__ bool phase_A(const Args<T, S> &A, const Basis &b, int k,
             sc.rr = red[3];
             sc.bb = ldcgd(&A.rec->bb);
             sc.beta = rz * ldcgd(A.rec->rinv + (k - 1));
-            if (blockIdx.x == 0) A.rec->rz[k] = rz;
+            if (A.vrank() == 0) A.rec->rz[k] = rz;
         }
     }
     __syncthreads();
     if (threadIdx.x == 0) {
         sc.stop = (A.rtol > 0.0 && sc.rr <= A.rtol * A.rtol * sc.bb) ? 1 : 0;
-        if (sc.stop && blockIdx.x == 0) {
+        if (sc.stop && A.vrank() == 0) {
             A.rec->iters = k;
             A.rec->done = 1;
         }
@@ -372,7 +372,7 @@ __device__ __noinline__ bool phase_A(const Args<T, S> &A, const Basis &b, int k,
         }
     });
     const int slots[2] = {kSlotA + (k & 1) * 2, kSlotA + (k & 1) * 2 + 1};
-    block_partials<2>(acc, A.part, slots, sred);
+    block_partials<2>(acc, A.part, slots, sred, A.vrank());
     return true;
 }
 
@@ -402,9 +402,9 @@ __device__ __noinline__ bool phase_C(const Args<T, S> &A, const Basis &b, int k,
             sc.stop = 1;
         } else if (!(sc.pq > 0.0) || !isfinite(sc.pq) || !isfinite(sc.rz)) {
             sc.stop = 1;
-            if (blockIdx.x == 0) set_status(A.rec, FEWHA_ERR_BREAKDOWN);
+            if (A.vrank() == 0) set_status(A.rec, FEWHA_ERR_BREAKDOWN);
         }
-        if (blockIdx.x == 0) {
+        if (A.vrank() == 0) {
             if (sc.stop) {
                 A.rec->iters = k;
                 A.rec->done = 1;
@@ -443,7 +443,7 @@ __device__ __noinline__ void phase_E_impl(const Args<T, S> &A, const Basis &b, i
     const T *qm = kv > 0 ? oldQ(A, b, kv - 1) : nullptr;
     constexpr int W = VW<T>::W;
     long lo, hi;
-    cta_range_vec(A.geo.n, W, lo, hi);
+    cta_range_vec(A.geo.n, W, A.vrank(), A.ncta, lo, hi);
     typedef typename AccT<T>::type Acc;
     const bool last = kv > 0 && !ALL;
     const bool all = kv > 0 && ALL;
@@ -497,7 +497,7 @@ __device__ __noinline__ void phase_E_impl(const Args<T, S> &A, const Basis &b, i
     const int e0 = kSlotE + (k & 1) * kSlotEStride;
     int slots[NA];
     for (int i = 0; i < NA; i++) slots[i] = e0 + i;
-    block_partials<NA>(acc, A.part, slots, sred);
+    block_partials<NA>(acc, A.part, slots, sred, A.vrank());
 }
 
 template <typename T, typename S>

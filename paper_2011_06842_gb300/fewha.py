@@ -98,6 +98,14 @@ def load_library(path=LIB_PATH):
     lib.fewha_set_timeout.restype = C.c_int
     lib.fewha_set_trace.argtypes = [vp, vp, C.c_int]
     lib.fewha_set_trace.restype = C.c_int
+    lib.fewha_batch_create.argtypes = [C.POINTER(vp), C.c_int, C.POINTER(C.c_int), C.POINTER(vp)]
+    lib.fewha_batch_create.restype = C.c_int
+    lib.fewha_batch_ctas.argtypes = [vp, C.POINTER(C.c_int)]
+    lib.fewha_batch_ctas.restype = C.c_int
+    lib.fewha_batch_solve.argtypes = [vp, C.POINTER(vp), C.POINTER(vp), C.POINTER(STATE), C.POINTER(OPTS), vp, vp]
+    lib.fewha_batch_solve.restype = C.c_int
+    lib.fewha_batch_destroy.argtypes = [vp]
+    lib.fewha_batch_destroy.restype = None
     lib.fewha_strerror.argtypes = [C.c_int]
     lib.fewha_strerror.restype = C.c_char_p
     for name in ("fewha_create", "fewha_get_prior", "fewha_get_precond", "fewha_apply_op",
@@ -111,7 +119,8 @@ def exported_symbols():
     """Entry points declared in include/fewha.h."""
     return ["fewha_create", "fewha_destroy", "fewha_n_unknowns", "fewha_n_slopes",
             "fewha_layer_spacing", "fewha_get_prior", "fewha_get_precond", "fewha_apply_op",
-            "fewha_rhs", "fewha_solve", "fewha_set_timeout", "fewha_set_trace", "fewha_apply_op_noalloc", "fewha_strerror"]
+            "fewha_rhs", "fewha_solve", "fewha_set_timeout", "fewha_set_trace", "fewha_apply_op_noalloc", "fewha_batch_create",
+            "fewha_batch_ctas", "fewha_batch_solve", "fewha_batch_destroy", "fewha_strerror"]
 
 
 def make_geometry(geom, noise_w, precision="f64", tile=0, grid=0) -> GEOMETRY:
@@ -307,3 +316,109 @@ class Fewha:
         st = STATS.from_buffer_copy(raw)
         return {"status": st.status, "iterations": st.iterations, "rel_res": st.rel_res,
                 "bnorm": st.bnorm, "rz": st.rz, "basis_count": st.basis_count}
+
+
+class FewhaBatch:
+    """Many instances (Fewha handles of one precision) solved by one
+    cooperative launch, each by its own group of CTAs (fewha_batch_*)."""
+
+    def __init__(self, fewhas, ctas=None):
+        import torch
+        self._torch = torch
+        self.fewhas = list(fewhas)
+        self.lib = load_library()
+        n = len(self.fewhas)
+        hs = (C.c_void_p * n)(*[f._h.value for f in self.fewhas])
+        cs = (C.c_int * n)(*ctas) if ctas is not None else None
+        b = C.c_void_p()
+        st = self.lib.fewha_batch_create(hs, n, cs, C.byref(b))
+        if st != 0:
+            raise FewhaError(st, "fewha_batch_create")
+        self._b = b
+        self.n = n
+        self.device = self.fewhas[0].device
+
+    def ctas(self):
+        out = (C.c_int * self.n)()
+        self.lib.fewha_batch_ctas(self._b, out)
+        return list(out)
+
+    def new_stats(self):
+        return self._torch.zeros(self.n * STATS_BYTES, dtype=self._torch.uint8, device=self.device)
+
+    def solve(self, slopes, cs, states, max_iter, rtol=0.0, augmented=True, recycle_all=False, stats=None):
+        """One time step of every instance; cs are updated in place."""
+        n = self.n
+        for f, sl, c in zip(self.fewhas, slopes, cs):
+            f._vec(sl, f.n_slopes, f.slope_dtype, "s")
+            f._vec(c, f.n, f.dtype, "c")
+        sp = (C.c_void_p * n)(*[t.data_ptr() for t in slopes])
+        cp = (C.c_void_p * n)(*[t.data_ptr() for t in cs])
+        stt = (STATE * n)(*[s_.c_struct for s_ in states])
+        o = OPTS(int(max_iter), float(rtol), 1 if augmented else 0, RECYCLE_ALL if recycle_all else RECYCLE_LAST,
+                 LAUNCH_PERSISTENT, 0)
+        stats = stats if stats is not None else self.new_stats()
+        st = self.lib.fewha_batch_solve(self._b, sp, cp, stt, C.byref(o), C.c_void_p(stats.data_ptr()),
+                                        _stream_ptr(self._torch))
+        if st != 0:
+            raise FewhaError(st, "fewha_batch_solve")
+        return stats
+
+    def read_stats(self, stats):
+        raw = stats.cpu().numpy().tobytes()
+        out = []
+        for i in range(self.n):
+            stt = STATS.from_buffer_copy(raw[i * STATS_BYTES:(i + 1) * STATS_BYTES])
+            out.append({"status": stt.status, "iterations": stt.iterations, "rel_res": stt.rel_res,
+                        "bnorm": stt.bnorm, "basis_count": stt.basis_count})
+        return out
+
+    def close(self):
+        if getattr(self, "_b", None):
+            self.lib.fewha_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def autotune_batch(fewhas, step, candidates=None, reps=3):
+    """Chooses the CTA groups of a batch by timing: `step(batch)` runs one
+    batched time step; each candidate split (None = the library's work-
+    proportional default, or a list of CTAs per instance) is timed over
+    `reps` steps with CUDA events and the fastest is returned with all
+    timings (ms per step)."""
+    import torch
+    n = len(fewhas)
+    if candidates is None:
+        sizes = [f.n for f in fewhas]
+        tot = sum(sizes)
+        cap = 148
+        candidates = [None,
+                      [max(1, int(cap * s / tot)) for s in sizes],
+                      [max(1, cap // n)] * n]
+    timings = []
+    best, best_ms = None, float("inf")
+    for cand in candidates:
+        try:
+            b = FewhaBatch(fewhas, cand)
+        except FewhaError:
+            timings.append((cand, None))
+            continue
+        step(b)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            step(b)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        timings.append((b.ctas(), ms))
+        if ms < best_ms:
+            best, best_ms = b.ctas(), ms
+        b.close()
+    return best, timings

@@ -1,0 +1,73 @@
+"""Batched time steps: instances of different geometries in one cooperative
+launch, each on its own group of CTAs, must match the FP64 oracle like
+single-instance solves (1e-10 in FP64 for fixed-iteration solves, 1e-5 in
+FP32)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import Oracle  # noqa: E402
+from synth import FrozenFlowSensors, configs  # noqa: E402
+
+
+def rel(a, b):
+    return np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2011_06842_gb300 import build
+    build.build()
+    import paper_2011_06842_gb300 as P
+    return P
+
+
+@pytest.mark.parametrize("prec,tol,ctas", [("f64", 1e-10, None), ("f32", 1e-5, None), ("f64", 1e-10, [1, 3, 2, 5, 4])])
+def test_batched_matches_oracle(lib, prec, tol, ctas):
+    names = ["tiny", "micro", "mixed", "tiny", "medium"]
+    frames = 3
+    inst = []
+    for i, name in enumerate(names):
+        geom = configs.get(name)
+        s, w = FrozenFlowSensors(geom, seed=40 + i).sequence(frames, seed=50 + i)
+        o = Oracle(geom, w)
+        f = lib.Fewha(geom, w, prec)
+        inst.append((o, o.new_state(4), f, f.new_state(4), torch.zeros(f.n, dtype=f.dtype, device="cuda"),
+                     s.to(f.slope_dtype).cuda(), s.numpy()))
+    batch = lib.FewhaBatch([x[2] for x in inst], ctas)
+    if ctas is not None:
+        assert batch.ctas() == ctas
+    for t in range(frames):
+        stats = batch.solve([x[5][t] for x in inst], [x[4] for x in inst], [x[3] for x in inst], max_iter=4)
+        for (o, st_o, f, st_g, c, sd, s64), rg in zip(inst, batch.read_stats(stats)):
+            ro = o.solve(s64[t], st_o, max_iter=4, augmented=True)
+            assert rg["status"] == 0 and rg["iterations"] == ro["iterations"]
+            assert rel(c.cpu().numpy(), st_o["c"]) < tol
+    batch.close()
+
+
+def test_batched_rtol_instances_finish_independently(lib):
+    """Instances stop at their own residual: each one's iteration count equals
+    its single-instance solve's."""
+    names = ["tiny", "mixed"]
+    inst = []
+    for i, name in enumerate(names):
+        geom = configs.get(name)
+        s, w = FrozenFlowSensors(geom, seed=60 + i).sequence(2, seed=70 + i)
+        f = lib.Fewha(geom, w, "f64")
+        g = lib.Fewha(geom, w, "f64")
+        inst.append((f, f.new_state(8), torch.zeros(f.n, dtype=torch.float64, device="cuda"),
+                     g, g.new_state(8), torch.zeros(g.n, dtype=torch.float64, device="cuda"), s.cuda()))
+    batch = lib.FewhaBatch([x[0] for x in inst])
+    for t in range(2):
+        rb = batch.read_stats(batch.solve([x[6][t] for x in inst], [x[2] for x in inst], [x[1] for x in inst],
+                                          max_iter=80, rtol=2e-2))
+        for (f, st, c, g, st2, c2, s), r in zip(inst, rb):
+            r2 = g.read_stats(g.solve(s[t], c2, st2, 80, rtol=2e-2))
+            assert r["iterations"] == r2["iterations"]
+            assert rel(c.cpu().numpy(), c2.cpu().numpy()) < 1e-9
+    batch.close()
