@@ -154,6 +154,13 @@ int fewha_get_precond(const void *handle, double *invJ_host);
 /* y = M x (Eq. M).  x, y: device vectors of length n; must not overlap. */
 int fewha_apply_op(void *handle, const void *x, void *y, cudaStream_t stream);
 
+/* y_v = M x_v for v = 0..nvec-1 (x_v = x + v*ldx, y_v = y + v*ldy elements,
+ * 1 <= nvec <= FEWHA_MAX_MULTI, ld >= n and a multiple of 4; x and y must not
+ * overlap).  One launch per operator stage for all vectors, each vector on
+ * its own share of the CTAs (used for the directions of a deflated warm start). */
+#define FEWHA_MAX_MULTI 8
+int fewha_apply_op_multi(void *handle, const void *x, long ldx, void *y, long ldy, int nvec, cudaStream_t stream);
+
 /* b = W^{-T} A^T C_eta^{-1} s (right-hand side of Eq. fewha; Algorithm 3). */
 int fewha_rhs(void *handle, const void *s, void *b, cudaStream_t stream);
 
@@ -183,6 +190,69 @@ int fewha_batch_ctas(const void *batch, int *ctas_out);
 int fewha_batch_solve(void *batch, const void *const *slopes, void *const *c, const fewha_state *states,
                       const fewha_solve_opts *opts, fewha_stats *stats_dev, cudaStream_t stream);
 void fewha_batch_destroy(void *batch);
+
+/* --- Learned warm start (not in the paper) ----------------------------------
+ * A small convolutional network over the last frames' layer coefficients
+ * predicts the next time step's warm-start increment and deflation
+ * directions; PCG stays the solver.  These calls are its building blocks: the
+ * network's forward and backward passes, its loss and optimizer, and the
+ * deflated warm start that combines the predicted directions with the new
+ * data.  FP32 device tensors addressed as base + b*bs + c*cs + y*W + x (batch
+ * and channel strides in elements, so that the layers of one grid size form a
+ * batch and a channel may be a whole coefficient vector; strides may be
+ * negative).  All calls are asynchronous on `s` and return FEWHA_ERR_ARG for
+ * NULL pointers or sizes below 1, FEWHA_ERR_CUDA if a launch fails.
+ *
+ * fewha_conv3x3_fwd: out[b][co] = act(bias[co] + sum_ci w[co][ci] (*) in[b][ci]),
+ *   3x3 cross-correlation with zero padding; act = ReLU if relu != 0; w is
+ *   Cout x Cin x 3 x 3 (row-major), bias may be NULL.
+ * fewha_conv3x3_bwd_data: gin = adjoint of that convolution (no bias, no act)
+ *   applied to gout.
+ * fewha_conv3x3_bwd_weight: gw (Cout x Cin x 9) and gb (Cout) of
+ *   sum_b,co,y,x gout * out; written, or added when accumulate != 0;
+ *   workspace: fewha_conv3x3_wgrad_workspace(...) floats; deterministic.
+ * fewha_relu_bwd: g[i] = 0 where act[i] <= 0 (act = the ReLU output).
+ * fewha_mse_grad: grad = 2 (pred - target) / n; loss_part512[512] partial sums
+ *   of (pred - target)^2 (the loss is their sum / n).
+ * fewha_adam_step: Adam (Kingma & Ba) with bias correction; step = 1, 2, ...
+ * fewha_scale: y = x sqrt(s) (mode 0), x / sqrt(s) (mode 1), y += x / sqrt(s)
+ *   (mode 2), elementwise; s > 0 (with s = alpha D this whitens coefficients
+ *   by the prior).
+ * fewha_learned_targets: targets5 (5 x n) from two consecutive solutions:
+ *   t0 = (c_next - c_cur) sqrt(scale), t_k = t0 on coefficients with
+ *   group[i] == k and 0 elsewhere (k = 1..4).
+ * fewha_deflate_warm_start: Galerkin correction of the warm start over nd
+ *   directions D (nd x n, leading dimension ldd) with Q = M D (ldq):
+ *   r0 = (b - b_prev) + r_prev (the warm restart of Algorithm 3),
+ *   w = (D^T Q)^{-1} D^T r0 in FP64 with a Cholesky factorisation that drops
+ *   directions whose pivot is below 1e-10 of their diagonal.  Taken only when
+ *   ||r0 - Q w|| < ||r0||; then c += D w, r_prev <- r0 - Q w, b_prev <- b, so
+ *   that the next fewha_solve starts from the corrected residual; otherwise
+ *   c, b_prev and r_prev are left as they are (the plain warm start).
+ *   r0_work: n floats; work: FEWHA_DEFLATE_WORK_DOUBLES; info:
+ *   FEWHA_DEFLATE_INFO_DOUBLES, info[0] taken (0/1), [1] ||r0 - Q w||,
+ *   [2] ||r0||, [3] directions kept, [4..4+nd) w.  1 <= nd <= FEWHA_MAX_DEFLATE. */
+#define FEWHA_MAX_DEFLATE 6
+#define FEWHA_DEFLATE_WORK_DOUBLES 4096
+#define FEWHA_DEFLATE_INFO_DOUBLES 16
+int fewha_conv3x3_fwd(const float *in, long in_bs, long in_cs, int Cin, const float *w, const float *bias,
+                      float *out, long out_bs, long out_cs, int Cout, int B, int H, int W, int relu, cudaStream_t s);
+int fewha_conv3x3_bwd_data(const float *gout, long gout_bs, long gout_cs, int Cout, const float *w, float *gin,
+                           long gin_bs, long gin_cs, int Cin, int B, int H, int W, cudaStream_t s);
+long fewha_conv3x3_wgrad_workspace(int Cin, int Cout, int B, int H, int W);
+int fewha_conv3x3_bwd_weight(const float *in, long in_bs, long in_cs, int Cin, const float *gout, long gout_bs,
+                             long gout_cs, int Cout, int B, int H, int W, float *gw, float *gb, int accumulate,
+                             float *workspace, cudaStream_t s);
+int fewha_relu_bwd(const float *act, float *g, long n, cudaStream_t s);
+int fewha_mse_grad(const float *pred, const float *target, float *grad, long n, double *loss_part512, cudaStream_t s);
+int fewha_adam_step(float *param, const float *grad, float *m, float *v, long n, float lr, float beta1, float beta2,
+                    float eps, int step, cudaStream_t s);
+int fewha_scale(const float *x, const float *s_, float *y, long n, int mode, cudaStream_t s);
+int fewha_learned_targets(const float *c_next, const float *c_cur, const float *scale, const signed char *group,
+                          float *targets5, long n, cudaStream_t s);
+int fewha_deflate_warm_start(const float *b, const float *D, long ldd, const float *Q, long ldq, int nd, float *c,
+                             float *b_prev, float *r_prev, long n, float *r0_work, double *work, double *info,
+                             cudaStream_t s);
 
 /* Time limit of every device-side wait of the persistent solver (grid
  * barriers), in ns; default 1 s.  A wait that runs out records

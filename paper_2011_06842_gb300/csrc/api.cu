@@ -179,6 +179,19 @@ int fewha_apply_op(void *handle, const void *x, void *y, cudaStream_t stream)
     return static_cast<Handle *>(handle)->w()->apply(x, y, stream);
 }
 
+int fewha_apply_op_multi(void *handle, const void *x, long ldx, void *y, long ldy, int nvec, cudaStream_t stream)
+{
+    if (!handle || !x || !y || nvec < 1 || nvec > FEWHA_MAX_MULTI || !aligned16(x) || !aligned16(y)) return FEWHA_ERR_ARG;
+    Handle *h = static_cast<Handle *>(handle);
+    const long n = h->plan.n;
+    if (ldx < n || ldy < n || (ldx % 4) || (ldy % 4)) return FEWHA_ERR_ARG;
+    const size_t es = h->w()->precision_id() == FEWHA_F64 ? 8 : 4;
+    const char *xb = static_cast<const char *>(x), *yb = static_cast<const char *>(y);
+    const char *xe = xb + ((nvec - 1) * ldx + n) * es, *ye = yb + ((nvec - 1) * ldy + n) * es;
+    if (xb < ye && yb < xe) return FEWHA_ERR_ARG;  // x and y must not overlap
+    return h->w()->apply_multi(x, ldx, y, ldy, nvec, stream);
+}
+
 int fewha_rhs(void *handle, const void *s, void *b, cudaStream_t stream)
 {
     if (!handle || !s || !b || !aligned16(b)) return FEWHA_ERR_ARG;

@@ -66,6 +66,57 @@ __global__ void __launch_bounds__(kThreads, 1) k_fdwt(Args<T, S> A)
     });
 }
 
+// --- y_v = M x_v for several vectors at once --------------------------------
+// Vector v is applied by CTAs [v*per, (v+1)*per) with its own scratch
+// buffers, so the per-layer transforms of all vectors run side by side.
+constexpr int kMaxVec = FEWHA_MAX_MULTI;
+
+template <typename T, typename S>
+struct MultiArgs {
+    Args<T, S> a[kMaxVec];
+    int per;
+};
+
+template <typename T, typename S>
+__global__ void __launch_bounds__(kThreads, 1) k_multi_idwt(const __grid_constant__ MultiArgs<T, S> M)
+{
+    const Args<T, S> &A = M.a[blockIdx.x / M.per];
+    constexpr int W = VW<T>::W;
+    layer_idwt<T, S>(A, dyn_smem<T>(), [&](long e, T (&x)[W]) { vld(A.x + e, x); }, [](int, const T *) {});
+}
+
+template <typename T, typename S>
+__global__ void __launch_bounds__(kThreads, 1) k_multi_wfs(const __grid_constant__ MultiArgs<T, S> M)
+{
+    const Args<T, S> &A = M.a[blockIdx.x / M.per];
+    __shared__ double sred[kSred];
+    typename AccT<T>::type acc[1] = {wfs_phase<T, S, false>(A, dyn_smem<T>())};
+    const int slots[1] = {kSlotB};
+    block_partials<1>(acc, A.part, slots, sred, A.vrank());
+}
+
+template <typename T, typename S>
+__global__ void __launch_bounds__(kThreads, 1) k_multi_gather(const __grid_constant__ MultiArgs<T, S> M)
+{
+    const Args<T, S> &A = M.a[blockIdx.x / M.per];
+    band_gather<T, S>(A, dyn_smem<T>());
+}
+
+template <typename T, typename S>
+__global__ void __launch_bounds__(kThreads, 1) k_multi_fdwt(const __grid_constant__ MultiArgs<T, S> M)
+{
+    const Args<T, S> &A = M.a[blockIdx.x / M.per];
+    constexpr int W = VW<T>::W;
+    layer_fdwt<T, S>(A, dyn_smem<T>(), [&](long e, const T (&v)[W]) {
+        T y[W], x[W], ad[W];
+        vld(A.x + e, x);
+        vld_nc(A.geo.alpha_d + e, ad);
+#pragma unroll
+        for (int i = 0; i < W; i++) y[i] = v[i] + ad[i] * x[i];
+        vst(A.y + e, y);
+    });
+}
+
 // --- solver phases, one kernel each (FEWHA_LAUNCH_PHASES) -------------------
 #define FEWHA_PHASE_GUARD                                             \
     __shared__ Scal sc;                                               \
@@ -289,6 +340,8 @@ struct ImplBase {
     virtual int init(int grid) = 0;
     virtual int get_invJ(double *host) const = 0;
     virtual int apply(const void *x, void *y, cudaStream_t s) = 0;
+    // y_v = M x_v for v < nvec (x_v = x + v*ldx, y_v = y + v*ldy), nvec <= kMaxVec
+    virtual int apply_multi(const void *x, long ldx, void *y, long ldy, int nvec, cudaStream_t s) = 0;
     virtual int rhs(const void *sl, void *b, cudaStream_t s) = 0;
     virtual int solve(const void *sl, void *c, const fewha_state *st, const fewha_solve_opts *o,
                       fewha_stats *stats, cudaStream_t s) = 0;
@@ -320,6 +373,8 @@ struct Impl : ImplBase {
     int ncta = 1;
     size_t smem = 0;
     std::vector<void *> owned;
+    unsigned char *multi_buf = nullptr;  // scratch of apply_multi (allocated on first use)
+    size_t multi_stride = 0;
 
     size_t sm_fixed = 0;  // dynamic shared memory of every phase but the WFS tiles
 
@@ -531,6 +586,9 @@ struct Impl : ImplBase {
         CK(setattr((const void *)k_solve_persistent<T, S>));
         CK(cudaFuncSetAttribute((const void *)k_solve_batched<T, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 200 * 1024));
+        for (const void *f : {(const void *)k_multi_idwt<T, S>, (const void *)k_multi_wfs<T, S>,
+                              (const void *)k_multi_gather<T, S>, (const void *)k_multi_fdwt<T, S>})
+            CK(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
         int per_sm = 0;
         CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve_persistent<T, S>, kThreads, smem));
         if (per_sm < 1) return FEWHA_ERR_CUDA;
@@ -579,6 +637,51 @@ struct Impl : ImplBase {
         k_wfs<T, S, false><<<ncta, kThreads, smem, s>>>(A);
         k_gather<T, S><<<ncta, kThreads, smem, s>>>(A);
         k_fdwt<T, S, false><<<ncta, kThreads, smem, s>>>(A);
+        return launch_check();
+    }
+
+    int apply_multi(const void *x, long ldx, void *y, long ldy, int nvec, cudaStream_t s) override
+    {
+        static_assert(sizeof(MultiArgs<T, S>) <= 32000, "kernel parameter size");
+        if (nvec < 1 || nvec > kMaxVec || ldx < P.n || ldy < P.n) return FEWHA_ERR_ARG;
+        auto up256 = [](size_t v) { return (v + 255) & ~(size_t)255; };
+        if (!multi_buf) {
+            multi_stride = up256((size_t)P.n * sizeof(S)) + up256((size_t)P.G * P.m * P.m * sizeof(S)) +
+                           up256((size_t)P.n * sizeof(T));
+            if (alloc(multi_stride * kMaxVec, &multi_buf)) return FEWHA_ERR_NOMEM;
+        }
+        const int per = std::max(1, ncta / nvec);
+        int ty, tx;
+        if (tiles_for(per, &ty, &tx)) return FEWHA_ERR_GEOMETRY;
+        const size_t sm = smem_for(ty, tx);
+        MultiArgs<T, S> M{};
+        M.per = per;
+        for (int v = 0; v < nvec; v++) {
+            Args<T, S> A = base;
+            unsigned char *b = multi_buf + (size_t)v * multi_stride;
+            A.nodal = reinterpret_cast<S *>(b);
+            A.psi = reinterpret_cast<S *>(b + up256((size_t)P.n * sizeof(S)));
+            A.u = reinterpret_cast<T *>(b + up256((size_t)P.n * sizeof(S)) + up256((size_t)P.G * P.m * P.m * sizeof(S)));
+            A.part = base.part + (size_t)v * per;  // disjoint partial-sum columns
+            A.x = static_cast<const T *>(x) + (size_t)v * ldx;
+            A.y = static_cast<T *>(y) + (size_t)v * ldy;
+            A.cta0 = v * per;
+            A.ncta = per;
+            A.geo.tile_y = ty;
+            A.geo.tile_x = tx;
+            A.geo.tiles_y = (P.m + ty - 1) / ty;
+            A.geo.tiles_x = (P.m + tx - 1) / tx;
+            A.smem_bytes = sm;
+            A.trace = nullptr;
+            A.trace_cap = 0;
+            M.a[v] = A;
+        }
+        CK(cudaMemsetAsync(base.rec, 0, offsetof(Record, rz), s));
+        const int grid = per * nvec;
+        k_multi_idwt<T, S><<<grid, kThreads, sm, s>>>(M);
+        k_multi_wfs<T, S><<<grid, kThreads, sm, s>>>(M);
+        k_multi_gather<T, S><<<grid, kThreads, sm, s>>>(M);
+        k_multi_fdwt<T, S><<<grid, kThreads, sm, s>>>(M);
         return launch_check();
     }
 

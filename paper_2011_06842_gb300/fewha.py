@@ -106,6 +106,26 @@ def load_library(path=LIB_PATH):
     lib.fewha_batch_solve.restype = C.c_int
     lib.fewha_batch_destroy.argtypes = [vp]
     lib.fewha_batch_destroy.restype = None
+    lib.fewha_apply_op_multi.argtypes = [vp, vp, C.c_long, vp, C.c_long, C.c_int, vp]
+    lib.fewha_apply_op_multi.restype = C.c_int
+    # learned warm start (float pointers as void*, strides and sizes as long/int)
+    L, I, F = C.c_long, C.c_int, C.c_float
+    learned = {
+        "fewha_conv3x3_fwd": [vp, L, L, I, vp, vp, vp, L, L, I, I, I, I, I, vp],
+        "fewha_conv3x3_bwd_data": [vp, L, L, I, vp, vp, L, L, I, I, I, I, vp],
+        "fewha_conv3x3_bwd_weight": [vp, L, L, I, vp, L, L, I, I, I, I, vp, vp, I, vp, vp],
+        "fewha_relu_bwd": [vp, vp, L, vp],
+        "fewha_mse_grad": [vp, vp, vp, L, vp, vp],
+        "fewha_adam_step": [vp, vp, vp, vp, L, F, F, F, F, I, vp],
+        "fewha_scale": [vp, vp, vp, L, I, vp],
+        "fewha_learned_targets": [vp, vp, vp, vp, vp, L, vp],
+        "fewha_deflate_warm_start": [vp, vp, L, vp, L, I, vp, vp, vp, L, vp, vp, vp, vp],
+    }
+    for name, args in learned.items():
+        getattr(lib, name).argtypes = args
+        getattr(lib, name).restype = C.c_int
+    lib.fewha_conv3x3_wgrad_workspace.argtypes = [I, I, I, I, I]
+    lib.fewha_conv3x3_wgrad_workspace.restype = C.c_long
     lib.fewha_strerror.argtypes = [C.c_int]
     lib.fewha_strerror.restype = C.c_char_p
     for name in ("fewha_create", "fewha_get_prior", "fewha_get_precond", "fewha_apply_op",
@@ -120,7 +140,11 @@ def exported_symbols():
     return ["fewha_create", "fewha_destroy", "fewha_n_unknowns", "fewha_n_slopes",
             "fewha_layer_spacing", "fewha_get_prior", "fewha_get_precond", "fewha_apply_op",
             "fewha_rhs", "fewha_solve", "fewha_set_timeout", "fewha_set_trace", "fewha_apply_op_noalloc", "fewha_batch_create",
-            "fewha_batch_ctas", "fewha_batch_solve", "fewha_batch_destroy", "fewha_strerror"]
+            "fewha_batch_ctas", "fewha_batch_solve", "fewha_batch_destroy", "fewha_strerror",
+            "fewha_apply_op_multi", "fewha_conv3x3_fwd", "fewha_conv3x3_bwd_data",
+            "fewha_conv3x3_wgrad_workspace", "fewha_conv3x3_bwd_weight", "fewha_relu_bwd",
+            "fewha_mse_grad", "fewha_adam_step", "fewha_scale", "fewha_learned_targets",
+            "fewha_deflate_warm_start"]
 
 
 def make_geometry(geom, noise_w, precision="f64", tile=0, grid=0) -> GEOMETRY:
@@ -247,6 +271,17 @@ class Fewha:
         self._check(self.lib.fewha_apply_op_noalloc(self._h, self._vec(x, self.n, self.dtype, "x"),
                                                     self._vec(y, self.n, self.dtype, "y"),
                                                     _stream_ptr(self._torch)), "fewha_apply_op_noalloc")
+        return y
+
+    def apply_op_multi(self, x, out=None):
+        """Y[v] = M X[v] for the rows of a (nvec, ld) tensor, one launch per stage."""
+        torch = self._torch
+        if x.dim() != 2 or x.dtype != self.dtype or x.device.type != "cuda" or x.stride(1) != 1:
+            raise TypeError("x must be a CUDA (nvec, ld) tensor of %s with unit inner stride" % self.dtype)
+        y = out if out is not None else torch.empty((x.shape[0], self.n), dtype=self.dtype, device=self.device)
+        self._check(self.lib.fewha_apply_op_multi(self._h, C.c_void_p(x.data_ptr()), x.stride(0),
+                                                  C.c_void_p(y.data_ptr()), y.stride(0), x.shape[0],
+                                                  _stream_ptr(torch)), "fewha_apply_op_multi")
         return y
 
     def rhs(self, s, out=None):

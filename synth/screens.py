@@ -93,12 +93,20 @@ class FrozenFlowSensors:
                 + fv * ((1 - fu) * S[iv1, iu] + fu * S[iv1, iu1]))
 
     def _phase(self, g, frame, x, y):
-        tot = torch.zeros_like(x)
+        """Phase at points (x, y) seen from guide star g; `frame` is an int or a
+        1-D tensor of frame indices (then a leading frame axis is added)."""
+        if isinstance(frame, torch.Tensor):
+            sh = (-1,) + (1,) * x.dim()
+            fr = frame.to(torch.float64).reshape(sh)
+            x, y = x.unsqueeze(0), y.unsqueeze(0)
+        else:
+            fr = frame
+        tot = 0.0
         for l, lay in enumerate(self.geom.layers):
             s = (1.0 - lay.h / g.H) if g.H > 0 else 1.0
             wx, wy = self.wind[l]
-            ox = g.theta_x * lay.h - wx * frame * self.dt
-            oy = g.theta_y * lay.h - wy * frame * self.dt
+            ox = g.theta_x * lay.h - wx * fr * self.dt
+            oy = g.theta_y * lay.h - wy * fr * self.dt
             tot = tot + self._sample(l, s * x + ox, s * y + oy)
         return tot
 
@@ -112,6 +120,17 @@ class FrozenFlowSensors:
             sy = Hh[1:, :] - Hh[:-1, :]
             out += [sx.reshape(-1), sy.reshape(-1)]
         return torch.cat(out)
+
+    def clean_slopes_many(self, frames) -> torch.Tensor:
+        """clean_slopes for a 1-D tensor of frame indices: (len(frames), n_slopes)."""
+        out = []
+        for g in self.geom.gs:
+            V = self._phase(g, frames, self.vx, self.vy).mean(-1)
+            Hh = self._phase(g, frames, self.hx, self.hy).mean(-1)
+            sx = V[:, :, 1:] - V[:, :, :-1]
+            sy = Hh[:, 1:, :] - Hh[:, :-1, :]
+            out += [sx.reshape(len(frames), -1), sy.reshape(len(frames), -1)]
+        return torch.cat(out, dim=1)
 
     def noise_sigma(self) -> np.ndarray:
         """sigma_g = rms of the noise-free slopes of g on lit subapertures / SNR."""
@@ -138,4 +157,21 @@ class FrozenFlowSensors:
                 s = s + sig_vec * torch.randn(s.shape, generator=gen, dtype=torch.float64,
                                               device=self.device)
             frames[t] = s.to(dtype)
+        return frames, 1.0 / sig ** 2
+
+    def sequence_chunked(self, n_frames, seed=1, dtype=torch.float32, first_frame=0, chunk=64):
+        """Like `sequence` (same sky and noise model) for long runs: frames
+        are produced `chunk` at a time and the noise of a chunk is drawn in one
+        call, so the noise values differ from `sequence` for the same seed."""
+        sig = self.noise_sigma()
+        gen = torch.Generator(device=self.device)
+        gen.manual_seed(seed)
+        ns2 = self.geom.n_sub ** 2
+        sig_vec = torch.tensor(np.repeat(sig, 2 * ns2), dtype=torch.float64, device=self.device)
+        frames = torch.empty((n_frames, self.geom.n_slopes), dtype=dtype, device=self.device)
+        for t0 in range(0, n_frames, chunk):
+            f = torch.arange(first_frame + t0, first_frame + min(n_frames, t0 + chunk), device=self.device)
+            s = self.clean_slopes_many(f)
+            s = s + sig_vec * torch.randn(s.shape, generator=gen, dtype=torch.float64, device=self.device)
+            frames[t0:t0 + len(f)] = s.to(dtype)
         return frames, 1.0 / sig ** 2
