@@ -51,6 +51,11 @@ def parse():
     p.add_argument("--grid", type=int, default=0)
     p.add_argument("--no-batched", action="store_true", help="skip the 64-instance batched measurement")
     p.add_argument("--batched-steps", type=int, default=20)
+    p.add_argument("--learned", action="store_true",
+                   help="learned warm start study instead of the time-step benchmark")
+    p.add_argument("--learned-train", type=int, default=20000, help="training frames")
+    p.add_argument("--learned-eval", type=int, default=500, help="held-out frames")
+    p.add_argument("--epochs", type=int, default=2)
     return p.parse_args()
 
 
@@ -443,8 +448,68 @@ def run_reference(args):
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def run_learned(args):
+    """Learned warm start vs the plain warm start of Algorithm 3 (both with
+    augmented PCG, FP32): train on frames the plain method solves, then run
+    both loops over held-out frames to the same relative residual."""
+    import numpy as np
+    import torch
+    from paper_2011_06842_gb300 import Fewha, build, learned
+    from synth import FrozenFlowSensors, configs
+    build.build()
+    geom = configs.get(args.config)
+    geom.snr = args.snr if args.snr else 100.0
+    geom.k_recycle = args.k
+    sim = FrozenFlowSensors(geom, seed=300, device="cuda")
+    t0 = time.time()
+    st, w = sim.sequence_chunked(args.learned_train, seed=301)
+    se, _ = sim.sequence_chunked(args.learned_eval, seed=302, first_frame=10 * args.learned_train + 1000)
+    t_slopes = time.time() - t0
+    f = Fewha(geom, w, "f32")
+    flush = None if args.no_flush else torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    clk = Clocks(0)
+    res = learned.study(f, geom, st, se, rtol=args.rtol, max_iter=args.max_iter, epochs=args.epochs,
+                        kcap=args.k, flush=flush, log=lambda m: print(m, file=sys.stderr, flush=True))
+    clocks = clk.stop()
+    lw = res.pop("learner")
+
+    def ev_us(fn, reps=20):
+        for _ in range(3):
+            fn()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) * 1e3 / reps
+
+    x = torch.randn(learned.N_DIR, f.n, device="cuda")
+    y = torch.empty_like(x)
+    cost = {"rhs_us": ev_us(lambda: f.rhs(se[0], out=y[0])),
+            "network_forward_us": ev_us(lambda: lw.net.forward(lw.ring[4].data_ptr(), -f.n, y)),
+            "apply_multi5_us": ev_us(lambda: f.apply_op_multi(x, out=y)),
+            "apply_single_us": ev_us(lambda: f.apply_op(x[0], out=y[1]))}
+    out = {"metric": METRIC, "mode": "learned warm start", "unit": "frames/s",
+           "value": 1e6 / res["learned"]["us"], "plain_value": 1e6 / res["plain"]["us"],
+           "higher_is_better": True, "n_gpus": 1, "dtype": "f32",
+           "data": "synthetic: seeded von Karman frozen-flow screens seen by SH sensors, SNR %g" % geom.snr,
+           "config": {"workload": workload_name(geom, args) + ", learned warm start",
+                      "rtol": args.rtol, "max_iter": args.max_iter, "k_recycle": args.k,
+                      "network": "3x3 conv 4-32-32-5, ReLU", "train_frames": args.learned_train,
+                      "eval_frames": args.learned_eval, "epochs": args.epochs,
+                      "l2": "flushed before every frame" if flush is not None else "not flushed"},
+           "slopes_generation_s": t_slopes, "study": res, "cost_breakdown": cost, "clocks": clocks}
+    f.close()
+    return out
+
+
 def main():
     args = parse()
+    if args.learned:
+        print(json.dumps(run_learned(args)))
+        return
     if args.impl == "reference":
         out = run_reference(args)
     else:

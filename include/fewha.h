@@ -191,6 +191,18 @@ int fewha_batch_solve(void *batch, const void *const *slopes, void *const *c, co
                       const fewha_solve_opts *opts, fewha_stats *stats_dev, cudaStream_t stream);
 void fewha_batch_destroy(void *batch);
 
+/* Fixed-buffer form for CUDA-graph capture.  fewha_batch_bind writes (and
+ * synchronously uploads) the argument table of one batched time step over
+ * fixed buffers, with the same arguments and checks as fewha_batch_solve;
+ * fewha_batch_launch then runs that time step on `stream` with no host work
+ * and no host-to-device copy (two kernel launches: flag reset and the
+ * cooperative solve), so it can be captured once into a CUDA graph and
+ * replayed every frame after the caller has written the new slopes into the
+ * bound slope buffers.  FEWHA_ERR_ARG if nothing is bound. */
+int fewha_batch_bind(void *batch, const void *const *slopes, void *const *c, const fewha_state *states,
+                     const fewha_solve_opts *opts, fewha_stats *stats_dev);
+int fewha_batch_launch(void *batch, cudaStream_t stream);
+
 /* --- Learned warm start (not in the paper) ----------------------------------
  * A small convolutional network over the last frames' layer coefficients
  * predicts the next time step's warm-start increment and deflation

@@ -34,6 +34,8 @@ struct Batch {
     std::vector<ImplBase *> impl;
     std::vector<int> cta0, ncta, ty, tx;
     void *d_args = nullptr;
+    void *d_bound = nullptr;  // argument table of fewha_batch_bind (fixed buffers, graph replay)
+    bool bound = false;
     int *d_map = nullptr;
     static constexpr int kRing = 4;  // pinned staging copies of the argument table
     void *h_args[kRing] = {};
@@ -42,6 +44,7 @@ struct Batch {
     ~Batch()
     {
         cudaFree(d_args);
+        cudaFree(d_bound);
         cudaFree(d_map);
         for (int i = 0; i < kRing; i++) {
             if (h_args[i]) cudaFreeHost(h_args[i]);
@@ -320,6 +323,41 @@ int fewha_batch_solve(void *batch, const void *const *slopes, void *const *c, co
         return FEWHA_ERR_CUDA;
     if (cudaEventRecord(b->ev[slot], stream) != cudaSuccess) return FEWHA_ERR_CUDA;
     return b->impl[0]->launch_batched(b->d_args, b->d_map, b->n, b->total, b->smem, stream);
+}
+
+int fewha_batch_bind(void *batch, const void *const *slopes, void *const *c, const fewha_state *states,
+                     const fewha_solve_opts *opts, fewha_stats *stats_dev)
+{
+    if (!batch || !slopes || !c || !states || !opts) return FEWHA_ERR_ARG;
+    Batch *b = static_cast<Batch *>(batch);
+    if (opts->max_iter < 1 || opts->max_iter > FEWHA_MAX_ITER || !(opts->rtol >= 0)) return FEWHA_ERR_ARG;
+    if (opts->recycle_mode != FEWHA_RECYCLE_LAST && opts->recycle_mode != FEWHA_RECYCLE_ALL) return FEWHA_ERR_ARG;
+    std::vector<unsigned char> h(b->asz * b->n);
+    for (int i = 0; i < b->n; i++) {
+        const fewha_state *st = states + i;
+        if (!slopes[i] || !c[i] || !st->b_prev || !st->r_prev || !st->basis_P || !st->basis_Q || !st->basis_pq ||
+            !st->meta || st->k_cap < 1 || st->k_cap > FEWHA_MAX_K)
+            return FEWHA_ERR_ARG;
+        if (!aligned16(c[i]) || !aligned16(st->b_prev) || !aligned16(st->r_prev) || !aligned16(st->basis_P) ||
+            !aligned16(st->basis_Q))
+            return FEWHA_ERR_ARG;
+        int r = b->impl[i]->batch_args(h.data() + b->asz * i, slopes[i], c[i], st, opts,
+                                       stats_dev ? stats_dev + i : nullptr, b->cta0[i], b->ncta[i], b->ty[i], b->tx[i],
+                                       b->smem);
+        if (r) return r;
+    }
+    if (!b->d_bound && cudaMalloc(&b->d_bound, b->asz * b->n) != cudaSuccess) return FEWHA_ERR_NOMEM;
+    if (cudaMemcpy(b->d_bound, h.data(), b->asz * b->n, cudaMemcpyHostToDevice) != cudaSuccess) return FEWHA_ERR_CUDA;
+    b->bound = true;
+    return FEWHA_OK;
+}
+
+int fewha_batch_launch(void *batch, cudaStream_t stream)
+{
+    if (!batch) return FEWHA_ERR_ARG;
+    Batch *b = static_cast<Batch *>(batch);
+    if (!b->bound) return FEWHA_ERR_ARG;
+    return b->impl[0]->launch_batched(b->d_bound, b->d_map, b->n, b->total, b->smem, stream);
 }
 
 void fewha_batch_destroy(void *batch)

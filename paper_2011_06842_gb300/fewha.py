@@ -104,6 +104,10 @@ def load_library(path=LIB_PATH):
     lib.fewha_batch_ctas.restype = C.c_int
     lib.fewha_batch_solve.argtypes = [vp, C.POINTER(vp), C.POINTER(vp), C.POINTER(STATE), C.POINTER(OPTS), vp, vp]
     lib.fewha_batch_solve.restype = C.c_int
+    lib.fewha_batch_bind.argtypes = [vp, C.POINTER(vp), C.POINTER(vp), C.POINTER(STATE), C.POINTER(OPTS), vp]
+    lib.fewha_batch_bind.restype = C.c_int
+    lib.fewha_batch_launch.argtypes = [vp, vp]
+    lib.fewha_batch_launch.restype = C.c_int
     lib.fewha_batch_destroy.argtypes = [vp]
     lib.fewha_batch_destroy.restype = None
     lib.fewha_apply_op_multi.argtypes = [vp, vp, C.c_long, vp, C.c_long, C.c_int, vp]
@@ -141,6 +145,7 @@ def exported_symbols():
             "fewha_layer_spacing", "fewha_get_prior", "fewha_get_precond", "fewha_apply_op",
             "fewha_rhs", "fewha_solve", "fewha_set_timeout", "fewha_set_trace", "fewha_apply_op_noalloc", "fewha_batch_create",
             "fewha_batch_ctas", "fewha_batch_solve", "fewha_batch_destroy", "fewha_strerror",
+            "fewha_batch_bind", "fewha_batch_launch",
             "fewha_apply_op_multi", "fewha_conv3x3_fwd", "fewha_conv3x3_bwd_data",
             "fewha_conv3x3_wgrad_workspace", "fewha_conv3x3_bwd_weight", "fewha_relu_bwd",
             "fewha_mse_grad", "fewha_adam_step", "fewha_scale", "fewha_learned_targets",
@@ -398,6 +403,42 @@ class FewhaBatch:
         if st != 0:
             raise FewhaError(st, "fewha_batch_solve")
         return stats
+
+    def bind(self, slopes, cs, states, max_iter, rtol=0.0, augmented=True, recycle_all=False, stats=None):
+        """Fixes the buffers of launch(): every launch solves one time step of every
+        instance from the current contents of `slopes` into `cs` (fewha_batch_bind)."""
+        n = self.n
+        for f, sl, c in zip(self.fewhas, slopes, cs):
+            f._vec(sl, f.n_slopes, f.slope_dtype, "s")
+            f._vec(c, f.n, f.dtype, "c")
+        sp = (C.c_void_p * n)(*[t.data_ptr() for t in slopes])
+        cp = (C.c_void_p * n)(*[t.data_ptr() for t in cs])
+        stt = (STATE * n)(*[s_.c_struct for s_ in states])
+        o = OPTS(int(max_iter), float(rtol), 1 if augmented else 0, RECYCLE_ALL if recycle_all else RECYCLE_LAST,
+                 LAUNCH_PERSISTENT, 0)
+        self._bound = (slopes, cs, states, stats if stats is not None else self.new_stats())
+        st = self.lib.fewha_batch_bind(self._b, sp, cp, stt, C.byref(o), C.c_void_p(self._bound[3].data_ptr()))
+        if st != 0:
+            raise FewhaError(st, "fewha_batch_bind")
+        return self._bound[3]
+
+    def launch(self):
+        """One time step over the bound buffers (no host work; capturable)."""
+        st = self.lib.fewha_batch_launch(self._b, _stream_ptr(self._torch))
+        if st != 0:
+            raise FewhaError(st, "fewha_batch_launch")
+
+    def capture_graph(self):
+        """A CUDA graph of one launch() (replay() after writing the bound slopes)."""
+        torch = self._torch
+        g = torch.cuda.CUDAGraph()
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            with torch.cuda.graph(g, stream=s):
+                self.launch()
+        torch.cuda.current_stream().wait_stream(s)
+        return g
 
     def read_stats(self, stats):
         raw = stats.cpu().numpy().tobytes()

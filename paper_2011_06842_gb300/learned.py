@@ -341,13 +341,14 @@ class LearnedWarmStart:
         return bool(i[0]), float(i[1]), float(i[2]), int(i[3])
 
 
-def solve_sequence(f, slopes, rtol, max_iter, kcap=8, augmented=True, learned=None, record=None):
+def solve_sequence(f, slopes, rtol, max_iter, kcap=8, augmented=True, learned=None, record=None, flush=None):
     """Runs the reconstructor loop over slopes (T, n_slopes) with fresh state.
     learned: a LearnedWarmStart used for the deflated warm start (None: the
     plain warm start of Algorithm 3).  record: optional (T, n) tensor that
     receives every solution.  Returns per-frame iterations, rel_res, device
     microseconds (CUDA events around prepare + solve) and, for the learned
-    loop, the deflation info."""
+    loop, the deflation info.  flush: optional tensor larger than L2, zeroed
+    before every frame (outside the timed region)."""
     torch = f._torch
     T = slopes.shape[0]
     c = torch.zeros(f.n, dtype=f.dtype, device=f.device)
@@ -358,6 +359,8 @@ def solve_sequence(f, slopes, rtol, max_iter, kcap=8, augmented=True, learned=No
     if learned is not None:
         learned.reset()
     for t in range(T):
+        if flush is not None:
+            flush.zero_()
         ev[t][0].record()
         used = learned.prepare(slopes[t], c, st) if learned is not None else False
         f.solve(slopes[t], c, st, max_iter, rtol=rtol, augmented=augmented, stats=stats[t])
@@ -382,7 +385,7 @@ def solve_sequence(f, slopes, rtol, max_iter, kcap=8, augmented=True, learned=No
 
 
 def study(f, geom, slopes_train, slopes_eval, rtol, max_iter=1000, epochs=2, lr=1e-3, kcap=8, seed=0,
-          skip=10, log=None):
+          skip=10, log=None, flush=None):
     """Trains the network on the solutions the plain method produces for
     slopes_train, then runs the plain and the learned loop over slopes_eval.
     Returns a summary dict (means over the evaluation frames after `skip`)."""
@@ -399,8 +402,8 @@ def study(f, geom, slopes_train, slopes_eval, rtol, max_iter=1000, epochs=2, lr=
     loss0, loss1 = lw.train(C_frames[skip:], epochs=epochs, lr=lr, seed=seed, log=log)
     torch.cuda.synchronize()
     t_train = time.time() - t0
-    plain = solve_sequence(f, slopes_eval, rtol, max_iter, kcap)
-    lrn = solve_sequence(f, slopes_eval, rtol, max_iter, kcap, learned=lw)
+    plain = solve_sequence(f, slopes_eval, rtol, max_iter, kcap, flush=flush)
+    lrn = solve_sequence(f, slopes_eval, rtol, max_iter, kcap, learned=lw, flush=flush)
     # the learned loop's own cost: network, M D and the projection (prepare() alone)
     sl = slice(skip, None)
 

@@ -71,3 +71,35 @@ def test_batched_rtol_instances_finish_independently(lib):
             assert r["iterations"] == r2["iterations"]
             assert rel(c.cpu().numpy(), c2.cpu().numpy()) < 1e-9
     batch.close()
+
+
+def test_batched_graph_replay_matches_oracle(lib):
+    """One batched time step captured once in a CUDA graph over fixed slope
+    buffers (fewha_batch_bind / fewha_batch_launch) and replayed every frame
+    after the new slopes are copied in: each instance equals the oracle."""
+    names = ["tiny", "mixed", "medium"]
+    frames = 3
+    inst = []
+    for i, name in enumerate(names):
+        geom = configs.get(name)
+        s, w = FrozenFlowSensors(geom, seed=80 + i).sequence(frames, seed=90 + i)
+        o = Oracle(geom, w)
+        f = lib.Fewha(geom, w, "f32")
+        inst.append((o, o.new_state(8), f, f.new_state(8), torch.zeros(f.n, dtype=f.dtype, device="cuda"),
+                     s.to(torch.float32).cuda(), s.numpy(), torch.zeros(f.n_slopes, dtype=torch.float32,
+                                                                         device="cuda")))
+    batch = lib.FewhaBatch([x[2] for x in inst])
+    stats = batch.bind([x[7] for x in inst], [x[4] for x in inst], [x[3] for x in inst], max_iter=4)
+    graph = batch.capture_graph()
+    torch.cuda.synchronize()
+    for x in inst:  # capture does not run the kernels: nothing may have changed
+        assert torch.count_nonzero(x[4]).item() == 0
+    for t in range(frames):
+        for x in inst:
+            x[7].copy_(x[5][t])
+        graph.replay()
+        for (o, st_o, f, st_g, c, sd, s64, buf), rg in zip(inst, batch.read_stats(stats)):
+            ro = o.solve(s64[t], st_o, max_iter=4, augmented=True)
+            assert rg["status"] == 0 and rg["iterations"] == ro["iterations"]
+            assert rel(c.cpu().numpy(), st_o["c"]) < 1e-5
+    batch.close()
