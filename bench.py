@@ -250,7 +250,7 @@ def run_ours(args):
                         "frac": achieved / peak, "traffic": traffic,
                         "kernel": "k_solve_persistent" if args.launch == "persistent" else "all phases",
                         "algorithmic_bytes_per_launch": algo_bytes, "peak_source": peak_kind},
-           "gpu_launches": args.steps * (1 if args.launch == "persistent" else 6 + 5 * args.max_iter)}
+           "gpu_launches": args.steps * (1 if args.launch == "persistent" else 6 + 6 * args.max_iter)}
     if clocks:
         out["clocks"] = clocks
 

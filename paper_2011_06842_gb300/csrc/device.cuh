@@ -52,7 +52,7 @@ constexpr int kSlotInit = kSlotGram + kK * kK + kK;  // K (q_j, z), rz, rr
 constexpr int kSlots = kSlotInit + kK + 2;
 
 struct Bar {
-    unsigned int count, gen;
+    unsigned int count, gen;  // arrivals; gen unused (kept for the layout)
 };
 
 // Device record of one solve (scalars shared between phases).
@@ -89,6 +89,7 @@ struct Geo {
     const int *band_layer, *band_row0, *band_rows;  // [nbands]
     const int *band_ilo, *band_ihi;  // [G][nbands] pupil rows the band touches
     int rows_chunk;             // pupil rows staged per pass of band_gather
+    int stage_tab;              // band_gather also stages its P^T weight tables in shared memory
     int pingpong;               // layer phases have a second n x n shared buffer
     // P_g^T weights per (g, l, axis, layer node k): pupil nodes adj_lo .. adj_lo +
     // adj_cnt - 1 with weights adj_w[..][0 .. adj_cnt), index ((g*L + l)*2 + axis)*FEWHA_MAX_GRID + k
@@ -411,10 +412,12 @@ __device__ __forceinline__ void set_status(Record *rec, int st)
 
 // Grid barrier with a time limit.  Returns false (and the CTA must return)
 // when any CTA has recorded an error or the wait ran past timeout_ns.
-__device__ __forceinline__ unsigned int atom_add_release_gpu(unsigned int *p, unsigned int v)
+// arrival: releases this CTA's writes and, for the last arriver, acquires
+// everyone else's
+__device__ __forceinline__ unsigned int atom_add_acq_rel_gpu(unsigned int *p, unsigned int v)
 {
     unsigned int r;
-    asm volatile("atom.add.release.gpu.u32 %0, [%1], %2;" : "=r"(r) : "l"(p), "r"(v) : "memory");
+    asm volatile("atom.add.acq_rel.gpu.u32 %0, [%1], %2;" : "=r"(r) : "l"(p), "r"(v) : "memory");
     return r;
 }
 __device__ __forceinline__ unsigned int ld_acquire_gpu(const unsigned int *p)
@@ -423,14 +426,10 @@ __device__ __forceinline__ unsigned int ld_acquire_gpu(const unsigned int *p)
     asm volatile("ld.acquire.gpu.u32 %0, [%1];" : "=r"(r) : "l"(p) : "memory");
     return r;
 }
-__device__ __forceinline__ void st_release_gpu(unsigned int *p, unsigned int v)
-{
-    asm volatile("st.release.gpu.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-// Barrier over the nctas CTAs of a group, with a time limit (generation counter).  Thread 0
-// arrives with a release add after the block barrier (publishing the CTA's
-// writes) and waits with acquire loads.  Returns false (and the CTA must
+// Barrier over the nctas CTAs of a group, with a time limit.  Thread 0 arrives
+// with an acquire-release add on a counter that only grows during a solve
+// (after the block barrier, publishing the CTA's writes) and waits with
+// acquire loads until the counter reaches the next multiple of nctas.  Returns false (and the CTA must
 // return) when any CTA has recorded an error or the wait ran past timeout_ns.
 __device__ inline bool grid_sync(Record *rec, unsigned long long timeout_ns, int nctas, int rank,
                                  unsigned long long *trace_slot = nullptr)
@@ -446,22 +445,25 @@ __device__ inline bool grid_sync(Record *rec, unsigned long long timeout_ns, int
             if (t_pass) atomicMax(trace_slot, now - t_pass);
         }
         volatile int *vst = &rec->status;
-        const unsigned int g = ld_acquire_gpu(&rec->bar.gen);
-        const unsigned int prev = atom_add_release_gpu(&rec->bar.count, 1u);
-        if (prev == (unsigned int)nctas - 1) {
-            rec->bar.count = 0;  // ordered before the release of the new generation
-            st_release_gpu(&rec->bar.gen, g + 1);
-        } else {
+        // the counter only grows within a solve (reset before every launch):
+        // the barrier of this arrival completes when it reaches the next
+        // multiple of nctas
+        const unsigned int prev = atom_add_acq_rel_gpu(&rec->bar.count, 1u);
+        const unsigned int target = (prev / (unsigned int)nctas + 1u) * (unsigned int)nctas;
+        if (prev + 1u != target) {
             const unsigned long long t0 = gtimer();
-            while (ld_acquire_gpu(&rec->bar.gen) == g) {
-                if (*vst != 0) {
-                    ok = 0;
-                    break;
-                }
-                if (gtimer() - t0 > timeout_ns) {
-                    set_status(rec, FEWHA_ERR_TIMEOUT);
-                    ok = 0;
-                    break;
+            unsigned int polls = 0;
+            while (ld_acquire_gpu(&rec->bar.count) < target) {
+                if ((++polls & 7u) == 1u) {  // polls 1, 9, 17, ...: status and time limit
+                    if (*vst != 0) {
+                        ok = 0;
+                        break;
+                    }
+                    if (gtimer() - t0 > timeout_ns) {
+                        set_status(rec, FEWHA_ERR_TIMEOUT);
+                        ok = 0;
+                        break;
+                    }
                 }
             }
         }
@@ -661,8 +663,8 @@ __device__ void fdwt2(T *buf, T *tmp, int lgn, int J, const Geo<T> &G)
 // Layer element e (row-major, n columns) <-> shared-memory index (pitch n + 1).
 __device__ __forceinline__ int spad(int e, int lgn) { return e + (e >> lgn); }
 
-template <typename T, typename S, class Load, class Post>
-__device__ void layer_idwt(const Args<T, S> &A, T *buf, Load load, Post post)
+template <typename T, typename S, class Load>
+__device__ void layer_idwt(const Args<T, S> &A, T *buf, Load load)
 {
     constexpr int W = VW<T>::W;
     const Geo<T> &G = A.geo;
@@ -678,7 +680,6 @@ __device__ void layer_idwt(const Args<T, S> &A, T *buf, Load load, Post post)
             for (int i = 0; i < W; i++) buf[s0 + i] = x[i];
         }
         __syncthreads();
-        post(l, buf);
         idwt2<T>(buf, G.pingpong ? buf + n * (n + 1) : buf, lgn, G.lay_J[l], G);
         const T sc = G.inv_delta[l];
         for (int v = threadIdx.x; v < nv; v += blockDim.x) {
@@ -716,22 +717,36 @@ __device__ __noinline__ typename AccT<T>::type wfs_phase(const Args<T, S> &A, T 
         const int g = w / per_g, tt = w - g * per_g;
         const int i0 = (tt / G.tiles_x) * TY, j0 = (tt % G.tiles_x) * TX;
         if (!RHS) {
-            // per (layer, halo node) bilinear value
-            for (int e = threadIdx.x; e < G.L * HY * HX; e += blockDim.x) {
-                const int l = e / (HY * HX), loc = e - l * HY * HX;
-                const int i = i0 - 1 + loc / HX, j = j0 - 1 + loc % HX;
-                T v = 0;
-                if (i >= 0 && i < m && j >= 0 && j < m) {
-                    const int bx = ((g * G.L + l) * 2 + 0) * m, by = ((g * G.L + l) * 2 + 1) * m;
-                    const int kx = __ldg(G.fk + bx + j), ky = __ldg(G.fk + by + i);
-                    const T wx = __ldg(G.fw + bx + j), wy = __ldg(G.fw + by + i);
-                    const int n = G.lay_n[l];
-                    const S *Lp = A.nodal + G.lay_off[l] + (long)ky * n + kx;
-                    const T v00 = Cv<S>::ld(ldcg(Lp)), v01 = Cv<S>::ld(ldcg(Lp + 1));
-                    const T v10 = Cv<S>::ld(ldcg(Lp + n)), v11 = Cv<S>::ld(ldcg(Lp + n + 1));
-                    v = (T(1) - wy) * ((T(1) - wx) * v00 + wx * v01) + wy * ((T(1) - wx) * v10 + wx * v11);
+            // per (layer, halo node) bilinear value; U items per thread with all
+            // of their loads in flight before the shared-memory stores
+            const int tot = G.L * HY * HX;
+            constexpr int U = 3;
+            for (int e0 = threadIdx.x; e0 < tot; e0 += U * blockDim.x) {
+                T v[U];
+#pragma unroll
+                for (int u = 0; u < U; u++) {
+                    const int e = e0 + u * blockDim.x;
+                    v[u] = 0;
+                    if (e < tot) {
+                        const int l = e / (HY * HX), loc = e - l * HY * HX;
+                        const int i = i0 - 1 + loc / HX, j = j0 - 1 + loc % HX;
+                        if (i >= 0 && i < m && j >= 0 && j < m) {
+                            const int bx = ((g * G.L + l) * 2 + 0) * m, by = ((g * G.L + l) * 2 + 1) * m;
+                            const int kx = __ldg(G.fk + bx + j), ky = __ldg(G.fk + by + i);
+                            const T wx = __ldg(G.fw + bx + j), wy = __ldg(G.fw + by + i);
+                            const int n = G.lay_n[l];
+                            const S *Lp = A.nodal + G.lay_off[l] + (long)ky * n + kx;
+                            const T v00 = Cv<S>::ld(ldcg(Lp)), v01 = Cv<S>::ld(ldcg(Lp + 1));
+                            const T v10 = Cv<S>::ld(ldcg(Lp + n)), v11 = Cv<S>::ld(ldcg(Lp + n + 1));
+                            v[u] = (T(1) - wy) * ((T(1) - wx) * v00 + wx * v01) + wy * ((T(1) - wx) * v10 + wx * v11);
+                        }
+                    }
                 }
-                phi[e] = v;
+#pragma unroll
+                for (int u = 0; u < U; u++) {
+                    const int e = e0 + u * blockDim.x;
+                    if (e < tot) phi[e] = v[u];
+                }
             }
             __syncthreads();
             for (int loc = threadIdx.x; loc < HY * HX; loc += blockDim.x) {
@@ -796,6 +811,8 @@ __device__ __noinline__ void band_gather(const Args<T, S> &A, T *sm)
 {
     const Geo<T> &G = A.geo;
     const int m = G.m, RC = G.rows_chunk, NB = G.nbands;
+    __shared__ int s_cum[FEWHA_MAX_GS + 1], s_base[FEWHA_MAX_GS + 1], s_ng;
+    __shared__ long s_off[FEWHA_MAX_GS];  // psi element = s_off[q] + staged index
     for (int w = A.vrank(); w < NB; w += A.ncta) {
         const int l = __ldg(G.band_layer + w), a0 = __ldg(G.band_row0 + w), BR = __ldg(G.band_rows + w);
         const int n = G.lay_n[l], lgn = G.lay_lg[l], nout = BR << lgn;
@@ -812,45 +829,131 @@ __device__ __noinline__ void band_gather(const Args<T, S> &A, T *sm)
                 rows_tot += r;
             }
             if (g1 == g0) g1 = g0 + 1;  // unreachable: the host sizes RC >= the rows of any one guide star
-            // stage psi rows (one latency round for the group)
-            for (int g = g0, base = 0; g < g1; g++) {
-                const int ilo = __ldg(G.band_ilo + g * NB + w), rows = __ldg(G.band_ihi + g * NB + w) - ilo;
-                const S *src = A.psi + (size_t)g * m * m + (size_t)ilo * m;
-                for (int e = threadIdx.x; e < rows * m; e += blockDim.x) ps[base * m + e] = Cv<S>::ld(ldcg(src + e));
-                base += rows;
+            // stage psi rows of the group's guide stars, flattened so that each
+            // thread has all of its loads in flight at once (one latency round)
+            if (threadIdx.x == 0) {
+                int c = 0;
+                for (int g = g0; g < g1; g++) {
+                    const int ilo = __ldg(G.band_ilo + g * NB + w), rows = __ldg(G.band_ihi + g * NB + w) - ilo;
+                    s_off[g - g0] = (long)g * m * m + (long)ilo * m - c;
+                    s_base[g - g0] = c / m;
+                    c += rows * m;
+                    s_cum[g - g0 + 1] = c;
+                }
+                s_cum[0] = 0;
+                s_base[g1 - g0] = c / m;
+                s_ng = g1 - g0;
+            }
+            __syncthreads();
+            const int ng = s_ng, nxt = ng << lgn, nyt = ng * BR;
+            // weight tables of the group (x: per guide star and layer column,
+            // y: per guide star and band row), loaded in the same latency round
+            T *xw = Tb + RC * n;                          // [ng][n][kAdjW]
+            T *yw = xw + (size_t)nxt * kAdjW;             // [ng][BR][kAdjW]
+            int *xlo = reinterpret_cast<int *>(yw + (size_t)nyt * kAdjW), *xct = xlo + nxt;
+            int *ylo = xct + nxt, *yct = ylo + nyt;
+            const bool tab = G.stage_tab != 0;
+            int t_lo = 0, t_ct = 0;
+            T t_w[kAdjW];
+            const int tt = threadIdx.x;  // one table entry per thread (nxt + nyt <= blockDim.x)
+            if (tab && tt < nxt + nyt) {
+                int idx;
+                if (tt < nxt) {
+                    const int q = tt >> lgn, bcol = tt & (n - 1);
+                    idx = ((g0 + q) * G.L + l) * 2 * FEWHA_MAX_GRID + bcol;
+                } else {
+                    const int q = (tt - nxt) / BR, r = (tt - nxt) - q * BR;
+                    idx = (((g0 + q) * G.L + l) * 2 + 1) * FEWHA_MAX_GRID + a0 + r;
+                }
+                t_lo = __ldg(G.adj_lo + idx);
+                t_ct = __ldg(G.adj_cnt + idx);
+#pragma unroll
+                for (int c = 0; c < kAdjW; c++) t_w[c] = __ldg(G.adj_w + (size_t)idx * kAdjW + c);
+            }
+            {
+                const int total = s_cum[ng];
+                constexpr int U = 4;
+                int q = 0;  // guide star of the staged index t (t only grows)
+                for (int t0 = threadIdx.x; t0 < total; t0 += U * blockDim.x) {
+                    S v[U];
+#pragma unroll
+                    for (int u = 0; u < U; u++) {
+                        const int t = t0 + u * blockDim.x;
+                        if (t < total) {
+                            while (t >= s_cum[q + 1]) q++;
+                            v[u] = ldcg(A.psi + s_off[q] + t);
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < U; u++) {
+                        const int t = t0 + u * blockDim.x;
+                        if (t < total) ps[t] = Cv<S>::ld(v[u]);
+                    }
+                }
+            }
+            if (tab && tt < nxt + nyt) {
+                if (tt < nxt) {
+                    xlo[tt] = t_lo;
+                    xct[tt] = t_ct;
+#pragma unroll
+                    for (int c = 0; c < kAdjW; c++) xw[(size_t)tt * kAdjW + c] = t_w[c];
+                } else {
+                    const int e = tt - nxt;
+                    ylo[e] = t_lo;
+                    yct[e] = t_ct;
+#pragma unroll
+                    for (int c = 0; c < kAdjW; c++) yw[(size_t)e * kAdjW + c] = t_w[c];
+                }
             }
             __syncthreads();
             // x-contraction: Tb[i][b] = sum_j Wx[j][b] psi[i][j]
-            for (int g = g0, base = 0; g < g1; g++) {
-                const int rows = __ldg(G.band_ihi + g * NB + w) - __ldg(G.band_ilo + g * NB + w);
-                const int tx = ((g * G.L + l) * 2) * FEWHA_MAX_GRID;
-                for (int e = threadIdx.x; e < (rows << lgn); e += blockDim.x) {
-                    const int i = e >> lgn, b = e & (n - 1);
-                    const int jlo = __ldg(G.adj_lo + tx + b), cnt = __ldg(G.adj_cnt + tx + b);
-                    const T *wt = G.adj_w + (size_t)(tx + b) * kAdjW;
-                    const T *row = ps + (base + i) * m + jlo;
+            {
+                const int total = s_base[ng];  // staged rows
+                int q = 0;                     // guide star of the staged row (rows only grow)
+                for (int e = threadIdx.x; e < (total << lgn); e += blockDim.x) {
+                    const int row = e >> lgn, bcol = e & (n - 1);
+                    while (row >= s_base[q + 1]) q++;
+                    int jlo, cnt;
+                    const T *wt;
+                    if (tab) {
+                        const int ti = (q << lgn) + bcol;
+                        jlo = xlo[ti];
+                        cnt = xct[ti];
+                        wt = xw + (size_t)ti * kAdjW;
+                    } else {
+                        const int tx = ((g0 + q) * G.L + l) * 2 * FEWHA_MAX_GRID + bcol;
+                        jlo = __ldg(G.adj_lo + tx);
+                        cnt = __ldg(G.adj_cnt + tx);
+                        wt = G.adj_w + (size_t)tx * kAdjW;
+                    }
+                    const T *rowp = ps + row * m + jlo;
                     T v = 0;
-#pragma unroll
-                    for (int c = 0; c < kAdjW; c++)
-                        if (c < cnt) v += __ldg(wt + c) * row[c];
-                    Tb[((base + i) << lgn) + b] = v;
+                    for (int c = 0; c < cnt; c++) v += wt[c] * rowp[c];  // cnt <= kAdjW, typically 1-4
+                    Tb[(row << lgn) + bcol] = v;
                 }
-                base += rows;
             }
             __syncthreads();
             // y-contraction into the owned output
             if (oa < BR) {
                 const int a = a0 + oa;
-                for (int g = g0, base = 0; g < g1; g++) {
-                    const int ilo = __ldg(G.band_ilo + g * NB + w), rows = __ldg(G.band_ihi + g * NB + w) - ilo;
-                    const int ty = ((g * G.L + l) * 2 + 1) * FEWHA_MAX_GRID + a;
-                    const int ilo_a = __ldg(G.adj_lo + ty), cnt = __ldg(G.adj_cnt + ty);
-                    const T *wt = G.adj_w + (size_t)ty * kAdjW;
-                    const T *col = Tb + ((base + ilo_a - ilo) << lgn) + ob;
-#pragma unroll
-                    for (int c = 0; c < kAdjW; c++)
-                        if (c < cnt) acc += __ldg(wt + c) * col[c << lgn];
-                    base += rows;
+                for (int q = 0; q < ng; q++) {
+                    const int g = g0 + q;
+                    const int ilo = __ldg(G.band_ilo + g * NB + w);
+                    int ilo_a, cnt;
+                    const T *wt;
+                    if (tab) {
+                        const int ti = q * BR + oa;
+                        ilo_a = ylo[ti];
+                        cnt = yct[ti];
+                        wt = yw + (size_t)ti * kAdjW;
+                    } else {
+                        const int ty = ((g * G.L + l) * 2 + 1) * FEWHA_MAX_GRID + a;
+                        ilo_a = __ldg(G.adj_lo + ty);
+                        cnt = __ldg(G.adj_cnt + ty);
+                        wt = G.adj_w + (size_t)ty * kAdjW;
+                    }
+                    const T *col = Tb + ((s_base[q] + ilo_a - ilo) << lgn) + ob;
+                    for (int c = 0; c < cnt; c++) acc += wt[c] * col[c << lgn];  // cnt <= kAdjW
                 }
             }
             __syncthreads();

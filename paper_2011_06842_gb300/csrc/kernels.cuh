@@ -23,18 +23,34 @@ __device__ __forceinline__ T *dyn_smem()
     return reinterpret_cast<T *>(fewha_smem);
 }
 
+// Kernel arguments are copied into shared memory once: the phases are not
+// inlined and take them by reference, which would otherwise place them in
+// local memory (a load through the L1 for every field read).
+template <typename T, typename S>
+__device__ __forceinline__ void args_to_smem(const Args<T, S> &src, Args<T, S> &dst)
+{
+    const int4 *s = reinterpret_cast<const int4 *>(&src);
+    int4 *d = reinterpret_cast<int4 *>(&dst);
+    for (int e = threadIdx.x; e < (int)(sizeof(Args<T, S>) / sizeof(int4)); e += blockDim.x) d[e] = s[e];
+    __syncthreads();
+}
+
 // apply: nodal = W^{-1} x
 template <typename T, typename S>
-__global__ void __launch_bounds__(kThreads, 1) k_apply_idwt(Args<T, S> A)
+__global__ void __launch_bounds__(kThreads, 1) k_apply_idwt(const __grid_constant__ Args<T, S> Ap)
 {
+    __shared__ __align__(16) Args<T, S> A;
+    args_to_smem(Ap, A);
     constexpr int W = VW<T>::W;
-    layer_idwt<T, S>(A, dyn_smem<T>(), [&](long e, T (&x)[W]) { vld(A.x + e, x); }, [](int, const T *) {});
+    layer_idwt<T, S>(A, dyn_smem<T>(), [&](long e, T (&x)[W]) { vld(A.x + e, x); });
 }
 
 // psi = Gamma^T C Gamma P nodal (RHS = false) or Gamma^T C s (RHS = true)
 template <typename T, typename S, bool RHS>
-__global__ void __launch_bounds__(kThreads, 1) k_wfs(Args<T, S> A)
+__global__ void __launch_bounds__(kThreads, 1) k_wfs(const __grid_constant__ Args<T, S> Ap)
 {
+    __shared__ __align__(16) Args<T, S> A;
+    args_to_smem(Ap, A);
     __shared__ double sred[kSred];
     typename AccT<T>::type acc[1] = {wfs_phase<T, S, RHS>(A, dyn_smem<T>())};
     const int slots[1] = {kSlotB};
@@ -43,16 +59,20 @@ __global__ void __launch_bounds__(kThreads, 1) k_wfs(Args<T, S> A)
 
 // u = P^T psi
 template <typename T, typename S>
-__global__ void __launch_bounds__(kThreads, 1) k_gather(Args<T, S> A)
+__global__ void __launch_bounds__(kThreads, 1) k_gather(const __grid_constant__ Args<T, S> Ap)
 {
+    __shared__ __align__(16) Args<T, S> A;
+    args_to_smem(Ap, A);
     if (ldcgi(&A.rec->done) || ldcgi(&A.rec->status)) return;
     band_gather<T, S>(A, dyn_smem<T>());
 }
 
 // y = W^{-T} u + alpha D x  (APPLY) or y = W^{-T} u (RHS)
 template <typename T, typename S, bool RHS>
-__global__ void __launch_bounds__(kThreads, 1) k_fdwt(Args<T, S> A)
+__global__ void __launch_bounds__(kThreads, 1) k_fdwt(const __grid_constant__ Args<T, S> Ap)
 {
+    __shared__ __align__(16) Args<T, S> A;
+    args_to_smem(Ap, A);
     constexpr int W = VW<T>::W;
     layer_fdwt<T, S>(A, dyn_smem<T>(), [&](long e, const T (&v)[W]) {
         T y[W], x[W], ad[W];
@@ -80,15 +100,17 @@ struct MultiArgs {
 template <typename T, typename S>
 __global__ void __launch_bounds__(kThreads, 1) k_multi_idwt(const __grid_constant__ MultiArgs<T, S> M)
 {
-    const Args<T, S> &A = M.a[blockIdx.x / M.per];
+    __shared__ __align__(16) Args<T, S> A;
+    args_to_smem(M.a[blockIdx.x / M.per], A);
     constexpr int W = VW<T>::W;
-    layer_idwt<T, S>(A, dyn_smem<T>(), [&](long e, T (&x)[W]) { vld(A.x + e, x); }, [](int, const T *) {});
+    layer_idwt<T, S>(A, dyn_smem<T>(), [&](long e, T (&x)[W]) { vld(A.x + e, x); });
 }
 
 template <typename T, typename S>
 __global__ void __launch_bounds__(kThreads, 1) k_multi_wfs(const __grid_constant__ MultiArgs<T, S> M)
 {
-    const Args<T, S> &A = M.a[blockIdx.x / M.per];
+    __shared__ __align__(16) Args<T, S> A;
+    args_to_smem(M.a[blockIdx.x / M.per], A);
     __shared__ double sred[kSred];
     typename AccT<T>::type acc[1] = {wfs_phase<T, S, false>(A, dyn_smem<T>())};
     const int slots[1] = {kSlotB};
@@ -98,14 +120,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_multi_wfs(const __grid_constant
 template <typename T, typename S>
 __global__ void __launch_bounds__(kThreads, 1) k_multi_gather(const __grid_constant__ MultiArgs<T, S> M)
 {
-    const Args<T, S> &A = M.a[blockIdx.x / M.per];
+    __shared__ __align__(16) Args<T, S> A;
+    args_to_smem(M.a[blockIdx.x / M.per], A);
     band_gather<T, S>(A, dyn_smem<T>());
 }
 
 template <typename T, typename S>
 __global__ void __launch_bounds__(kThreads, 1) k_multi_fdwt(const __grid_constant__ MultiArgs<T, S> M)
 {
-    const Args<T, S> &A = M.a[blockIdx.x / M.per];
+    __shared__ __align__(16) Args<T, S> A;
+    args_to_smem(M.a[blockIdx.x / M.per], A);
     constexpr int W = VW<T>::W;
     layer_fdwt<T, S>(A, dyn_smem<T>(), [&](long e, const T (&v)[W]) {
         T y[W], x[W], ad[W];
@@ -121,6 +145,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_multi_fdwt(const __grid_constan
 #define FEWHA_PHASE_GUARD                                             \
     __shared__ Scal sc;                                               \
     __shared__ double sred[kSred];                                   \
+    __shared__ __align__(16) Args<T, S> A;                            \
+    args_to_smem(Ap, A);                                              \
     (void)sred;                                                       \
     if (ldcgi(&A.rec->done) || ldcgi(&A.rec->status)) return;         \
     const Basis b = basis_info(A);                                    \
@@ -128,8 +154,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_multi_fdwt(const __grid_constan
 
 // R1: weighted slopes -> psi, and the Gram matrix of the old basis
 template <typename T, typename S>
-__global__ void __launch_bounds__(kThreads, 1) k_rhs_wfs(Args<T, S> A)
+__global__ void __launch_bounds__(kThreads, 1) k_rhs_wfs(const __grid_constant__ Args<T, S> Ap)
 {
+    __shared__ __align__(16) Args<T, S> A;
+    args_to_smem(Ap, A);
     wfs_phase<T, S, true>(A, dyn_smem<T>());
     const Basis b = basis_info(A);
     if (b.kv > 0) phase_gram<T, S>(A, b, dyn_smem<T>(), (int)(A.smem_bytes / sizeof(T)));
@@ -137,7 +165,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_rhs_wfs(Args<T, S> A)
 
 // R2: u = P^T psi; the last CTA also factorises the Gram matrix
 template <typename T, typename S>
-__global__ void __launch_bounds__(kThreads, 1) k_rhs_gather(Args<T, S> A)
+__global__ void __launch_bounds__(kThreads, 1) k_rhs_gather(const __grid_constant__ Args<T, S> Ap)
 {
     FEWHA_PHASE_GUARD
     band_gather<T, S>(A, dyn_smem<T>());
@@ -145,7 +173,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_rhs_gather(Args<T, S> A)
 }
 
 template <typename T, typename S>
-__global__ void __launch_bounds__(kThreads, 1) k_rhs_fdwt(Args<T, S> A)
+__global__ void __launch_bounds__(kThreads, 1) k_rhs_fdwt(const __grid_constant__ Args<T, S> Ap)
 {
     FEWHA_PHASE_GUARD
     (void)sc;
@@ -153,7 +181,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_rhs_fdwt(Args<T, S> A)
 }
 
 template <typename T, typename S>
-__global__ void __launch_bounds__(kThreads, 1) k_ptr(Args<T, S> A)
+__global__ void __launch_bounds__(kThreads, 1) k_ptr(const __grid_constant__ Args<T, S> Ap)
 {
     FEWHA_PHASE_GUARD
     (void)sc;
@@ -161,21 +189,29 @@ __global__ void __launch_bounds__(kThreads, 1) k_ptr(Args<T, S> A)
 }
 
 template <typename T, typename S>
-__global__ void __launch_bounds__(kThreads, 1) k_init(Args<T, S> A)
+__global__ void __launch_bounds__(kThreads, 1) k_init(const __grid_constant__ Args<T, S> Ap)
 {
     FEWHA_PHASE_GUARD
     if (b.kv > 0) phase_init<T, S>(A, b, sc, sred);
 }
 
 template <typename T, typename S>
-__global__ void __launch_bounds__(kThreads, 1) k_A(Args<T, S> A, int k)
+__global__ void __launch_bounds__(kThreads, 1) k_U(const __grid_constant__ Args<T, S> Ap, int k)
 {
     FEWHA_PHASE_GUARD
-    phase_A<T, S>(A, b, k, dyn_smem<T>(), sc, sred);
+    phase_U<T, S>(A, b, k, sc, sred);
 }
 
 template <typename T, typename S>
-__global__ void __launch_bounds__(kThreads, 1) k_B(Args<T, S> A, int k)
+__global__ void __launch_bounds__(kThreads, 1) k_A(const __grid_constant__ Args<T, S> Ap, int k)
+{
+    FEWHA_PHASE_GUARD
+    (void)sc;
+    phase_A<T, S>(A, b, k, dyn_smem<T>());
+}
+
+template <typename T, typename S>
+__global__ void __launch_bounds__(kThreads, 1) k_B(const __grid_constant__ Args<T, S> Ap, int k)
 {
     FEWHA_PHASE_GUARD
     (void)sc;
@@ -185,14 +221,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_B(Args<T, S> A, int k)
 }
 
 template <typename T, typename S>
-__global__ void __launch_bounds__(kThreads, 1) k_C(Args<T, S> A, int k)
+__global__ void __launch_bounds__(kThreads, 1) k_C(const __grid_constant__ Args<T, S> Ap, int k)
 {
     FEWHA_PHASE_GUARD
     phase_C<T, S>(A, b, k, dyn_smem<T>(), sc);
 }
 
 template <typename T, typename S>
-__global__ void __launch_bounds__(kThreads, 1) k_D(Args<T, S> A, int k)
+__global__ void __launch_bounds__(kThreads, 1) k_D(const __grid_constant__ Args<T, S> Ap, int k)
 {
     FEWHA_PHASE_GUARD
     (void)sc;
@@ -200,7 +236,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_D(Args<T, S> A, int k)
 }
 
 template <typename T, typename S>
-__global__ void __launch_bounds__(kThreads, 1) k_E(Args<T, S> A, int k)
+__global__ void __launch_bounds__(kThreads, 1) k_E(const __grid_constant__ Args<T, S> Ap, int k)
 {
     FEWHA_PHASE_GUARD
     (void)sc;
@@ -208,9 +244,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_E(Args<T, S> A, int k)
 }
 
 template <typename T, typename S>
-__global__ void __launch_bounds__(kThreads, 1) k_finish(Args<T, S> A)
+__global__ void __launch_bounds__(kThreads, 1) k_finish(const __grid_constant__ Args<T, S> Ap)
 {
     __shared__ Scal sc;
+    __shared__ __align__(16) Args<T, S> A;
+    args_to_smem(Ap, A);
     if (A.vrank() != 0) return;
     const Basis b = basis_info(A);
     int K = ldcgi(&A.rec->done) ? ldcgi(&A.rec->iters) : A.max_iter;
@@ -251,10 +289,12 @@ __device__ void solve_body(const Args<T, S> &A, Scal &sc, double *sred)
             if (!sync(5)) break;
         }
         for (int k = 0; k < A.max_iter; k++) {
-            if (!phase_A<T, S>(A, b, k, sm, sc, sred)) {
+            if (!phase_U<T, S>(A, b, k, sc, sred)) {
                 K = k;
                 break;
             }
+            if (!sync(10)) break;
+            phase_A<T, S>(A, b, k, sm);
             if (!sync(11)) break;
             {
                 typename AccT<T>::type acc[1] = {wfs_phase<T, S, false>(A, sm)};
@@ -280,10 +320,12 @@ __device__ void solve_body(const Args<T, S> &A, Scal &sc, double *sred)
 
 // One instance on the whole grid (cooperative launch).
 template <typename T, typename S>
-__global__ void __launch_bounds__(kThreads, 1) k_solve_persistent(Args<T, S> A)
+__global__ void __launch_bounds__(kThreads, 1) k_solve_persistent(const __grid_constant__ Args<T, S> Ap)
 {
     __shared__ Scal sc;
     __shared__ double sred[kSred];
+    __shared__ __align__(16) Args<T, S> A;
+    args_to_smem(Ap, A);
     solve_body<T, S>(A, sc, sred);
 }
 
@@ -296,12 +338,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_solve_batched(const Args<T, S> 
     __shared__ double sred[kSred];
     __shared__ __align__(16) Args<T, S> A;
     const int i = cta_inst[blockIdx.x];
-    {
-        const int4 *src = reinterpret_cast<const int4 *>(inst + i);
-        int4 *dst = reinterpret_cast<int4 *>(&A);
-        for (int e = threadIdx.x; e < (int)(sizeof(Args<T, S>) / sizeof(int4)); e += blockDim.x) dst[e] = src[e];
-    }
-    __syncthreads();
+    args_to_smem(inst[i], A);
     solve_body<T, S>(A, sc, sred);
 }
 
@@ -560,6 +597,18 @@ struct Impl : ImplBase {
         G.rows_chunk = (int)std::min<size_t>(max_rows_sum, smem / row_bytes);
         if (smem > smem_cap || G.rows_chunk < max_rows) return FEWHA_ERR_GEOMETRY;
         sm_fixed = std::max(sm_layer, std::min(want, smem_cap));
+        // P^T weight tables of one band (all guide stars) staged beside the
+        // psi rows when one thread per entry and the shared memory suffice
+        const int band_rows_max = std::min(nmax, std::min(kThreads / nmax, 8));
+        const size_t tab_entries = (size_t)P.G * (nmax + band_rows_max);
+        const size_t tab_bytes = tab_entries * (kAdjW * sizeof(T) + 2 * sizeof(int));
+        const size_t gather_bytes = (size_t)G.rows_chunk * row_bytes + tab_bytes;
+        G.stage_tab = 0;
+        if (tab_entries <= (size_t)kThreads && gather_bytes <= smem_cap) {
+            G.stage_tab = 1;
+            smem = std::max(smem, gather_bytes);
+            sm_fixed = std::max(sm_fixed, gather_bytes);
+        }
         int dev, nsm;
         CK(cudaGetDevice(&dev));
         CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
@@ -577,6 +626,7 @@ struct Impl : ImplBase {
         CK(setattr((const void *)k_rhs_gather<T, S>));
         CK(setattr((const void *)k_ptr<T, S>));
         CK(setattr((const void *)k_init<T, S>));
+        CK(setattr((const void *)k_U<T, S>));
         CK(setattr((const void *)k_A<T, S>));
         CK(setattr((const void *)k_B<T, S>));
         CK(setattr((const void *)k_C<T, S>));
@@ -823,6 +873,7 @@ struct Impl : ImplBase {
         k_ptr<T, S><<<ncta, kThreads, smem, s>>>(A);
         k_init<T, S><<<ncta, kThreads, smem, s>>>(A);
         for (int k = 0; k < A.max_iter; k++) {
+            k_U<T, S><<<ncta, kThreads, smem, s>>>(A, k);
             k_A<T, S><<<ncta, kThreads, smem, s>>>(A, k);
             k_B<T, S><<<ncta, kThreads, smem, s>>>(A, k);
             k_C<T, S><<<ncta, kThreads, smem, s>>>(A, k);

@@ -249,16 +249,18 @@ __device__ __noinline__ void phase_init(const Args<T, S> &A, const Basis &b, Sca
 }
 
 // ---------------------------------------------------------------------------
-// A_k: iteration scalars, then the direction update fused with W^{-1}:
+// U_k: iteration scalars, then the direction update, element-parallel over all
+// CTAs (each CTA its own element range):
 //   k = 0: p_0 = z_0 - P G^{-1} Q^T z_0 (Algorithm 2) or z_0 (Algorithm 1)
 //   k > 0: p_k = (z_k - mu p_m) + beta p_{k-1},  mu = (z_k, q_m)/(p_m, q_m),
 //          rz_k = (r_k, z_k) - mu (r_k, p_m),  beta = rz_k / rz_{k-1}
 //          (all-directions variant: z_k - P G^{-1} Q^T z_k)
 // Returns false (uniformly) when the stopping test holds before iteration k.
-// CTA 0 records rz_k (k > 0) and ||b||^2 (k = 0).
+// CTA 0 records rz_k (k > 0) and ||b||^2 (k = 0).  Partial sums of
+// (alpha D p_k, p_k) and (r_k, p_k) go to the A slots.
 // ---------------------------------------------------------------------------
 template <typename T, typename S>
-__device__ __noinline__ bool phase_A(const Args<T, S> &A, const Basis &b, int k, T *sm, Scal &sc, double *sred)
+__device__ __noinline__ bool phase_U(const Args<T, S> &A, const Basis &b, int k, Scal &sc, double *sred)
 {
     const int kv = b.kv;
     double *red = sc.red;
@@ -329,7 +331,10 @@ __device__ __noinline__ bool phase_A(const Args<T, S> &A, const Basis &b, int k,
     typedef typename AccT<T>::type Acc;
     constexpr int W = VW<T>::W;
     Acc acc[2] = {0, 0};
-    layer_idwt<T, S>(A, sm, [&](long e, T (&p)[W]) {
+    long lo, hi;
+    cta_range_vec(A.geo.n, W, A.vrank(), A.ncta, lo, hi);
+    for (long e = lo + (long)threadIdx.x * W; e < hi; e += (long)blockDim.x * W) {
+        T p[W];
         T rv[W], jv[W], ad[W], pp[W];
         vld_cg(A.r + e, rv);
         vld_nc(A.geo.invJ + e, jv);
@@ -359,21 +364,23 @@ __device__ __noinline__ bool phase_A(const Args<T, S> &A, const Basis &b, int k,
             acc[0] += (Acc)ad[i] * (Acc)p[i] * (Acc)p[i];
             acc[1] += (Acc)rv[i] * (Acc)p[i];
         }
-    }, [&](int l, const T *buf) {
-        // p_k into its basis slot (from shared memory, before W^{-1} overwrites it)
-        const long off = A.geo.lay_off[l];
-        const int lgn = A.geo.lay_lg[l], nv = A.geo.lay_n[l] * A.geo.lay_n[l] / W;
-        for (int v = threadIdx.x; v < nv; v += blockDim.x) {
-            T x[W];
-            const int s0 = spad(v * W, lgn);
-#pragma unroll
-            for (int i = 0; i < W; i++) x[i] = buf[s0 + i];
-            vst(pk + off + (long)v * W, x);
-        }
-    });
+        vst(pk + e, p);  // p_k into its basis slot
+    }
     const int slots[2] = {kSlotA + (k & 1) * 2, kSlotA + (k & 1) * 2 + 1};
     block_partials<2>(acc, A.part, slots, sred, A.vrank());
     return true;
+}
+
+// ---------------------------------------------------------------------------
+// A_k: nodal layers = W^{-1} p_k, one CTA per layer (p_k from U_k, written by
+// other CTAs: L2 loads).
+// ---------------------------------------------------------------------------
+template <typename T, typename S>
+__device__ __noinline__ void phase_A(const Args<T, S> &A, const Basis &b, int k, T *sm)
+{
+    constexpr int W = VW<T>::W;
+    const T *pk = newP(A, b, k);
+    layer_idwt<T, S>(A, sm, [&](long e, T (&p)[W]) { vld_cg(pk + e, p); });
 }
 
 // ---------------------------------------------------------------------------
