@@ -812,6 +812,7 @@ __device__ __noinline__ void band_gather(const Args<T, S> &A, T *sm)
     const Geo<T> &G = A.geo;
     const int m = G.m, RC = G.rows_chunk, NB = G.nbands;
     __shared__ int s_cum[FEWHA_MAX_GS + 1], s_base[FEWHA_MAX_GS + 1], s_ng;
+    __shared__ int s_ilo[FEWHA_MAX_GS], s_ihi[FEWHA_MAX_GS];
     __shared__ long s_off[FEWHA_MAX_GS];  // psi element = s_off[q] + staged index
     for (int w = A.vrank(); w < NB; w += A.ncta) {
         const int l = __ldg(G.band_layer + w), a0 = __ldg(G.band_row0 + w), BR = __ldg(G.band_rows + w);
@@ -820,11 +821,18 @@ __device__ __noinline__ void band_gather(const Args<T, S> &A, T *sm)
         T acc = 0;
         T *ps = sm;           // [RC][m] staged psi rows
         T *Tb = sm + RC * m;  // [RC][n] their x-contraction
+        // pupil rows [ilo, ihi) of every guide star for this band, one load each
+        // in parallel (the grouping below reads them from shared memory)
+        if (threadIdx.x < G.G) {
+            s_ilo[threadIdx.x] = __ldg(G.band_ilo + threadIdx.x * NB + w);
+            s_ihi[threadIdx.x] = __ldg(G.band_ihi + threadIdx.x * NB + w);
+        }
+        __syncthreads();
         // guide stars in groups whose pupil rows fit the RC staged rows
         for (int g0 = 0, g1; g0 < G.G; g0 = g1) {
             int rows_tot = 0;
             for (g1 = g0; g1 < G.G; g1++) {
-                const int r = __ldg(G.band_ihi + g1 * NB + w) - __ldg(G.band_ilo + g1 * NB + w);
+                const int r = s_ihi[g1] - s_ilo[g1];
                 if (rows_tot + r > RC) break;
                 rows_tot += r;
             }
@@ -834,7 +842,7 @@ __device__ __noinline__ void band_gather(const Args<T, S> &A, T *sm)
             if (threadIdx.x == 0) {
                 int c = 0;
                 for (int g = g0; g < g1; g++) {
-                    const int ilo = __ldg(G.band_ilo + g * NB + w), rows = __ldg(G.band_ihi + g * NB + w) - ilo;
+                    const int ilo = s_ilo[g], rows = s_ihi[g] - ilo;
                     s_off[g - g0] = (long)g * m * m + (long)ilo * m - c;
                     s_base[g - g0] = c / m;
                     c += rows * m;
@@ -848,7 +856,7 @@ __device__ __noinline__ void band_gather(const Args<T, S> &A, T *sm)
             const int ng = s_ng, nxt = ng << lgn, nyt = ng * BR;
             // weight tables of the group (x: per guide star and layer column,
             // y: per guide star and band row), loaded in the same latency round
-            T *xw = Tb + RC * n;                          // [ng][n][kAdjW]
+            T *xw = Tb + RC * n;                          // [kAdjW][ng * n] (tap-major: no bank conflicts)
             T *yw = xw + (size_t)nxt * kAdjW;             // [ng][BR][kAdjW]
             int *xlo = reinterpret_cast<int *>(yw + (size_t)nyt * kAdjW), *xct = xlo + nxt;
             int *ylo = xct + nxt, *yct = ylo + nyt;
@@ -896,7 +904,7 @@ __device__ __noinline__ void band_gather(const Args<T, S> &A, T *sm)
                     xlo[tt] = t_lo;
                     xct[tt] = t_ct;
 #pragma unroll
-                    for (int c = 0; c < kAdjW; c++) xw[(size_t)tt * kAdjW + c] = t_w[c];
+                    for (int c = 0; c < kAdjW; c++) xw[(size_t)c * nxt + tt] = t_w[c];
                 } else {
                     const int e = tt - nxt;
                     ylo[e] = t_lo;
@@ -910,26 +918,53 @@ __device__ __noinline__ void band_gather(const Args<T, S> &A, T *sm)
             {
                 const int total = s_base[ng];  // staged rows
                 int q = 0;                     // guide star of the staged row (rows only grow)
-                for (int e = threadIdx.x; e < (total << lgn); e += blockDim.x) {
-                    const int row = e >> lgn, bcol = e & (n - 1);
-                    while (row >= s_base[q + 1]) q++;
-                    int jlo, cnt;
-                    const T *wt;
-                    if (tab) {
-                        const int ti = (q << lgn) + bcol;
-                        jlo = xlo[ti];
-                        cnt = xct[ti];
-                        wt = xw + (size_t)ti * kAdjW;
-                    } else {
-                        const int tx = ((g0 + q) * G.L + l) * 2 * FEWHA_MAX_GRID + bcol;
-                        jlo = __ldg(G.adj_lo + tx);
-                        cnt = __ldg(G.adj_cnt + tx);
-                        wt = G.adj_w + (size_t)tx * kAdjW;
+                if (tab && (int)blockDim.x % n == 0) {
+                    // each thread keeps one column b; its weights stay in registers
+                    // until the guide star changes
+                    const int bcol = threadIdx.x & (n - 1), rstep = blockDim.x >> lgn;
+                    int qc = -1, jlo = 0, cnt = 0;
+                    T wr[kAdjW];
+                    for (int row = threadIdx.x >> lgn; row < total; row += rstep) {
+                        while (row >= s_base[q + 1]) q++;
+                        if (q != qc) {
+                            const int ti = (q << lgn) + bcol;
+                            jlo = xlo[ti];
+                            cnt = xct[ti];
+#pragma unroll
+                            for (int c = 0; c < kAdjW; c++) wr[c] = c < cnt ? xw[(size_t)c * nxt + ti] : T(0);
+                            qc = q;
+                        }
+                        const T *rowp = ps + row * m + jlo;
+                        T v = 0;
+#pragma unroll
+                        for (int c = 0; c < kAdjW; c++)
+                            if (c < cnt) v += wr[c] * rowp[c];
+                        Tb[(row << lgn) + bcol] = v;
                     }
-                    const T *rowp = ps + row * m + jlo;
-                    T v = 0;
-                    for (int c = 0; c < cnt; c++) v += wt[c] * rowp[c];  // cnt <= kAdjW, typically 1-4
-                    Tb[(row << lgn) + bcol] = v;
+                } else {
+                    for (int e = threadIdx.x; e < (total << lgn); e += blockDim.x) {
+                        const int row = e >> lgn, bcol = e & (n - 1);
+                        while (row >= s_base[q + 1]) q++;
+                        int jlo, cnt, ws;
+                        const T *wt;
+                        if (tab) {
+                            const int ti = (q << lgn) + bcol;
+                            jlo = xlo[ti];
+                            cnt = xct[ti];
+                            wt = xw + ti;
+                            ws = nxt;
+                        } else {
+                            const int tx = ((g0 + q) * G.L + l) * 2 * FEWHA_MAX_GRID + bcol;
+                            jlo = __ldg(G.adj_lo + tx);
+                            cnt = __ldg(G.adj_cnt + tx);
+                            wt = G.adj_w + (size_t)tx * kAdjW;
+                            ws = 1;
+                        }
+                        const T *rowp = ps + row * m + jlo;
+                        T v = 0;
+                        for (int c = 0; c < cnt; c++) v += wt[c * ws] * rowp[c];  // cnt <= kAdjW
+                        Tb[(row << lgn) + bcol] = v;
+                    }
                 }
             }
             __syncthreads();
@@ -938,7 +973,7 @@ __device__ __noinline__ void band_gather(const Args<T, S> &A, T *sm)
                 const int a = a0 + oa;
                 for (int q = 0; q < ng; q++) {
                     const int g = g0 + q;
-                    const int ilo = __ldg(G.band_ilo + g * NB + w);
+                    const int ilo = s_ilo[g];
                     int ilo_a, cnt;
                     const T *wt;
                     if (tab) {

@@ -289,7 +289,7 @@ __device__ void solve_body(const Args<T, S> &A, Scal &sc, double *sred)
             if (!sync(5)) break;
         }
         for (int k = 0; k < A.max_iter; k++) {
-            if (!phase_U<T, S>(A, b, k, sc, sred)) {
+            if (!phase_U<T, S>(A, b, k, sc, sred, true)) {
                 K = k;
                 break;
             }
@@ -302,14 +302,14 @@ __device__ void solve_body(const Args<T, S> &A, Scal &sc, double *sred)
                 block_partials<1>(acc, A.part, slots, sred, rank);
             }
             if (!sync(12)) break;
-            if (!phase_C<T, S>(A, b, k, sm, sc)) {
+            if (!phase_C<T, S>(A, b, k, sm, sc, true)) {
                 K = k;
                 break;
             }
             if (!sync(13)) break;
             phase_D<T, S>(A, sm);
             if (!sync(14)) break;
-            phase_E<T, S>(A, b, k, sred);
+            phase_E<T, S>(A, b, k, sred, &sc.alpha);
             if (!sync(15)) break;
         }
     } while (0);

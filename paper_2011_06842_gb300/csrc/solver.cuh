@@ -65,7 +65,7 @@ struct Scal {
     double gram[kK * kK];          // reduced Gram matrix
     double L[kK * kK], dinv[kK];   // Cholesky factor (copy of the record's)
     double tau[kK];                // projection coefficients
-    double rz, beta, mu, rr, bb, pq, alpha, rinv_pqm;
+    double rz, beta, mu, rr, bb, pq, alpha, rinv_pqm, rinv;
     int stop;
 };
 
@@ -260,7 +260,8 @@ __device__ __noinline__ void phase_init(const Args<T, S> &A, const Basis &b, Sca
 // (alpha D p_k, p_k) and (r_k, p_k) go to the A slots.
 // ---------------------------------------------------------------------------
 template <typename T, typename S>
-__device__ __noinline__ bool phase_U(const Args<T, S> &A, const Basis &b, int k, Scal &sc, double *sred)
+__device__ __noinline__ bool phase_U(const Args<T, S> &A, const Basis &b, int k, Scal &sc, double *sred,
+                                     bool scalars_in_sc = false)
 {
     const int kv = b.kv;
     double *red = sc.red;
@@ -301,14 +302,16 @@ __device__ __noinline__ bool phase_U(const Args<T, S> &A, const Basis &b, int k,
                 if (A.recycle_all) {
                     for (int j = 0; j < kv; j++) rz -= sc.tau[j] * red[4 + kK + j];
                 } else {
-                    sc.mu = red[1] * ldcgd(&A.rec->rinv_pqm);
+                    sc.mu = red[1] * (scalars_in_sc ? sc.rinv_pqm : ldcgd(&A.rec->rinv_pqm));
                     rz -= sc.mu * red[2];
                 }
             }
             sc.rz = rz;
             sc.rr = red[3];
-            sc.bb = ldcgd(&A.rec->bb);
-            sc.beta = rz * ldcgd(A.rec->rinv + (k - 1));
+            // 1/rz_{k-1}, ||b||^2, 1/(p_m, q_m): kept in shared memory by the
+            // persistent kernel, else read from the record
+            if (!scalars_in_sc) sc.bb = ldcgd(&A.rec->bb);
+            sc.beta = rz * (scalars_in_sc ? sc.rinv : ldcgd(A.rec->rinv + (k - 1)));
             if (A.vrank() == 0) A.rec->rz[k] = rz;
         }
     }
@@ -385,23 +388,25 @@ __device__ __noinline__ void phase_A(const Args<T, S> &A, const Basis &b, int k,
 
 // ---------------------------------------------------------------------------
 // C_k: scalars of iteration k and u = P^T psi.  (p_k, q_k) comes from the
-// forward pass: sum w s^2 (WFS phase) + sum alpha d p^2 (A phase), equal to
+// forward pass: sum w s^2 (WFS phase) + sum alpha d p^2 (U phase), equal to
 // (p_k, M p_k) by Eq. M.  alpha_k = rz_k / (p_k, q_k) and 1/rz_k are
 // computed by two threads at once.  Returns false (uniformly) on rz == 0
 // (converged) or breakdown; CTA 0 records alpha_k, 1/rz_k and (p_k, q_k).
 // ---------------------------------------------------------------------------
 template <typename T, typename S>
-__device__ __noinline__ bool phase_C(const Args<T, S> &A, const Basis &b, int k, T *sm, Scal &sc)
+__device__ __noinline__ bool phase_C(const Args<T, S> &A, const Basis &b, int k, T *sm, Scal &sc,
+                                     bool rz_in_sc = false)
 {
     double *red = sc.red;  // [0] ws, [1] pd, [2] rz0 (k = 0)
     reduce_ranges(A.part, A.ncta, {kSlotB + (k & 1), 1, red}, {kSlotA + (k & 1) * 2, k == 0 ? 2 : 1, red + 1});
     if (threadIdx.x == 0) {
-        sc.rz = k == 0 ? red[2] : ldcgd(A.rec->rz + k);
+        // rz_k: from U_k in this CTA's shared memory (persistent kernel) or the record
+        sc.rz = k == 0 ? red[2] : (rz_in_sc ? sc.rz : ldcgd(A.rec->rz + k));
         sc.pq = red[0] + red[1];
     }
     __syncthreads();
     if (threadIdx.x == 0) sc.alpha = sc.rz / sc.pq;
-    if (threadIdx.x == 32) red[3] = 1.0 / sc.rz;
+    if (threadIdx.x == 32) sc.rinv = red[3] = 1.0 / sc.rz;
     __syncthreads();
     if (threadIdx.x == 0) {
         sc.stop = 0;
@@ -440,9 +445,10 @@ __device__ __noinline__ void phase_D(const Args<T, S> &A, T *sm)
 // E_k: q_k = wq + alpha D p_k (stored in the basis slot), c += alpha p,
 // r -= alpha q, and the inner products of the next step.
 template <typename T, typename S, bool ALL>
-__device__ __noinline__ void phase_E_impl(const Args<T, S> &A, const Basis &b, int k, double *sred)
+__device__ __noinline__ void phase_E_impl(const Args<T, S> &A, const Basis &b, int k, double *sred,
+                                         const double *alpha_sc)
 {
-    const T alpha = (T)ldcgd(A.rec->alpha + k);
+    const T alpha = (T)(alpha_sc ? *alpha_sc : ldcgd(A.rec->alpha + k));
     const T *pk = newP(A, b, k);
     T *qk = newQ(A, b, k);
     const int kv = b.kv;
@@ -508,12 +514,12 @@ __device__ __noinline__ void phase_E_impl(const Args<T, S> &A, const Basis &b, i
 }
 
 template <typename T, typename S>
-__device__ void phase_E(const Args<T, S> &A, const Basis &b, int k, double *sred)
+__device__ void phase_E(const Args<T, S> &A, const Basis &b, int k, double *sred, const double *alpha_sc = nullptr)
 {
     if (A.recycle_all)
-        phase_E_impl<T, S, true>(A, b, k, sred);
+        phase_E_impl<T, S, true>(A, b, k, sred, alpha_sc);
     else
-        phase_E_impl<T, S, false>(A, b, k, sred);
+        phase_E_impl<T, S, false>(A, b, k, sred, alpha_sc);
 }
 
 // Stats and the recycled-basis metadata for the next time step (CTA 0).
