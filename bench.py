@@ -144,11 +144,35 @@ def dist_setup(args):
     return ws, rank, local
 
 
+def max_over_ranks(total_ms, ws, device):
+    """The timed region's length as the job sees it: the maximum over ranks
+    (all-reduce MAX, then a barrier).  Replicas share no data; this is the only
+    collective of the measurement."""
+    if ws <= 1:
+        return total_ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.barrier()
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, ws, max_ms):
+    """Units of all ranks per second over the slowest rank's time."""
+    return ws * units_per_rank / (max_ms / 1e3)
+
+
 def make_frames(geom, nframes, seed, device):
     from synth import FrozenFlowSensors
     sim = FrozenFlowSensors(geom, seed=seed, device=device)
-    s, w = sim.sequence(nframes, seed=seed + 1)
+    s, w = sim.sequence_chunked(nframes, seed=seed + 1, dtype=torch_float64())
     return s, w
+
+
+def torch_float64():
+    import torch
+    return torch.float64
 
 
 def time_solves(f, frames, dtype, args, nwarm, nsteps, aug, flush_buf, stats_buf, rtol):
@@ -206,17 +230,13 @@ def run_ours(args):
                                args.rtol)
     clocks = clk.stop() if clk else None
     total_ms = sum(times)
-    if ws > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-        torch.distributed.barrier()
+    total_ms = max_over_ranks(total_ms, ws, "cuda")
     bad = [s for s in stats if s["status"] != 0]
     if bad:
         raise RuntimeError("device-side error in a timed frame: %s" % bad[0])
     iters = [s["iterations"] for s in stats]
     relres = [s["rel_res"] for s in stats]
-    fps = ws * args.steps / (total_ms / 1e3)
+    fps = whole_job_rate(args.steps, ws, total_ms)
     us_frame = total_ms / args.steps * 1e3
 
     # roofline of the dominant kernel (the persistent solver kernel; one launch per frame)
@@ -423,7 +443,7 @@ def run_reference(args):
     if args.snr:
         geom.snr = args.snr
     sim = FrozenFlowSensors(geom, seed=100)
-    s, w = sim.sequence(args.warmup + args.steps, seed=101)
+    s, w = sim.sequence_chunked(args.warmup + args.steps, seed=101, dtype=torch_float64())
     s = s.numpy()
     o = Oracle(geom, w)
     st = o.new_state(args.k)
