@@ -17,6 +17,7 @@
  *   - diagonal prior D, modified Jacobi preconditioner J      (Sec. 3, Sec. 4)
  *   - PCG (Algorithm 1) and augmented PCG (Algorithm 2)      (Sec. 4)
  *   - warm-restart residual of the reconstructor loop        (Algorithm 3)
+ *   - pseudo-open-loop slopes, fitting, gain control          (Algorithm 3)
  * Where the paper is silent or garbled the reading is stated beside the code.
  */
 #include <math.h>
@@ -374,6 +375,69 @@ void orc_rhs(const orc_ctx *c, const double *s_in, double *b)
     W_invT(c, u, b);
     free(s);
     free(u);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Mirror side of the reconstructor loop (Algorithm 3)                       */
+/* Reading: one deformable mirror conjugated to the ground whose actuators   */
+/* sit on the (n_s+1)^2 pupil nodes (the subaperture corners); the phase it  */
+/* adds at a pupil node is its actuator value there, the same for every      */
+/* guide star (no cone, no shift at height 0).                               */
+/* ------------------------------------------------------------------------ */
+
+/* Fitting step a~ = F W^{-1} c: the on-axis projection (direction 0, no cone)
+ * of every layer onto the actuators, bilinear on each layer grid.  Returns
+ * ORC_ERR_GEOMETRY if an actuator projects outside a layer grid. */
+int orc_fit(const orc_ctx *c, const double *coef, double *a)
+{
+    int m = c->p.n_sub + 1;
+    double *nodal = malloc(sizeof(double) * c->n);
+    W_inv(c, coef, nodal);
+    int st = ORC_OK;
+    for (int i = 0; i < m && st == ORC_OK; i++) {
+        for (int j = 0; j < m; j++) {
+            double x = pupil_coord(c, j), y = pupil_coord(c, i), v = 0.0;
+            for (int l = 0; l < c->p.n_layers; l++) {
+                int n = c->lay_n[l];
+                double d = c->lay_d[l];
+                double fx = x / d + 0.5 * n, fy = y / d + 0.5 * n;
+                int kx = (int)floor(fx), ky = (int)floor(fy);
+                double wx = fx - kx, wy = fy - ky;
+                if (kx < 0 || ky < 0 || kx + 1 > n - 1 || ky + 1 > n - 1) {
+                    st = ORC_ERR_GEOMETRY;
+                    break;
+                }
+                const double *L = nodal + c->lay_off[l];
+                v += (1 - wy) * ((1 - wx) * L[ky * n + kx] + wx * L[ky * n + kx + 1]) +
+                     wy * ((1 - wx) * L[(ky + 1) * n + kx] + wx * L[(ky + 1) * n + kx + 1]);
+            }
+            a[i * m + j] = v;
+        }
+    }
+    free(nodal);
+    return st;
+}
+
+/* Pseudo-open-loop measurements (closed loop): s_out = s + Gamma a for every
+ * guide star, a the mirror shape applied two steps earlier. */
+void orc_pol_slopes(const orc_ctx *c, const double *s, const double *a, double *s_out)
+{
+    int ns = c->p.n_sub;
+    long per = 2L * ns * ns;
+    double *ga = malloc(sizeof(double) * per);
+    orc_gamma_fwd(ns, a, ga);
+    for (int g = 0; g < c->p.n_gs; g++)
+        for (long e = 0; e < per; e++) s_out[g * per + e] = s[g * per + e] + ga[e];
+    free(ga);
+}
+
+/* Gain control: closed loop a_next = a_i + gain (a~ - a_{i-1}); open loop
+ * a_next = (1 - gain) a_i + gain a~. */
+void orc_control(long na, int closed, double gain, const double *a_im1, const double *a_i,
+                 const double *a_fit, double *a_next)
+{
+    for (long e = 0; e < na; e++)
+        a_next[e] = closed ? a_i[e] + gain * (a_fit[e] - a_im1[e]) : (1.0 - gain) * a_i[e] + gain * a_fit[e];
 }
 
 /* ------------------------------------------------------------------------ */

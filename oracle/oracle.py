@@ -100,6 +100,10 @@ def _load():
             lib.orc_solve.argtypes = [vp, _dp, _dp, _dp, _dp, _dp, _dp, _dp, C.c_int, _ip,
                                       C.POINTER(_Opts), C.POINTER(_Stats), _dp]
             lib.orc_solve.restype = C.c_int
+            lib.orc_fit.argtypes = [vp, _dp, _dp]
+            lib.orc_fit.restype = C.c_int
+            lib.orc_pol_slopes.argtypes = [vp, _dp, _dp, _dp]
+            lib.orc_control.argtypes = [C.c_long, C.c_int, C.c_double, _dp, _dp, _dp, _dp]
             _lib = lib
     return _lib
 
@@ -247,6 +251,35 @@ class Oracle:
 
     def apply_op(self, x):
         return self._unary("orc_apply_op", x, self.n)
+
+    # -- mirror side of Algorithm 3 (one ground DM on the pupil nodes) -------
+    @property
+    def n_actuators(self):
+        return (self.n_sub + 1) ** 2
+
+    def fit(self, c):
+        """a~ = F W^{-1} c (on-axis projection of the layers onto the actuators)."""
+        c = _f64(c)
+        a = np.zeros(self.n_actuators)
+        st = self._lib.orc_fit(self._h, _ptr(c), _ptr(a))
+        if st != 0:
+            raise ValueError("fitting direction outside a layer grid")
+        return a
+
+    def pol_slopes(self, s, a):
+        """s + Gamma a for every guide star (pseudo-open-loop measurements)."""
+        s, a = _f64(s), _f64(a)
+        out = np.zeros_like(s)
+        self._lib.orc_pol_slopes(self._h, _ptr(s), _ptr(a), _ptr(out))
+        return out
+
+    def control(self, closed, gain, a_im1, a_i, a_fit):
+        """Gain control of Algorithm 3 (closed or open loop)."""
+        a_im1, a_i, a_fit = _f64(a_im1), _f64(a_i), _f64(a_fit)
+        out = np.zeros_like(a_i)
+        self._lib.orc_control(a_i.size, 1 if closed else 0, float(gain), _ptr(a_im1), _ptr(a_i),
+                              _ptr(a_fit), _ptr(out))
+        return out
 
     def rhs(self, s):
         return self._unary("orc_rhs", s, self.n)
