@@ -276,6 +276,7 @@ def run_ours(args):
 
     if rank == 0:
         out["e2e"] = run_e2e(f, geom, frames, sdt, args, aug)
+        out["algorithm3"] = run_algorithm3(f, frames, sdt, args, aug, flush)
         if not args.no_compare:
             out["compare"] = run_compare(geom, w, frames, args, stats_buf, flush)
         if not args.no_cpu and ws == 1:
@@ -385,6 +386,56 @@ def run_e2e(f, geom, frames, sdt, args, aug):
     esz = torch.tensor([], dtype=sdt).element_size()
     return {"value": K / (ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": f.n_slopes * esz,
             "d2h_bytes_per_step": f.n * c.element_size(), "us_per_frame": ms / K * 1e3}
+
+
+def run_algorithm3(f, frames, sdt, args, aug, flush):
+    """Whole closed-loop time steps of Algorithm 3 on the device: pseudo-open-loop
+    slopes, the solve, fitting onto the ground mirror and gain control (gain
+    0.4), per-frame CUDA events, L2 flushed before every frame.  The frames'
+    slopes are open-loop; the closed-loop measurement s - Gamma a^(i-1) is
+    formed before each timed step."""
+    import torch
+    K = min(args.steps, 200)
+    sl = frames.to(sdt)
+    c = torch.zeros(f.n, dtype=f.dtype, device="cuda")
+    st = f.new_state(args.k)
+    stats = f.new_stats()
+    mir = [f.new_mirror() for _ in range(3)]  # a^(i-1), a^(i), next (rotated, no copies)
+    a_f, neg = f.new_mirror(), f.new_mirror()
+    s_cl, s_pol = torch.empty_like(sl[0]), torch.empty_like(sl[0])
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+
+    def plant(t):
+        # the sensors see the atmosphere minus the mirror applied two steps
+        # earlier (outside the timed region: this is the telescope, not the
+        # reconstructor)
+        torch.neg(mir[0], out=neg)
+        f.pol_slopes(sl[t], neg, out=s_cl)
+
+    def step(t):
+        f.pol_slopes(s_cl, mir[0], out=s_pol)
+        f.solve(s_pol, c, st, args.max_iter, rtol=args.rtol, augmented=aug,
+                persistent=args.launch == "persistent", stats=stats)
+        f.fit(c, out=a_f)
+        f.control(True, 0.4, mir[0], mir[1], a_f, out=mir[2])
+        mir[:] = [mir[1], mir[2], mir[0]]
+
+    for t in range(args.warmup):
+        plant(t)
+        step(t)
+    torch.cuda.synchronize()
+    for k in range(K):
+        plant(args.warmup + k)
+        if flush is not None:
+            flush.zero_()
+        ev[k][0].record()
+        step(args.warmup + k)
+        ev[k][1].record()
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    it = f.read_stats(stats)["iterations"]
+    return {"us_per_frame": ms / K * 1e3, "frames_per_s": K / (ms / 1e3), "frames": K, "gain": 0.4,
+            "loop": "closed", "iterations_last_frame": it, "gpu_launches_per_frame": 1 + 1 + 2 + 1}
 
 
 def run_compare(geom, w, frames, args, stats_buf, flush):

@@ -164,6 +164,32 @@ int fewha_apply_op_multi(void *handle, const void *x, long ldx, void *y, long ld
 /* b = W^{-T} A^T C_eta^{-1} s (right-hand side of Eq. fewha; Algorithm 3). */
 int fewha_rhs(void *handle, const void *s, void *b, cudaStream_t stream);
 
+/* Mirror side of the reconstructor loop (Algorithm 3).  Reading of the
+ * fitting operator F, which the paper names but does not write out: one
+ * deformable mirror conjugated to the ground whose actuators sit on the
+ * (n_s+1)^2 pupil nodes (the subaperture corners, Fried geometry); the phase it
+ * adds at a pupil node is the actuator value there, the same for every guide
+ * star.  Mirror vectors (n_actuators, row-major (n_s+1) x (n_s+1)) are device
+ * arrays of the working precision's vector type (double for FEWHA_F64, float
+ * otherwise); slopes use the slope type of fewha_solve.
+ *
+ * fewha_n_actuators: (n_s+1)^2.
+ * fewha_fit: a_fit = F W^{-1} c, the on-axis projection (direction 0, no cone)
+ *   of every layer onto the actuators, bilinear on each layer grid (the
+ *   fitting step of Algorithm 3).  FEWHA_ERR_GEOMETRY if an actuator projects
+ *   outside a layer grid.  c 16-byte aligned.
+ * fewha_pol_slopes: s_out = s + Gamma a_prev for every guide star (the
+ *   pseudo-open-loop measurements of a closed loop; a_prev is the mirror shape
+ *   applied two steps earlier).  s_out may equal s.
+ * fewha_control: closed != 0: a_next = a_i + gain (a_fit - a_{i-1}); closed ==
+ *   0: a_next = (1 - gain) a_i + gain a_fit (gain control); 0 <= gain <= 1.
+ * All asynchronous on `stream`; FEWHA_ERR_ARG for NULL handles or pointers. */
+long fewha_n_actuators(const void *handle);
+int fewha_fit(void *handle, const void *c, void *a_fit, cudaStream_t stream);
+int fewha_pol_slopes(void *handle, const void *s, const void *a_prev, void *s_out, cudaStream_t stream);
+int fewha_control(void *handle, int closed, double gain, const void *a_im1, const void *a_i, const void *a_fit,
+                  void *a_next, cudaStream_t stream);
+
 /* One reconstructor time step (Algorithm 3, RHS to augPCG):
  *   b = rhs(s); r0 = (b - b_prev) + r_prev; b_prev <- b;
  *   (aug)PCG from the warm start c, updating c (in/out, device, n) and r_prev;

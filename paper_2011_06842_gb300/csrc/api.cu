@@ -195,6 +195,32 @@ int fewha_apply_op_multi(void *handle, const void *x, long ldx, void *y, long ld
     return h->w()->apply_multi(x, ldx, y, ldy, nvec, stream);
 }
 
+long fewha_n_actuators(const void *handle)
+{
+    if (!handle) return -1;
+    const long m = static_cast<const Handle *>(handle)->plan.m;
+    return m * m;
+}
+
+int fewha_fit(void *handle, const void *c, void *a_fit, cudaStream_t stream)
+{
+    if (!handle || !c || !a_fit || !aligned16(c)) return FEWHA_ERR_ARG;
+    return static_cast<Handle *>(handle)->w()->fit(c, a_fit, stream);
+}
+
+int fewha_pol_slopes(void *handle, const void *s, const void *a_prev, void *s_out, cudaStream_t stream)
+{
+    if (!handle || !s || !a_prev || !s_out) return FEWHA_ERR_ARG;
+    return static_cast<Handle *>(handle)->w()->pol_slopes(s, a_prev, s_out, stream);
+}
+
+int fewha_control(void *handle, int closed, double gain, const void *a_im1, const void *a_i, const void *a_fit,
+                  void *a_next, cudaStream_t stream)
+{
+    if (!handle || !a_im1 || !a_i || !a_fit || !a_next || !(gain >= 0.0 && gain <= 1.0)) return FEWHA_ERR_ARG;
+    return static_cast<Handle *>(handle)->w()->control(closed ? 1 : 0, gain, a_im1, a_i, a_fit, a_next, stream);
+}
+
 int fewha_rhs(void *handle, const void *s, void *b, cudaStream_t stream)
 {
     if (!handle || !s || !b || !aligned16(b)) return FEWHA_ERR_ARG;

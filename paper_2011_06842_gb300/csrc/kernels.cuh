@@ -141,6 +141,69 @@ __global__ void __launch_bounds__(kThreads, 1) k_multi_fdwt(const __grid_constan
     });
 }
 
+// --- mirror side of the reconstructor loop (Algorithm 3) --------------------
+// One deformable mirror conjugated to the ground with its actuators on the
+// (n_s+1)^2 pupil nodes (reading of the fitting operator F).
+template <typename T>
+struct FitTab {
+    long off[FEWHA_MAX_LAYERS];
+    int n[FEWHA_MAX_LAYERS];
+    int L, m;
+    const int *fk;  // [L][m] lower node of pupil index j (both axes)
+    const T *fw;    // [L][m] fractional position
+};
+
+// a~ = F W^{-1} c with nodal = W^{-1} c already in place: on-axis bilinear
+// sample of every layer at every actuator, summed over layers.
+template <typename T, typename S>
+__global__ void k_fit(const __grid_constant__ FitTab<T> F, const S *__restrict__ nodal, T *__restrict__ a)
+{
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= F.m * F.m) return;
+    const int i = e / F.m, j = e - i * F.m;
+    T v = 0;
+    for (int l = 0; l < F.L; l++) {
+        const int n = F.n[l];
+        const int kx = F.fk[l * F.m + j], ky = F.fk[l * F.m + i];
+        const T wx = F.fw[l * F.m + j], wy = F.fw[l * F.m + i];
+        const S *Lp = nodal + F.off[l] + (long)ky * n + kx;
+        const T v00 = Cv<S>::ld(Lp[0]), v01 = Cv<S>::ld(Lp[1]);
+        const T v10 = Cv<S>::ld(Lp[n]), v11 = Cv<S>::ld(Lp[n + 1]);
+        v += (T(1) - wy) * ((T(1) - wx) * v00 + wx * v01) + wy * ((T(1) - wx) * v10 + wx * v11);
+    }
+    a[e] = v;
+}
+
+// Pseudo-open-loop slopes: s_out = s + Gamma a for every guide star (the
+// ground mirror adds the same phase to every sensor).
+template <typename T, typename S>
+__global__ void k_pol(const S *s_in, const T *__restrict__ a, S *s_out, int G, int ns)  // s_out may be s_in
+{
+    const int m = ns + 1, per = ns * ns;
+    const long total = (long)G * per;
+    for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
+        const int g = (int)(idx / per), e = (int)(idx - (long)g * per);
+        const int i = e / ns, j = e - i * ns;
+        const T p00 = a[i * m + j], p01 = a[i * m + j + 1];
+        const T p10 = a[(i + 1) * m + j], p11 = a[(i + 1) * m + j + 1];
+        const T gx = T(0.5) * ((p01 - p00) + (p11 - p10));
+        const T gy = T(0.5) * ((p10 - p00) + (p11 - p01));
+        const size_t b = (size_t)g * 2 * per;
+        s_out[b + e] = Cv<S>::st(Cv<S>::ld(s_in[b + e]) + gx);
+        s_out[b + per + e] = Cv<S>::st(Cv<S>::ld(s_in[b + per + e]) + gy);
+    }
+}
+
+// Gain control: closed loop a_next = a_i + gain (a~ - a_{i-1}); open loop
+// a_next = (1 - gain) a_i + gain a~.
+template <typename T>
+__global__ void k_control(int closed, T gain, const T *__restrict__ am1, const T *__restrict__ ai,
+                          const T *__restrict__ af, T *__restrict__ an, int na)
+{
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < na; e += gridDim.x * blockDim.x)
+        an[e] = closed ? ai[e] + gain * (af[e] - am1[e]) : (T(1) - gain) * ai[e] + gain * af[e];
+}
+
 // --- solver phases, one kernel each (FEWHA_LAUNCH_PHASES) -------------------
 #define FEWHA_PHASE_GUARD                                             \
     __shared__ Scal sc;                                               \
@@ -377,6 +440,11 @@ struct ImplBase {
     virtual int init(int grid) = 0;
     virtual int get_invJ(double *host) const = 0;
     virtual int apply(const void *x, void *y, cudaStream_t s) = 0;
+    // mirror side of Algorithm 3 (ground DM on the pupil nodes)
+    virtual int fit(const void *c, void *a, cudaStream_t s) = 0;
+    virtual int pol_slopes(const void *s_in, const void *a, void *s_out, cudaStream_t s) = 0;
+    virtual int control(int closed, double gain, const void *am1, const void *ai, const void *af, void *an,
+                        cudaStream_t s) = 0;
     // y_v = M x_v for v < nvec (x_v = x + v*ldx, y_v = y + v*ldy), nvec <= kMaxVec
     virtual int apply_multi(const void *x, long ldx, void *y, long ldy, int nvec, cudaStream_t s) = 0;
     virtual int rhs(const void *sl, void *b, cudaStream_t s) = 0;
@@ -410,6 +478,8 @@ struct Impl : ImplBase {
     int ncta = 1;
     size_t smem = 0;
     std::vector<void *> owned;
+    const int *fit_k = nullptr;          // fitting tables (device)
+    const T *fit_w = nullptr;
     unsigned char *multi_buf = nullptr;  // scratch of apply_multi (allocated on first use)
     size_t multi_stride = 0;
 
@@ -571,6 +641,10 @@ struct Impl : ImplBase {
                     }
                 }
             if ((st = up(alo, &G.adj_lo)) || (st = up(acnt, &G.adj_cnt)) || (st = up(aw, &G.adj_w))) return st;
+            {
+                std::vector<T> fw2(P.fit_w.begin(), P.fit_w.end());
+                if ((st = up(P.fit_k, &fit_k)) || (st = up(fw2, &fit_w))) return st;
+            }
         }
         if ((st = up(bl, &G.band_layer)) || (st = up(br0, &G.band_row0)) || (st = up(brs, &G.band_rows)) ||
             (st = up(bilo, &G.band_ilo)) || (st = up(bihi, &G.band_ihi)))
@@ -687,6 +761,43 @@ struct Impl : ImplBase {
         k_wfs<T, S, false><<<ncta, kThreads, smem, s>>>(A);
         k_gather<T, S><<<ncta, kThreads, smem, s>>>(A);
         k_fdwt<T, S, false><<<ncta, kThreads, smem, s>>>(A);
+        return launch_check();
+    }
+
+    int fit(const void *c, void *a, cudaStream_t s) override
+    {
+        if (!P.fit_ok) return FEWHA_ERR_GEOMETRY;
+        Args<T, S> A = base;
+        A.x = static_cast<const T *>(c);
+        CK(cudaMemsetAsync(A.rec, 0, offsetof(Record, rz), s));
+        k_apply_idwt<T, S><<<ncta, kThreads, smem, s>>>(A);  // nodal = W^{-1} c
+        FitTab<T> F{};
+        for (int l = 0; l < P.L; l++) {
+            F.off[l] = P.lay_off[l];
+            F.n[l] = P.geom.layers[l].n;
+        }
+        F.L = P.L;
+        F.m = P.m;
+        F.fk = fit_k;
+        F.fw = fit_w;
+        k_fit<T, S><<<(P.m * P.m + 255) / 256, 256, 0, s>>>(F, base.nodal, static_cast<T *>(a));
+        return launch_check();
+    }
+
+    int pol_slopes(const void *s_in, const void *a, void *s_out, cudaStream_t s) override
+    {
+        k_pol<T, S><<<256, 256, 0, s>>>(static_cast<const S *>(s_in), static_cast<const T *>(a),
+                                        static_cast<S *>(s_out), P.G, P.ns);
+        return launch_check();
+    }
+
+    int control(int closed, double gain, const void *am1, const void *ai, const void *af, void *an,
+                cudaStream_t s) override
+    {
+        const int na = P.m * P.m;
+        k_control<T><<<(na + 255) / 256, 256, 0, s>>>(closed, (T)gain, static_cast<const T *>(am1),
+                                                      static_cast<const T *>(ai), static_cast<const T *>(af),
+                                                      static_cast<T *>(an), na);
         return launch_check();
     }
 

@@ -225,6 +225,25 @@ int build_plan(const fewha_geometry &g, Plan &p)
         }
     }
 
+    // fitting step of Algorithm 3 (reading: one DM conjugated to the ground,
+    // actuators on the pupil nodes): on-axis projection, no cone, no shift
+    p.fit_k.assign((size_t)p.L * p.m, 0);
+    p.fit_w.assign((size_t)p.L * p.m, 0.0);
+    p.fit_ok = 1;
+    for (int l = 0; l < p.L; l++) {
+        const int n = g.layers[l].n;
+        for (int j = 0; j < p.m; j++) {
+            const double f = (-0.5 * g.D + j * p.ds) / p.lay_d[l] + 0.5 * n;
+            const int kk = (int)std::floor(f);
+            if (kk < 0 || kk + 1 > n - 1) {
+                p.fit_ok = 0;
+                continue;
+            }
+            p.fit_k[(size_t)l * p.m + j] = kk;
+            p.fit_w[(size_t)l * p.m + j] = f - kk;
+        }
+    }
+
     // prior D (reading: Kolmogorov spectrum in the wavelet domain)
     //   D = kappa_l 2^{(11/3) s}, kappa_l = 2^{-(11/3) J} / (0.5 * 6.88 (d_l/r0_l)^{5/3}),
     //   r0_l = r0 cn2_l^{-3/5}, s = 0 approximation, 1..J detail levels coarse to fine.

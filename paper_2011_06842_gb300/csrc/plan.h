@@ -25,6 +25,11 @@ struct Plan {
     // P_g^T ranges, index ((g*L + l)*2 + axis)*FEWHA_MAX_GRID + k: pupil nodes
     // [alo, ahi) whose cell touches layer node k
     std::vector<int> alo, ahi;
+    // fitting onto the ground DM (actuators on the pupil nodes), on-axis: per
+    // (layer l, pupil index j) the lower node and fractional position, both axes
+    std::vector<int> fit_k;
+    std::vector<double> fit_w;
+    int fit_ok = 0;                   // every actuator projects inside every layer grid
     std::vector<double> alpha_d;      // n, alpha * D
     // preconditioner sampling: class of every coefficient, and the sampled
     // coefficients (global index, class)

@@ -110,6 +110,14 @@ def load_library(path=LIB_PATH):
     lib.fewha_batch_launch.restype = C.c_int
     lib.fewha_batch_destroy.argtypes = [vp]
     lib.fewha_batch_destroy.restype = None
+    lib.fewha_n_actuators.argtypes = [vp]
+    lib.fewha_n_actuators.restype = C.c_long
+    lib.fewha_fit.argtypes = [vp, vp, vp, vp]
+    lib.fewha_fit.restype = C.c_int
+    lib.fewha_pol_slopes.argtypes = [vp, vp, vp, vp, vp]
+    lib.fewha_pol_slopes.restype = C.c_int
+    lib.fewha_control.argtypes = [vp, C.c_int, C.c_double, vp, vp, vp, vp, vp]
+    lib.fewha_control.restype = C.c_int
     lib.fewha_apply_op_multi.argtypes = [vp, vp, C.c_long, vp, C.c_long, C.c_int, vp]
     lib.fewha_apply_op_multi.restype = C.c_int
     # learned warm start (float pointers as void*, strides and sizes as long/int)
@@ -145,7 +153,8 @@ def exported_symbols():
             "fewha_layer_spacing", "fewha_get_prior", "fewha_get_precond", "fewha_apply_op",
             "fewha_rhs", "fewha_solve", "fewha_set_timeout", "fewha_set_trace", "fewha_apply_op_noalloc", "fewha_batch_create",
             "fewha_batch_ctas", "fewha_batch_solve", "fewha_batch_destroy", "fewha_strerror",
-            "fewha_batch_bind", "fewha_batch_launch",
+            "fewha_batch_bind", "fewha_batch_launch", "fewha_n_actuators", "fewha_fit",
+            "fewha_pol_slopes", "fewha_control",
             "fewha_apply_op_multi", "fewha_conv3x3_fwd", "fewha_conv3x3_bwd_data",
             "fewha_conv3x3_wgrad_workspace", "fewha_conv3x3_bwd_weight", "fewha_relu_bwd",
             "fewha_mse_grad", "fewha_adam_step", "fewha_scale", "fewha_learned_targets",
@@ -299,6 +308,43 @@ class Fewha:
 
     def new_state(self, kcap):
         return FewhaState(self._torch, self.n, kcap, self.dtype, self.device)
+
+    # -- mirror side of Algorithm 3 (ground DM on the pupil nodes) ---------------
+    @property
+    def n_actuators(self):
+        return self.lib.fewha_n_actuators(self._h)
+
+    def new_mirror(self):
+        return self._torch.zeros(self.n_actuators, dtype=self.dtype, device=self.device)
+
+    def fit(self, c, out=None):
+        """a~ = F W^{-1} c (fitting step)."""
+        a = out if out is not None else self.new_mirror()
+        self._check(self.lib.fewha_fit(self._h, self._vec(c, self.n, self.dtype, "c"),
+                                       self._vec(a, self.n_actuators, self.dtype, "a"),
+                                       _stream_ptr(self._torch)), "fewha_fit")
+        return a
+
+    def pol_slopes(self, s, a_prev, out=None):
+        """s + Gamma a_prev for every guide star (pseudo-open-loop slopes)."""
+        o = out if out is not None else self._torch.empty_like(s)
+        self._check(self.lib.fewha_pol_slopes(self._h, self._vec(s, self.n_slopes, self.slope_dtype, "s"),
+                                              self._vec(a_prev, self.n_actuators, self.dtype, "a_prev"),
+                                              self._vec(o, self.n_slopes, self.slope_dtype, "out"),
+                                              _stream_ptr(self._torch)), "fewha_pol_slopes")
+        return o
+
+    def control(self, closed, gain, a_im1, a_i, a_fit, out=None):
+        """Gain control of Algorithm 3; returns the next mirror shape."""
+        na = self.n_actuators
+        o = out if out is not None else self.new_mirror()
+        self._check(self.lib.fewha_control(self._h, 1 if closed else 0, float(gain),
+                                           self._vec(a_im1, na, self.dtype, "a_im1"),
+                                           self._vec(a_i, na, self.dtype, "a_i"),
+                                           self._vec(a_fit, na, self.dtype, "a_fit"),
+                                           self._vec(o, na, self.dtype, "out"), _stream_ptr(self._torch)),
+                    "fewha_control")
+        return o
 
     def new_stats(self):
         return self._torch.zeros(STATS_BYTES, dtype=self._torch.uint8, device=self.device)
