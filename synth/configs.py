@@ -90,6 +90,20 @@ def elt() -> Geometry:
                     r0=0.129, L0=25.0, k_recycle=8, wind=_winds(9, 1001))
 
 
+def ltao() -> Geometry:
+    """The paper's LTAO asterism (Sec. 5.1): 3 NGS on a 10' diameter circle and
+    6 LGS at 90 km on a 7.5' diameter circle, every sensor 80x80; 39 m pupil with
+    28 % obstruction; the 9-layer profile of the ELT workload (128^2 up to 8 km,
+    64^2 above; the wide NGS field makes the high layers' grids coarser)."""
+    hs = [2000.0 * i for i in range(9)]
+    w = [math.exp(-h / 4000.0) for h in hs]
+    tot = sum(w)
+    layers = [Layer(h, wi / tot, 128 if h <= 8000.0 else 64, 5) for h, wi in zip(hs, w)]
+    return Geometry("ltao", D=39.0, obstruction=0.28, n_sub=80,
+                    gs=_ring(3, 300 * ARCSEC, 0.0, phase=math.pi / 2) + _ring(6, 225 * ARCSEC, 90000.0),
+                    layers=layers, r0=0.129, L0=25.0, k_recycle=8, wind=_winds(9, 1005))
+
+
 def medium() -> Geometry:
     """16 m, 40x40 SH, 4 LGS at 90 km on a 45'' ring, 5 layers on 64x64 grids
     (0-12 km), Daubechies-3 with 4 levels (the mid-size batched instance)."""
@@ -123,7 +137,7 @@ def mixed_ngs_lgs() -> Geometry:
                     r0=0.14, wind=_winds(3, 1004))
 
 
-CONFIGS = {"tiny": tiny, "elt": elt, "medium": medium, "micro": micro, "mixed": mixed_ngs_lgs}
+CONFIGS = {"tiny": tiny, "elt": elt, "ltao": ltao, "medium": medium, "micro": micro, "mixed": mixed_ngs_lgs}
 
 
 def get(name: str) -> Geometry:

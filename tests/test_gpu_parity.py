@@ -63,7 +63,7 @@ def test_tables_match_oracle(lib, name):
 
 
 @pytest.mark.parametrize("prec", ["f64", "f32"])
-@pytest.mark.parametrize("name", ["micro", "tiny", "mixed"])
+@pytest.mark.parametrize("name", ["micro", "tiny", "mixed", "ltao"])
 def test_apply_op_and_rhs(lib, name, prec):
     geom, s, w, o = setup(name)
     f = lib.Fewha(geom, w, prec)
@@ -124,6 +124,18 @@ def test_solve_sequence_f64(lib, name, aug, persistent):
     assert rel(P.cpu().numpy(), st_o["P"][:kv]) < 1e-9
     assert rel(Q.cpu().numpy(), st_o["Q"][:kv]) < 1e-9
     assert rel(pq.cpu().numpy(), st_o["pq"][:kv]) < 1e-10
+
+
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-10), ("f32", 1e-5)])
+def test_ltao_mixed_asterism_sequence(lib, prec, tol):
+    """The paper's LTAO asterism at ELT size (3 NGS + 6 LGS, 80x80 sensors, 9
+    layers): 3 frames of 4 augmented PCG iterations equal the oracle's."""
+    geom, s, w, o = setup("ltao")
+    f = lib.Fewha(geom, w, prec)
+    res = _run_sequence(lib, o, f, s, 3, max_iter=4, aug=True, kcap=8, persistent=True, prec=prec)
+    for ro, rg, ec, er, st_o, st_g in res:
+        assert rg["iterations"] == ro["iterations"]
+        assert ec < tol, ec
 
 
 def test_solve_recycle_all_f64(lib):
