@@ -56,6 +56,9 @@ def parse():
     p.add_argument("--learned-train", type=int, default=20000, help="training frames")
     p.add_argument("--learned-eval", type=int, default=500, help="held-out frames")
     p.add_argument("--epochs", type=int, default=2)
+    p.add_argument("--diagnostics", action="store_true",
+                   help="condition numbers kappa_0..2 of the configuration (Lanczos on the FP64 operator)")
+    p.add_argument("--lanczos-steps", type=int, default=300)
     return p.parse_args()
 
 
@@ -576,8 +579,38 @@ def run_learned(args):
     return out
 
 
+def run_diagnostics(args):
+    """kappa_0 = cond(M), kappa_1 = cond(J^{-1/2} M J^{-1/2}), kappa_2 with the
+    recycled basis after 5 time steps (Sec. 6.2); Lanczos lower bounds."""
+    import torch
+    from paper_2011_06842_gb300 import Fewha, build
+    from paper_2011_06842_gb300.diagnostics import condition_numbers
+    from synth import configs
+    build.build()
+    geom = configs.get(args.config)
+    if args.snr:
+        geom.snr = args.snr
+    frames, w = make_frames(geom, 5, seed=100, device="cuda")
+    f = Fewha(geom, w, "f64")
+    st = f.new_state(args.k)
+    c = torch.zeros(f.n, dtype=torch.float64, device="cuda")
+    for t in range(5):
+        f.solve(frames[t], c, st, args.max_iter, rtol=args.rtol)
+    P, Q, _ = st.basis()
+    t0 = time.time()
+    res = condition_numbers(f, basis=(P, Q), steps=args.lanczos_steps)
+    res["seconds"] = time.time() - t0
+    res["config"] = workload_name(geom, args)
+    res["note"] = "Lanczos with %d steps: kappa values are lower bounds" % args.lanczos_steps
+    f.close()
+    return res
+
+
 def main():
     args = parse()
+    if args.diagnostics:
+        print(json.dumps(run_diagnostics(args)))
+        return
     if args.learned:
         print(json.dumps(run_learned(args)))
         return
