@@ -212,6 +212,13 @@ int fewha_solve(void *handle, const void *s, void *c, const fewha_state *state,
  * four staging buffers are still in flight.  Not in the paper: the paper
  * solves one system per time step. */
 int fewha_batch_create(void *const *handles, int n, const int *ctas, void **batch_out);
+/* Same, with the instances in rounds: rounds[i] (0, 1, ...) is the round of
+ * instance i (NULL: all in round 0).  The launch runs round 0's instances,
+ * then, after a barrier over all its CTAs, round 1's on the same CTAs, and so
+ * on; only each round's groups must fit the GPU at once, so a few large
+ * instances can take many CTAs in one round and many small ones the next.
+ * With ctas == NULL the CTAs of each round are split in proportion to work. */
+int fewha_batch_create_rounds(void *const *handles, int n, const int *ctas, const int *rounds, void **batch_out);
 int fewha_batch_ctas(const void *batch, int *ctas_out);
 int fewha_batch_solve(void *batch, const void *const *slopes, void *const *c, const fewha_state *states,
                       const fewha_solve_opts *opts, fewha_stats *stats_dev, cudaStream_t stream);

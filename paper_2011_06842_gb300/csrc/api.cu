@@ -29,14 +29,15 @@ ImplBase *handle_impl(void *handle) { return handle ? static_cast<Handle *>(hand
 // A batch: many instances (handles of one precision on one device) run by one
 // cooperative launch, each by its own group of CTAs.
 struct Batch {
-    int n = 0, total = 0;
+    int n = 0, total = 0, nrounds = 1;  // total: CTAs of the launch (the largest round)
     size_t smem = 0, asz = 0;
     std::vector<ImplBase *> impl;
     std::vector<int> cta0, ncta, ty, tx;
     void *d_args = nullptr;
     void *d_bound = nullptr;  // argument table of fewha_batch_bind (fixed buffers, graph replay)
     bool bound = false;
-    int *d_map = nullptr;
+    int *d_map = nullptr;                 // [nrounds][total] instance of each CTA, -1 idle
+    Record *d_brec = nullptr;             // barrier between rounds
     static constexpr int kRing = 4;  // pinned staging copies of the argument table
     void *h_args[kRing] = {};
     cudaEvent_t ev[kRing] = {};
@@ -46,6 +47,7 @@ struct Batch {
         cudaFree(d_args);
         cudaFree(d_bound);
         cudaFree(d_map);
+        cudaFree(d_brec);
         for (int i = 0; i < kRing; i++) {
             if (h_args[i]) cudaFreeHost(h_args[i]);
             if (ev[i]) cudaEventDestroy(ev[i]);
@@ -245,6 +247,11 @@ int fewha_solve(void *handle, const void *s, void *c, const fewha_state *st, con
 
 int fewha_batch_create(void *const *handles, int n, const int *ctas, void **batch_out)
 {
+    return fewha_batch_create_rounds(handles, n, ctas, nullptr, batch_out);
+}
+
+int fewha_batch_create_rounds(void *const *handles, int n, const int *ctas, const int *rounds, void **batch_out)
+{
     if (!handles || n < 1 || !batch_out) return FEWHA_ERR_ARG;
     *batch_out = nullptr;
     std::unique_ptr<Batch> b(new (std::nothrow) Batch());
@@ -252,6 +259,7 @@ int fewha_batch_create(void *const *handles, int n, const int *ctas, void **batc
     b->n = n;
     int prec = -1;
     std::vector<double> weight(n);
+    std::vector<int> round(n, 0);
     for (int i = 0; i < n; i++) {
         if (!handles[i]) return FEWHA_ERR_ARG;
         Handle *h = static_cast<Handle *>(handles[i]);
@@ -260,8 +268,13 @@ int fewha_batch_create(void *const *handles, int n, const int *ctas, void **batc
         prec = h->w()->precision_id();
         // work of one iteration ~ unknowns + adjoint wavefront nodes
         weight[i] = (double)h->plan.n + (double)h->plan.G * h->plan.m * h->plan.m;
+        if (rounds) {
+            if (rounds[i] < 0 || rounds[i] >= n) return FEWHA_ERR_ARG;
+            round[i] = rounds[i];
+        }
     }
-    // CTA groups: given, or proportional to the work (at least one each)
+    b->nrounds = 1 + *std::max_element(round.begin(), round.end());
+    // CTA groups: given, or per round proportional to the work (at least one each)
     int cap = 0;
     int st = b->impl[0]->batch_capacity(200 * 1024, &cap);
     if (st) return st;
@@ -272,39 +285,51 @@ int fewha_batch_create(void *const *handles, int n, const int *ctas, void **batc
             b->ncta[i] = ctas[i];
         }
     } else {
-        if (n > cap) return FEWHA_ERR_ARG;
-        double wsum = 0;
-        for (double w : weight) wsum += w;
-        int used = 0;
-        for (int i = 0; i < n; i++) {
-            b->ncta[i] = std::max(1, (int)((cap - n) * weight[i] / wsum) + 1);
-            used += b->ncta[i];
-        }
-        while (used > cap) {  // trim the largest groups
-            int j = (int)(std::max_element(b->ncta.begin(), b->ncta.end()) - b->ncta.begin());
-            b->ncta[j]--;
-            used--;
+        for (int r = 0; r < b->nrounds; r++) {
+            int nr = 0;
+            double wsum = 0;
+            for (int i = 0; i < n; i++)
+                if (round[i] == r) nr++, wsum += weight[i];
+            if (nr == 0) continue;
+            if (nr > cap) return FEWHA_ERR_ARG;
+            int used = 0;
+            for (int i = 0; i < n; i++)
+                if (round[i] == r) {
+                    b->ncta[i] = std::max(1, (int)((cap - nr) * weight[i] / wsum) + 1);
+                    used += b->ncta[i];
+                }
+            while (used > cap) {  // trim the largest groups of the round
+                int j = -1;
+                for (int i = 0; i < n; i++)
+                    if (round[i] == r && (j < 0 || b->ncta[i] > b->ncta[j])) j = i;
+                b->ncta[j]--;
+                used--;
+            }
         }
     }
     b->cta0.resize(n);
     b->ty.resize(n);
     b->tx.resize(n);
-    b->total = 0;
+    std::vector<int> used(b->nrounds, 0);
     for (int i = 0; i < n; i++) {
-        b->cta0[i] = b->total;
-        b->total += b->ncta[i];
+        b->cta0[i] = used[round[i]];
+        used[round[i]] += b->ncta[i];
         if ((st = b->impl[i]->tiles_for(b->ncta[i], &b->ty[i], &b->tx[i]))) return st;
         b->smem = std::max(b->smem, b->impl[i]->smem_for(b->ty[i], b->tx[i]));
     }
+    b->total = *std::max_element(used.begin(), used.end());
     if ((st = b->impl[0]->batch_capacity(b->smem, &cap))) return st;
-    if (b->total > cap) return FEWHA_ERR_ARG;  // the groups must be co-resident
+    if (b->total > cap) return FEWHA_ERR_ARG;  // every round's groups must be co-resident
     b->asz = b->impl[0]->args_size();
-    std::vector<int> map(b->total);
+    std::vector<int> map((size_t)b->nrounds * b->total, -1);
     for (int i = 0; i < n; i++)
-        for (int c = 0; c < b->ncta[i]; c++) map[b->cta0[i] + c] = i;
-    if (cudaMalloc(&b->d_args, b->asz * n) != cudaSuccess || cudaMalloc(&b->d_map, sizeof(int) * b->total) != cudaSuccess)
+        for (int c = 0; c < b->ncta[i]; c++) map[(size_t)round[i] * b->total + b->cta0[i] + c] = i;
+    if (cudaMalloc(&b->d_args, b->asz * n) != cudaSuccess ||
+        cudaMalloc(&b->d_map, sizeof(int) * map.size()) != cudaSuccess ||
+        cudaMalloc(&b->d_brec, sizeof(Record)) != cudaSuccess)
         return FEWHA_ERR_NOMEM;
-    if (cudaMemcpy(b->d_map, map.data(), sizeof(int) * b->total, cudaMemcpyHostToDevice) != cudaSuccess)
+    if (cudaMemcpy(b->d_map, map.data(), sizeof(int) * map.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(b->d_brec, 0, sizeof(Record)) != cudaSuccess)
         return FEWHA_ERR_CUDA;
     for (int i = 0; i < Batch::kRing; i++) {
         if (cudaHostAlloc(&b->h_args[i], b->asz * n, cudaHostAllocDefault) != cudaSuccess) return FEWHA_ERR_NOMEM;
@@ -348,7 +373,7 @@ int fewha_batch_solve(void *batch, const void *const *slopes, void *const *c, co
     if (cudaMemcpyAsync(b->d_args, h, b->asz * b->n, cudaMemcpyHostToDevice, stream) != cudaSuccess)
         return FEWHA_ERR_CUDA;
     if (cudaEventRecord(b->ev[slot], stream) != cudaSuccess) return FEWHA_ERR_CUDA;
-    return b->impl[0]->launch_batched(b->d_args, b->d_map, b->n, b->total, b->smem, stream);
+    return b->impl[0]->launch_batched(b->d_args, b->d_map, b->n, b->total, b->smem, b->nrounds, b->d_brec, stream);
 }
 
 int fewha_batch_bind(void *batch, const void *const *slopes, void *const *c, const fewha_state *states,
@@ -383,7 +408,8 @@ int fewha_batch_launch(void *batch, cudaStream_t stream)
     if (!batch) return FEWHA_ERR_ARG;
     Batch *b = static_cast<Batch *>(batch);
     if (!b->bound) return FEWHA_ERR_ARG;
-    return b->impl[0]->launch_batched(b->d_bound, b->d_map, b->n, b->total, b->smem, stream);
+    return b->impl[0]->launch_batched(b->d_bound, b->d_map, b->n, b->total, b->smem, b->nrounds, b->d_brec,
+                                      stream);
 }
 
 void fewha_batch_destroy(void *batch)

@@ -395,20 +395,34 @@ __global__ void __launch_bounds__(kThreads, 1) k_solve_persistent(const __grid_c
 // Many instances in one cooperative launch: CTA c runs instance cta_inst[c]
 // with the group of CTAs [inst.cta0, inst.cta0 + inst.ncta).
 template <typename T, typename S>
-__global__ void __launch_bounds__(kThreads, 1) k_solve_batched(const Args<T, S> *inst, const int *cta_inst)
+__global__ void __launch_bounds__(kThreads, 1) k_solve_batched(const Args<T, S> *inst, const int *cta_inst,
+                                                              int nrounds, int total, Record *brec,
+                                                              unsigned long long timeout_ns)
 {
+    // Instances run in rounds: in round r, CTA c runs instance cta_inst[r * total + c]
+    // (-1: idle in this round); a barrier over the whole launch separates rounds, so
+    // one launch can give a few large instances many CTAs and then the small ones.
     __shared__ Scal sc;
     __shared__ double sred[kSred];
     __shared__ __align__(16) Args<T, S> A;
-    const int i = cta_inst[blockIdx.x];
-    args_to_smem(inst[i], A);
-    solve_body<T, S>(A, sc, sred);
+    for (int r = 0; r < nrounds; r++) {
+        const int i = cta_inst[r * total + blockIdx.x];
+        if (i >= 0) {
+            args_to_smem(inst[i], A);
+            solve_body<T, S>(A, sc, sred);
+        }
+        if (r + 1 < nrounds && !grid_sync(brec, timeout_ns, total, blockIdx.x)) return;
+    }
 }
 
 // Resets the record flags and the barrier of every instance of a batch.
 template <typename T, typename S>
-__global__ void k_batch_reset(const Args<T, S> *inst, int n)
+__global__ void k_batch_reset(const Args<T, S> *inst, int n, Record *brec)
 {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        brec->status = 0;
+        brec->bar.count = brec->bar.gen = 0;
+    }
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         Record *r = inst[i].rec;
         r->status = r->done = r->iters = r->chol_ok = 0;
@@ -464,8 +478,8 @@ struct ImplBase {
                            fewha_stats *stats, int cta0, int ncta, int ty, int tx, size_t smem) const = 0;
     // CTAs that can be co-resident for the batched kernel with `smem` bytes
     virtual int batch_capacity(size_t smem, int *max_ctas) const = 0;
-    virtual int launch_batched(const void *d_args, const int *d_map, int n, int total, size_t smem,
-                               cudaStream_t s) const = 0;
+    virtual int launch_batched(const void *d_args, const int *d_map, int n, int total, size_t smem, int nrounds,
+                               Record *brec, cudaStream_t s) const = 0;
     // y = M x with every scratch buffer carved from caller-provided device
     // memory (no allocation); FEWHA_ERR_SCRATCH if `bytes` is too small.
     virtual int apply_in_scratch(const void *x, void *y, void *scratch, size_t bytes, cudaStream_t s) = 0;
@@ -938,11 +952,11 @@ struct Impl : ImplBase {
         return FEWHA_OK;
     }
 
-    int launch_batched(const void *d_args, const int *d_map, int n, int total, size_t sm,
-                       cudaStream_t s) const override
+    int launch_batched(const void *d_args, const int *d_map, int n, int total, size_t sm, int nrounds,
+                       Record *brec, cudaStream_t s) const override
     {
         const Args<T, S> *args = static_cast<const Args<T, S> *>(d_args);
-        k_batch_reset<T, S><<<(n + 255) / 256, 256, 0, s>>>(args, n);
+        k_batch_reset<T, S><<<(n + 255) / 256, 256, 0, s>>>(args, n, brec);
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(total);
         cfg.blockDim = dim3(kThreads);
@@ -953,7 +967,9 @@ struct Impl : ImplBase {
         attr[0].val.cooperative = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        CK(cudaLaunchKernelEx(&cfg, k_solve_batched<T, S>, args, d_map));
+        // a round may run as long as one time step of its slowest instance
+        const unsigned long long to = base.timeout_ns * 4;
+        CK(cudaLaunchKernelEx(&cfg, k_solve_batched<T, S>, args, d_map, nrounds, total, brec, to));
         return cudaGetLastError() == cudaSuccess ? FEWHA_OK : FEWHA_ERR_CUDA;
     }
 

@@ -100,6 +100,9 @@ def load_library(path=LIB_PATH):
     lib.fewha_set_trace.restype = C.c_int
     lib.fewha_batch_create.argtypes = [C.POINTER(vp), C.c_int, C.POINTER(C.c_int), C.POINTER(vp)]
     lib.fewha_batch_create.restype = C.c_int
+    lib.fewha_batch_create_rounds.argtypes = [C.POINTER(vp), C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                              C.POINTER(vp)]
+    lib.fewha_batch_create_rounds.restype = C.c_int
     lib.fewha_batch_ctas.argtypes = [vp, C.POINTER(C.c_int)]
     lib.fewha_batch_ctas.restype = C.c_int
     lib.fewha_batch_solve.argtypes = [vp, C.POINTER(vp), C.POINTER(vp), C.POINTER(STATE), C.POINTER(OPTS), vp, vp]
@@ -153,7 +156,7 @@ def exported_symbols():
             "fewha_layer_spacing", "fewha_get_prior", "fewha_get_precond", "fewha_apply_op",
             "fewha_rhs", "fewha_solve", "fewha_set_timeout", "fewha_set_trace", "fewha_apply_op_noalloc", "fewha_batch_create",
             "fewha_batch_ctas", "fewha_batch_solve", "fewha_batch_destroy", "fewha_strerror",
-            "fewha_batch_bind", "fewha_batch_launch", "fewha_n_actuators", "fewha_fit",
+            "fewha_batch_bind", "fewha_batch_launch", "fewha_batch_create_rounds", "fewha_n_actuators", "fewha_fit",
             "fewha_pol_slopes", "fewha_control",
             "fewha_apply_op_multi", "fewha_conv3x3_fwd", "fewha_conv3x3_bwd_data",
             "fewha_conv3x3_wgrad_workspace", "fewha_conv3x3_bwd_weight", "fewha_relu_bwd",
@@ -408,7 +411,7 @@ class FewhaBatch:
     """Many instances (Fewha handles of one precision) solved by one
     cooperative launch, each by its own group of CTAs (fewha_batch_*)."""
 
-    def __init__(self, fewhas, ctas=None):
+    def __init__(self, fewhas, ctas=None, rounds=None):
         import torch
         self._torch = torch
         self.fewhas = list(fewhas)
@@ -416,10 +419,12 @@ class FewhaBatch:
         n = len(self.fewhas)
         hs = (C.c_void_p * n)(*[f._h.value for f in self.fewhas])
         cs = (C.c_int * n)(*ctas) if ctas is not None else None
+        rs = (C.c_int * n)(*rounds) if rounds is not None else None
+        self.rounds = list(rounds) if rounds is not None else [0] * n
         b = C.c_void_p()
-        st = self.lib.fewha_batch_create(hs, n, cs, C.byref(b))
+        st = self.lib.fewha_batch_create_rounds(hs, n, cs, rs, C.byref(b))
         if st != 0:
-            raise FewhaError(st, "fewha_batch_create")
+            raise FewhaError(st, "fewha_batch_create_rounds")
         self._b = b
         self.n = n
         self.device = self.fewhas[0].device
@@ -508,11 +513,11 @@ class FewhaBatch:
 
 
 def autotune_batch(fewhas, step, candidates=None, reps=3):
-    """Chooses the CTA groups of a batch by timing: `step(batch)` runs one
-    batched time step; each candidate split (None = the library's work-
-    proportional default, or a list of CTAs per instance) is timed over
-    `reps` steps with CUDA events and the fastest is returned with all
-    timings (ms per step)."""
+    """Chooses the CTA groups (and rounds) of a batch by timing: `step(batch)`
+    runs one batched time step; each candidate (None = the library's work-
+    proportional default, a list of CTAs per instance, or a pair (ctas,
+    rounds)) is timed over `reps` steps with CUDA events.  Returns the fastest
+    as a pair (ctas, rounds) and all timings (ms per step)."""
     import torch
     n = len(fewhas)
     if candidates is None:
@@ -525,8 +530,9 @@ def autotune_batch(fewhas, step, candidates=None, reps=3):
     timings = []
     best, best_ms = None, float("inf")
     for cand in candidates:
+        ctas, rounds = cand if isinstance(cand, tuple) else (cand, None)
         try:
-            b = FewhaBatch(fewhas, cand)
+            b = FewhaBatch(fewhas, ctas, rounds)
         except FewhaError:
             timings.append((cand, None))
             continue
@@ -539,8 +545,8 @@ def autotune_batch(fewhas, step, candidates=None, reps=3):
         e1.record()
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / reps
-        timings.append((b.ctas(), ms))
+        timings.append(((b.ctas(), b.rounds), ms))
         if ms < best_ms:
-            best, best_ms = b.ctas(), ms
+            best, best_ms = (b.ctas(), b.rounds), ms
         b.close()
     return best, timings

@@ -26,8 +26,11 @@ def lib():
     return P
 
 
-@pytest.mark.parametrize("prec,tol,ctas", [("f64", 1e-10, None), ("f32", 1e-5, None), ("f64", 1e-10, [1, 3, 2, 5, 4])])
-def test_batched_matches_oracle(lib, prec, tol, ctas):
+@pytest.mark.parametrize("prec,tol,ctas,rounds", [("f64", 1e-10, None, None), ("f32", 1e-5, None, None),
+                                                 ("f64", 1e-10, [1, 3, 2, 5, 4], None),
+                                                 ("f64", 1e-10, [1, 3, 2, 5, 9], [1, 1, 0, 1, 0]),
+                                                 ("f32", 1e-5, None, [2, 0, 1, 2, 0])])
+def test_batched_matches_oracle(lib, prec, tol, ctas, rounds):
     names = ["tiny", "micro", "mixed", "tiny", "medium"]
     frames = 3
     inst = []
@@ -38,7 +41,7 @@ def test_batched_matches_oracle(lib, prec, tol, ctas):
         f = lib.Fewha(geom, w, prec)
         inst.append((o, o.new_state(4), f, f.new_state(4), torch.zeros(f.n, dtype=f.dtype, device="cuda"),
                      s.to(f.slope_dtype).cuda(), s.numpy()))
-    batch = lib.FewhaBatch([x[2] for x in inst], ctas)
+    batch = lib.FewhaBatch([x[2] for x in inst], ctas, rounds)
     if ctas is not None:
         assert batch.ctas() == ctas
     for t in range(frames):
