@@ -466,17 +466,18 @@ def run_algorithm3(f, frames, sdt, args, aug, flush):
 
 
 def run_compare(geom, w, frames, args, stats_buf, flush):
-    """Plain PCG and the FP64 forms on the same frames and residual target."""
+    """Plain PCG, the FP64 forms and the mixed-precision (BF16 storage) form on
+    the same frames and residual target."""
     import numpy as np
     import torch
     from paper_2011_06842_gb300 import Fewha
     K = min(args.steps, 60)
     res = {}
-    for prec, aug in (("f32", False), ("f64", False), ("f64", True), ("f32", True)):
+    for prec, aug in (("f32", False), ("f64", False), ("f64", True), ("f32", True), ("bf16s", True)):
         if prec == args.precision and aug == (not args.plain):
             continue
         f = Fewha(geom, w, prec, tile=args.tile, grid=args.grid)
-        sdt = torch.float64 if prec == "f64" else torch.float32
+        sdt = {"f64": torch.float64, "f32": torch.float32, "bf16s": torch.bfloat16}[prec]
         times, stats = time_solves(f, frames, sdt, args, args.warmup, K, aug, flush, stats_buf, args.rtol)
         f.close()
         it = [s["iterations"] for s in stats]

@@ -602,13 +602,18 @@ struct Impl : ImplBase {
         if ((st = up(fw, &G.fw)) || (st = up(wm, &G.wmask)) || (st = up(ad, &G.alpha_d)) ||
             (st = up(one, &G.invJ)))
             return st;
-        // P^T work items: bands of rows with band_rows * n_l <= kThreads outputs
+        // P^T work items: bands of rows with band_rows * n_l <= kThreads outputs;
+        // 8 rows, and 4 rows on layers smaller than the largest (their coarser
+        // grid touches about twice as many pupil rows per layer row, so a
+        // half-height band balances the staged work)
         std::vector<int> bl, br0, brs;
+        int n_largest = 0;
+        for (int l = 0; l < P.L; l++) n_largest = std::max(n_largest, P.geom.layers[l].n);
         for (int l = 0; l < P.L; l++) {
             int n = P.geom.layers[l].n, lg = 0;
             while ((1 << lg) < n) lg++;
             G.lay_lg[l] = lg;
-            int BR = std::max(1, std::min(n, std::min(kThreads / n, 8)));  // 8 rows: balanced work items
+            int BR = std::max(1, std::min(n, std::min(kThreads / n, n < n_largest ? 4 : 8)));
             for (int a0 = 0; a0 < n; a0 += BR) {
                 bl.push_back(l);
                 br0.push_back(a0);
