@@ -74,6 +74,7 @@ struct Geo {
     long n;
     int lay_n[FEWHA_MAX_LAYERS], lay_J[FEWHA_MAX_LAYERS];
     long lay_off[FEWHA_MAX_LAYERS + 1];
+    long ll_off[FEWHA_MAX_LAYERS + 1];  // (n_l/2)^2 blocks: level-1 approximation scratch
     T inv_delta[FEWHA_MAX_LAYERS];
     int n_taps;
     T h[kMaxT], g[kMaxT];
@@ -107,6 +108,7 @@ struct __align__(16) Args {
     S *psi;          // [G][m*m] Gamma^T C Gamma P_g (...) per guide star
     T *u;            // [n]  P^T psi (layer nodal adjoint)
     T *wq;           // [n]  W^{-T} u / delta (operator output before + alpha D p)
+    T *ll;           // [sum (n_l/2)^2] level-1 approximation of each layer (split transforms)
     const T *x;      // apply: input
     T *y;            // apply / rhs: output
     const S *slopes; // rhs / solve: measured slopes

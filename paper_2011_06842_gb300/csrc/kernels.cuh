@@ -259,18 +259,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_init(const __grid_constant__ Ar
 }
 
 template <typename T, typename S>
-__global__ void __launch_bounds__(kThreads, 1) k_U(const __grid_constant__ Args<T, S> Ap, int k)
+__global__ void __launch_bounds__(kThreads, 1) k_UA1(const __grid_constant__ Args<T, S> Ap, int k)
 {
     FEWHA_PHASE_GUARD
-    phase_U<T, S>(A, b, k, sc, sred);
+    phase_UA1<T, S>(A, b, k, dyn_smem<T>(), sc, sred);
 }
 
 template <typename T, typename S>
-__global__ void __launch_bounds__(kThreads, 1) k_A(const __grid_constant__ Args<T, S> Ap, int k)
+__global__ void __launch_bounds__(kThreads, 1) k_A2(const __grid_constant__ Args<T, S> Ap, int k)
 {
     FEWHA_PHASE_GUARD
     (void)sc;
-    phase_A<T, S>(A, b, k, dyn_smem<T>());
+    phase_A2<T, S>(A, b, k, dyn_smem<T>());
 }
 
 template <typename T, typename S>
@@ -291,19 +291,19 @@ __global__ void __launch_bounds__(kThreads, 1) k_C(const __grid_constant__ Args<
 }
 
 template <typename T, typename S>
-__global__ void __launch_bounds__(kThreads, 1) k_D(const __grid_constant__ Args<T, S> Ap, int k)
+__global__ void __launch_bounds__(kThreads, 1) k_D1(const __grid_constant__ Args<T, S> Ap, int k)
 {
     FEWHA_PHASE_GUARD
     (void)sc;
-    phase_D<T, S>(A, dyn_smem<T>());
+    phase_D1<T, S>(A, dyn_smem<T>());
 }
 
 template <typename T, typename S>
-__global__ void __launch_bounds__(kThreads, 1) k_E(const __grid_constant__ Args<T, S> Ap, int k)
+__global__ void __launch_bounds__(kThreads, 1) k_D2E(const __grid_constant__ Args<T, S> Ap, int k)
 {
     FEWHA_PHASE_GUARD
     (void)sc;
-    phase_E<T, S>(A, b, k, sred);
+    phase_D2E<T, S>(A, b, k, dyn_smem<T>(), sred);
 }
 
 template <typename T, typename S>
@@ -352,13 +352,13 @@ __device__ void solve_body(const Args<T, S> &A, Scal &sc, double *sred)
             if (!sync(5)) break;
         }
         for (int k = 0; k < A.max_iter; k++) {
-            if (!phase_U<T, S>(A, b, k, sc, sred, true)) {
+            if (!phase_UA1<T, S>(A, b, k, sm, sc, sred, true)) {
                 K = k;
                 break;
             }
             if (!sync(10)) break;
-            phase_A<T, S>(A, b, k, sm);
-            if (!sync(11)) break;
+            phase_A2<T, S>(A, b, k, sm);
+            if (!sync(16)) break;
             {
                 typename AccT<T>::type acc[1] = {wfs_phase<T, S, false>(A, sm)};
                 const int slots[1] = {kSlotB + (k & 1)};
@@ -370,9 +370,9 @@ __device__ void solve_body(const Args<T, S> &A, Scal &sc, double *sred)
                 break;
             }
             if (!sync(13)) break;
-            phase_D<T, S>(A, sm);
+            phase_D1<T, S>(A, sm);
             if (!sync(14)) break;
-            phase_E<T, S>(A, b, k, sred, &sc.alpha);
+            phase_D2E<T, S>(A, b, k, sm, sred, &sc.alpha);
             if (!sync(15)) break;
         }
     } while (0);
@@ -576,6 +576,11 @@ struct Impl : ImplBase {
             G.inv_delta[l] = (T)(1.0 / P.geom.layers[l].delta);
         }
         G.lay_off[P.L] = P.lay_off[P.L];
+        G.ll_off[0] = 0;
+        for (int l = 0; l < P.L; l++) {
+            const long h = P.geom.layers[l].n / 2;
+            G.ll_off[l + 1] = G.ll_off[l] + h * h;
+        }
         G.n_taps = (int)P.taps.size();
         for (int t = 0; t < kMaxT; t++) {
             G.h[t] = t < G.n_taps ? (T)P.taps[t] : T(0);
@@ -670,7 +675,7 @@ struct Impl : ImplBase {
             return st;
         if ((st = alloc((size_t)P.n, &base.nodal)) || (st = alloc((size_t)P.n, &base.u)) ||
             (st = alloc((size_t)P.n, &base.wq)) ||
-            (st = alloc((size_t)P.G * P.m * P.m, &base.psi)) ||
+            (st = alloc((size_t)P.G * P.m * P.m, &base.psi)) || (st = alloc((size_t)P.n / 4 + 1, &base.ll)) ||
             (st = alloc((size_t)kSlots * kMaxCtas, &base.part)) || (st = alloc((size_t)1, &base.rec)))
             return st;
         // launch geometry: dynamic shared memory = max over phases
@@ -680,6 +685,18 @@ struct Impl : ImplBase {
         G.pingpong = sizeof(T) == 4 ? 1 : 0;  // FP32: second buffer for out-of-place DWT passes
         if (G.pingpong) sm_layer *= 2;
         const size_t sm_wfs = wfs_bytes(G.tile_y, G.tile_x);
+        // tiles of the finest wavelet level (analysis: input window and row-pass
+        // output; synthesis: four subband windows and the column-pass output)
+        size_t sm_fine = 0;
+        {
+            const int Lt = (int)P.taps.size();
+            for (int l = 0; l < P.L; l++) {
+                const size_t t = std::min(kFineTile, P.geom.layers[l].n / 2);
+                const size_t ia = (2 * t + Lt - 2), wa = t + Lt / 2 - 1;
+                sm_fine = std::max(sm_fine, std::max(ia * ia + ia * 2 * t, 4 * wa * wa + 2 * t * 2 * wa) * sizeof(T));
+            }
+        }
+        sm_layer = std::max(sm_layer, sm_fine);
         smem = std::max(sm_layer, sm_wfs);
         // band_gather stages rows_chunk psi rows and their x-contraction
         // (all guide stars of a band at once when they fit, else in groups)
@@ -719,12 +736,12 @@ struct Impl : ImplBase {
         CK(setattr((const void *)k_rhs_gather<T, S>));
         CK(setattr((const void *)k_ptr<T, S>));
         CK(setattr((const void *)k_init<T, S>));
-        CK(setattr((const void *)k_U<T, S>));
-        CK(setattr((const void *)k_A<T, S>));
+        CK(setattr((const void *)k_UA1<T, S>));
+        CK(setattr((const void *)k_A2<T, S>));
         CK(setattr((const void *)k_B<T, S>));
         CK(setattr((const void *)k_C<T, S>));
-        CK(setattr((const void *)k_D<T, S>));
-        CK(setattr((const void *)k_E<T, S>));
+        CK(setattr((const void *)k_D1<T, S>));
+        CK(setattr((const void *)k_D2E<T, S>));
         CK(setattr((const void *)k_finish<T, S>));
         CK(setattr((const void *)k_solve_persistent<T, S>));
         CK(cudaFuncSetAttribute((const void *)k_solve_batched<T, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1005,12 +1022,12 @@ struct Impl : ImplBase {
         k_ptr<T, S><<<ncta, kThreads, smem, s>>>(A);
         k_init<T, S><<<ncta, kThreads, smem, s>>>(A);
         for (int k = 0; k < A.max_iter; k++) {
-            k_U<T, S><<<ncta, kThreads, smem, s>>>(A, k);
-            k_A<T, S><<<ncta, kThreads, smem, s>>>(A, k);
+            k_UA1<T, S><<<ncta, kThreads, smem, s>>>(A, k);
+            k_A2<T, S><<<ncta, kThreads, smem, s>>>(A, k);
             k_B<T, S><<<ncta, kThreads, smem, s>>>(A, k);
             k_C<T, S><<<ncta, kThreads, smem, s>>>(A, k);
-            k_D<T, S><<<ncta, kThreads, smem, s>>>(A, k);
-            k_E<T, S><<<ncta, kThreads, smem, s>>>(A, k);
+            k_D1<T, S><<<ncta, kThreads, smem, s>>>(A, k);
+            k_D2E<T, S><<<ncta, kThreads, smem, s>>>(A, k);
         }
         k_finish<T, S><<<1, kThreads, smem, s>>>(A);
         return launch_check();

@@ -249,19 +249,62 @@ __device__ __noinline__ void phase_init(const Args<T, S> &A, const Basis &b, Sca
 }
 
 // ---------------------------------------------------------------------------
-// U_k: iteration scalars, then the direction update, element-parallel over all
-// CTAs (each CTA its own element range):
+// Element loops of the fused phases.  Every layer's top-left (n/2)^2 block (the
+// approximation part of the finest wavelet level) belongs to the layer's CTA,
+// which transforms it in shared memory; every other coefficient to the CTA
+// whose element range holds it.
+// ---------------------------------------------------------------------------
+template <typename T, typename F>
+__device__ __forceinline__ void for_detail_vectors(const Geo<T> &G, long lo, long hi, F body)
+{
+    constexpr int W = VW<T>::W;
+    int l = 0;
+    for (long e = lo + (long)threadIdx.x * W; e < hi; e += (long)blockDim.x * W) {
+        while (e >= G.lay_off[l + 1]) l++;
+        const long loc = e - G.lay_off[l];
+        const int h = G.lay_n[l] >> 1;
+        if ((int)(loc >> G.lay_lg[l]) < h && (int)(loc & (G.lay_n[l] - 1)) < h) continue;
+        body(e);
+    }
+}
+
+// CTAs that own a layer and take no detail coefficients: the first L when
+// there are at least twice as many CTAs as layers (the layers' transforms are
+// then the critical path), else none (every CTA takes its share).
+template <typename T, typename S>
+__device__ __forceinline__ int layer_ctas(const Args<T, S> &A)
+{
+    return A.ncta >= 2 * A.geo.L ? A.geo.L : 0;
+}
+
+// body(global element, index in the (n/2)^2 block), one W-vector per call
+template <typename T, typename F>
+__device__ __forceinline__ void for_block_vectors(const Geo<T> &G, int l, F body)
+{
+    constexpr int W = VW<T>::W;
+    const int n = G.lay_n[l], h = n >> 1, lgh = G.lay_lg[l] - 1, nv = h * h / W;
+    for (int v = threadIdx.x; v < nv; v += blockDim.x) {
+        const int be = v * W;
+        body(G.lay_off[l] + (long)(be >> lgh) * n + (be & (h - 1)), be);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// UA1_k: iteration scalars, the direction update (element-parallel), and the
+// coarser synthesis levels of W^{-1} p_k on each layer's (n/2)^2 block (the
+// layer's CTA updates that block straight into shared memory):
 //   k = 0: p_0 = z_0 - P G^{-1} Q^T z_0 (Algorithm 2) or z_0 (Algorithm 1)
 //   k > 0: p_k = (z_k - mu p_m) + beta p_{k-1},  mu = (z_k, q_m)/(p_m, q_m),
 //          rz_k = (r_k, z_k) - mu (r_k, p_m),  beta = rz_k / rz_{k-1}
 //          (all-directions variant: z_k - P G^{-1} Q^T z_k)
 // Returns false (uniformly) when the stopping test holds before iteration k.
 // CTA 0 records rz_k (k > 0) and ||b||^2 (k = 0).  Partial sums of
-// (alpha D p_k, p_k) and (r_k, p_k) go to the A slots.
+// (alpha D p_k, p_k) and (r_k, p_k) go to the A slots; the blocks' level-1
+// approximations go to A.ll for A2_k.
 // ---------------------------------------------------------------------------
 template <typename T, typename S>
-__device__ __noinline__ bool phase_U(const Args<T, S> &A, const Basis &b, int k, Scal &sc, double *sred,
-                                     bool scalars_in_sc = false)
+__device__ __noinline__ bool phase_UA1(const Args<T, S> &A, const Basis &b, int k, T *buf, Scal &sc,
+                                       double *sred, bool scalars_in_sc = false)
 {
     const int kv = b.kv;
     double *red = sc.red;
@@ -334,15 +377,12 @@ __device__ __noinline__ bool phase_U(const Args<T, S> &A, const Basis &b, int k,
     typedef typename AccT<T>::type Acc;
     constexpr int W = VW<T>::W;
     Acc acc[2] = {0, 0};
-    long lo, hi;
-    cta_range_vec(A.geo.n, W, A.vrank(), A.ncta, lo, hi);
-    for (long e = lo + (long)threadIdx.x * W; e < hi; e += (long)blockDim.x * W) {
-        T p[W];
+    auto update = [&](long e, T (&p)[W]) {
         T rv[W], jv[W], ad[W], pp[W];
         vld_cg(A.r + e, rv);
         vld_nc(A.geo.invJ + e, jv);
         vld_nc(A.geo.alpha_d + e, ad);
-        if (k > 0) vld(pprev + e, pp);
+        if (k > 0) vld_cg(pprev + e, pp);
 #pragma unroll
         for (int i = 0; i < W; i++) p[i] = jv[i] * rv[i];
         if (kv > 0) {
@@ -368,22 +408,41 @@ __device__ __noinline__ bool phase_U(const Args<T, S> &A, const Basis &b, int k,
             acc[1] += (Acc)rv[i] * (Acc)p[i];
         }
         vst(pk + e, p);  // p_k into its basis slot
+    };
+    const Geo<T> &G = A.geo;
+    for (int l = A.vrank(); l < G.L; l += A.ncta) {
+        const int h = G.lay_n[l] >> 1, lgh = G.lay_lg[l] - 1;
+        for_block_vectors(G, l, [&](long e, int be) {
+            T p[W];
+            update(e, p);
+            const int s0 = spad(be, lgh);
+#pragma unroll
+            for (int i = 0; i < W; i++) buf[s0 + i] = p[i];
+        });
+        __syncthreads();
+        idwt2<T>(buf, G.pingpong ? buf + h * (h + 1) : buf, lgh, G.lay_J[l] - 1, G);
+        T *ll = A.ll + G.ll_off[l];
+        for (int v = threadIdx.x; v < h * h / W; v += blockDim.x) {
+            const int be = v * W, s0 = spad(be, lgh);
+            T x[W];
+#pragma unroll
+            for (int i = 0; i < W; i++) x[i] = buf[s0 + i];
+            vst(ll + be, x);
+        }
+        __syncthreads();
+    }
+    const int nl = layer_ctas(A);
+    if (A.vrank() >= nl) {
+        long lo, hi;
+        cta_range_vec(G.n, W, A.vrank() - nl, A.ncta - nl, lo, hi);
+        for_detail_vectors(G, lo, hi, [&](long e) {
+            T p[W];
+            update(e, p);
+        });
     }
     const int slots[2] = {kSlotA + (k & 1) * 2, kSlotA + (k & 1) * 2 + 1};
     block_partials<2>(acc, A.part, slots, sred, A.vrank());
     return true;
-}
-
-// ---------------------------------------------------------------------------
-// A_k: nodal layers = W^{-1} p_k, one CTA per layer (p_k from U_k, written by
-// other CTAs: L2 loads).
-// ---------------------------------------------------------------------------
-template <typename T, typename S>
-__device__ __noinline__ void phase_A(const Args<T, S> &A, const Basis &b, int k, T *sm)
-{
-    constexpr int W = VW<T>::W;
-    const T *pk = newP(A, b, k);
-    layer_idwt<T, S>(A, sm, [&](long e, T (&p)[W]) { vld_cg(pk + e, p); });
 }
 
 // ---------------------------------------------------------------------------
@@ -434,19 +493,189 @@ __device__ __noinline__ bool phase_C(const Args<T, S> &A, const Basis &b, int k,
     return true;
 }
 
-// D_k: wq = W^{-T} u / delta (E_k adds alpha D p_k to form q_k).
-template <typename T, typename S>
-__device__ __noinline__ void phase_D(const Args<T, S> &A, T *sm)
+// ---------------------------------------------------------------------------
+// Split layer transforms.  The finest level of the periodic 2-D DWT is a local
+// stencil: a level-1 coefficient pair depends on an L x L window of the layer
+// (analysis), and a pair of nodal values on Lh x Lh windows of the four level-1
+// subbands (synthesis).  That level runs in tiles of kFineTile x kFineTile
+// coefficient pairs on all CTAs; only the coarser levels, on the (n/2)^2
+// approximation block, stay on one CTA per layer.  Same sums in the same order
+// as the single-CTA transform (rows then columns for analysis, columns then
+// rows for synthesis).
+// ---------------------------------------------------------------------------
+constexpr int kFineTile = 16;
+
+// Work item w -> layer l and tile origin (in coefficient pairs); false past the end.
+template <typename T>
+__device__ __forceinline__ bool fine_tile(const Geo<T> &G, int w, int &l, int &p0y, int &p0x)
 {
-    constexpr int W = VW<T>::W;
-    layer_fdwt<T, S>(A, sm, [&](long e, const T (&v)[W]) { vst(A.wq + e, v); });
+    for (l = 0; l < G.L; l++) {
+        const int h = G.lay_n[l] >> 1, nt = (h + kFineTile - 1) / kFineTile;
+        if (w < nt * nt) {
+            p0y = (w / nt) * kFineTile;
+            p0x = (w % nt) * kFineTile;
+            return true;
+        }
+        w -= nt * nt;
+    }
+    return false;
 }
 
-// E_k: q_k = wq + alpha D p_k (stored in the basis slot), c += alpha p,
-// r -= alpha q, and the inner products of the next step.
+// D1: level-1 analysis of u; the three detail bands are final coefficients of
+// W^{-T} u / delta (into wq), the approximation block goes to A.ll.
+template <typename T, typename S, int L>
+__device__ void fine_analysis(const Args<T, S> &A, T *sm)
+{
+    const Geo<T> &G = A.geo;
+    const Taps<T, L> tp = load_taps<T, L>(G);
+    int l, p0y, p0x;
+    for (int w = A.vrank(); fine_tile(G, w, l, p0y, p0x); w += A.ncta) {
+        const int n = G.lay_n[l], h = n >> 1;
+        const int ty = min(kFineTile, h - p0y), tx = min(kFineTile, h - p0x);
+        const int IR = 2 * ty + L - 2, IC = 2 * tx + L - 2, MC = 2 * tx;
+        T *in = sm, *mid = sm + IR * IC;
+        const T *u = A.u + G.lay_off[l];
+        for (int e = threadIdx.x; e < IR * IC; e += blockDim.x) {
+            const int r = e / IC, c = e - r * IC;
+            in[e] = ldcg(u + (long)((2 * p0y + r) & (n - 1)) * n + ((2 * p0x + c) & (n - 1)));
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < IR * tx; e += blockDim.x) {  // rows
+            const int r = e / tx, k = e - r * tx;
+            const T *x = in + r * IC + 2 * k;
+            T a = 0, d = 0;
+#pragma unroll
+            for (int t = 0; t < L; t++) {
+                a += tp.h[t] * x[t];
+                d += tp.g[t] * x[t];
+            }
+            mid[r * MC + k] = a;
+            mid[r * MC + tx + k] = d;
+        }
+        __syncthreads();
+        const T sc = G.inv_delta[l];
+        T *wq = A.wq + G.lay_off[l];
+        T *ll = A.ll + G.ll_off[l];
+        for (int e = threadIdx.x; e < ty * MC; e += blockDim.x) {  // columns
+            const int k = e / MC, c = e - k * MC;
+            const T *x = mid + 2 * k * MC + c;
+            T a = 0, d = 0;
+#pragma unroll
+            for (int t = 0; t < L; t++) {
+                a += tp.h[t] * x[t * MC];
+                d += tp.g[t] * x[t * MC];
+            }
+            const int row = p0y + k;
+            if (c < tx) {  // low x: LL (unscaled, coarser levels follow) and HL
+                ll[(long)row * h + p0x + c] = a;
+                wq[(long)(h + row) * n + p0x + c] = d * sc;
+            } else {       // high x: LH and HH
+                const int q = h + p0x + (c - tx);
+                wq[(long)row * n + q] = a * sc;
+                wq[(long)(h + row) * n + q] = d * sc;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// A2: level-1 synthesis of p_k's layers from the approximation block in A.ll
+// (A1) and p_k's three detail bands; nodal = W^{-1} p_k.
+template <typename T, typename S, int L>
+__device__ void fine_synthesis(const Args<T, S> &A, const T *pk, T *sm)
+{
+    constexpr int Lh = L / 2;
+    const Geo<T> &G = A.geo;
+    const Taps<T, L> tp = load_taps<T, L>(G);
+    int l, p0y, p0x;
+    for (int w = A.vrank(); fine_tile(G, w, l, p0y, p0x); w += A.ncta) {
+        const int n = G.lay_n[l], h = n >> 1;
+        const int ty = min(kFineTile, h - p0y), tx = min(kFineTile, h - p0x);
+        const int WR = ty + Lh - 1, WC = tx + Lh - 1, Q = WR * WC;
+        T *win = sm;              // [4][WR][WC]: LL, LH, HL, HH windows
+        T *mid = sm + 4 * Q;      // [2 ty][2 WC]: columns synthesised, low-x then high-x
+        const T *ll = A.ll + G.ll_off[l];
+        const T *pl = pk + G.lay_off[l];
+        for (int e = threadIdx.x; e < 4 * Q; e += blockDim.x) {
+            const int qd = e / Q, r = (e - qd * Q) / WC, c = e - qd * Q - r * WC;
+            const int m = (p0y - Lh + 1 + r) & (h - 1), j = (p0x - Lh + 1 + c) & (h - 1);
+            T v;
+            if (qd == 0)
+                v = ldcg(ll + (long)m * h + j);
+            else if (qd == 1)
+                v = ldcg(pl + (long)m * n + h + j);
+            else if (qd == 2)
+                v = ldcg(pl + (long)(h + m) * n + j);
+            else
+                v = ldcg(pl + (long)(h + m) * n + h + j);
+            win[e] = v;
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < 2 * ty * 2 * WC; e += blockDim.x) {  // columns
+            const int yy = e / (2 * WC), cc = e - yy * (2 * WC);
+            const int i = yy >> 1, ey = yy & 1, half = cc >= WC ? 1 : 0, c = cc - half * WC;
+            const T *lo = win + (half ? 1 : 0) * Q + c;  // low y: LL or LH
+            const T *hi = win + (half ? 3 : 2) * Q + c;  // high y: HL or HH
+            T x = 0;
+#pragma unroll
+            for (int u = 0; u < Lh; u++) {
+                const int r = i + Lh - 1 - u;
+                x += tp.h[ey + 2 * u] * lo[r * WC] + tp.g[ey + 2 * u] * hi[r * WC];
+            }
+            mid[e] = x;
+        }
+        __syncthreads();
+        const T sc = G.inv_delta[l];
+        S *nodal = A.nodal + G.lay_off[l];
+        for (int e = threadIdx.x; e < 2 * ty * 2 * tx; e += blockDim.x) {  // rows
+            const int yy = e / (2 * tx), xx = e - yy * (2 * tx), j = xx >> 1, ex = xx & 1;
+            const T *row = mid + yy * 2 * WC;
+            T x = 0;
+#pragma unroll
+            for (int u = 0; u < Lh; u++) {
+                const int c = j + Lh - 1 - u;
+                x += tp.h[ex + 2 * u] * row[c] + tp.g[ex + 2 * u] * row[WC + c];
+            }
+            nodal[(long)(2 * p0y + yy) * n + 2 * p0x + xx] = Cv<S>::st(x * sc);
+        }
+        __syncthreads();
+    }
+}
+
+// A2_k: the finest synthesis level, tiled over all CTAs: nodal = W^{-1} p_k.
+template <typename T, typename S>
+__device__ __noinline__ void phase_A2(const Args<T, S> &A, const Basis &b, int k, T *sm)
+{
+    const T *pk = newP(A, b, k);
+    switch (A.geo.n_taps) {
+    case 2: fine_synthesis<T, S, 2>(A, pk, sm); break;
+    case 4: fine_synthesis<T, S, 4>(A, pk, sm); break;
+    case 6: fine_synthesis<T, S, 6>(A, pk, sm); break;
+    default: fine_synthesis<T, S, 8>(A, pk, sm); break;
+    }
+}
+
+// D1_k: the finest analysis level of u, tiled over all CTAs.
+template <typename T, typename S>
+__device__ __noinline__ void phase_D1(const Args<T, S> &A, T *sm)
+{
+    switch (A.geo.n_taps) {
+    case 2: fine_analysis<T, S, 2>(A, sm); break;
+    case 4: fine_analysis<T, S, 4>(A, sm); break;
+    case 6: fine_analysis<T, S, 6>(A, sm); break;
+    default: fine_analysis<T, S, 8>(A, sm); break;
+    }
+}
+
+
+// D2E_k: the coarser analysis levels of each layer's approximation block (the
+// layer's CTA; W^{-T} u / delta is then complete), and the update
+// q_k = wq + alpha D p_k (stored in the basis slot), c += alpha p,
+// r -= alpha q with the inner products of the next step (element-parallel;
+// each layer's block by its CTA right after its transform).
 template <typename T, typename S, bool ALL>
-__device__ __noinline__ void phase_E_impl(const Args<T, S> &A, const Basis &b, int k, double *sred,
-                                         const double *alpha_sc)
+__device__ __noinline__ void phase_D2E_impl(const Args<T, S> &A, const Basis &b, int k, T *buf, double *sred,
+                                           const double *alpha_sc)
 {
     const T alpha = (T)(alpha_sc ? *alpha_sc : ldcgd(A.rec->alpha + k));
     const T *pk = newP(A, b, k);
@@ -455,20 +684,18 @@ __device__ __noinline__ void phase_E_impl(const Args<T, S> &A, const Basis &b, i
     const T *pm = kv > 0 ? oldP(A, b, kv - 1) : nullptr;
     const T *qm = kv > 0 ? oldQ(A, b, kv - 1) : nullptr;
     constexpr int W = VW<T>::W;
-    long lo, hi;
-    cta_range_vec(A.geo.n, W, A.vrank(), A.ncta, lo, hi);
     typedef typename AccT<T>::type Acc;
     const bool last = kv > 0 && !ALL;
     const bool all = kv > 0 && ALL;
     constexpr int NA = ALL ? 4 + 2 * kK : 4;
     Acc acc[NA];
     for (int i = 0; i < NA; i++) acc[i] = 0;
-    for (long e = lo + (long)threadIdx.x * W; e < hi; e += (long)blockDim.x * W) {
+    auto update = [&](long e) {
         T p[W], wq[W], ad[W], c[W], r[W], jv[W], q[W], z[W];
         vld_cg(pk + e, p);
         vld_cg(A.wq + e, wq);
         vld_nc(A.geo.alpha_d + e, ad);
-        vld(A.c + e, c);
+        vld_cg(A.c + e, c);
         vld_cg(A.r + e, r);
         vld_nc(A.geo.invJ + e, jv);
         T pmv[W], qmv[W];
@@ -506,6 +733,40 @@ __device__ __noinline__ void phase_E_impl(const Args<T, S> &A, const Basis &b, i
                 }
             }
         }
+    };
+    // the layer's CTA: coarser analysis levels of the approximation block (from
+    // D1_k) -> wq, then the update on that block
+    const Geo<T> &G = A.geo;
+    for (int l = A.vrank(); l < G.L; l += A.ncta) {
+        const int n = G.lay_n[l], h = n >> 1, lgh = G.lay_lg[l] - 1, nv = h * h / W;
+        const T *ll = A.ll + G.ll_off[l];
+#pragma unroll 4
+        for (int v = threadIdx.x; v < nv; v += blockDim.x) {
+            T x[W];
+            vld_cg(ll + (long)v * W, x);
+            const int s0 = spad(v * W, lgh);
+#pragma unroll
+            for (int i = 0; i < W; i++) buf[s0 + i] = x[i];
+        }
+        __syncthreads();
+        fdwt2<T>(buf, G.pingpong ? buf + h * (h + 1) : buf, lgh, G.lay_J[l] - 1, G);
+        const T sc = G.inv_delta[l];
+        for_block_vectors(G, l, [&](long e, int be) {
+            T x[W];
+            const int s0 = spad(be, lgh);
+#pragma unroll
+            for (int i = 0; i < W; i++) x[i] = buf[s0 + i] * sc;
+            vst(A.wq + e, x);
+        });
+        __syncthreads();
+        for_block_vectors(G, l, [&](long e, int) { update(e); });
+        __syncthreads();
+    }
+    const int nl = layer_ctas(A);
+    if (A.vrank() >= nl) {
+        long lo, hi;
+        cta_range_vec(G.n, W, A.vrank() - nl, A.ncta - nl, lo, hi);
+        for_detail_vectors(G, lo, hi, update);
     }
     const int e0 = kSlotE + (k & 1) * kSlotEStride;
     int slots[NA];
@@ -514,12 +775,13 @@ __device__ __noinline__ void phase_E_impl(const Args<T, S> &A, const Basis &b, i
 }
 
 template <typename T, typename S>
-__device__ void phase_E(const Args<T, S> &A, const Basis &b, int k, double *sred, const double *alpha_sc = nullptr)
+__device__ void phase_D2E(const Args<T, S> &A, const Basis &b, int k, T *buf, double *sred,
+                          const double *alpha_sc = nullptr)
 {
     if (A.recycle_all)
-        phase_E_impl<T, S, true>(A, b, k, sred, alpha_sc);
+        phase_D2E_impl<T, S, true>(A, b, k, buf, sred, alpha_sc);
     else
-        phase_E_impl<T, S, false>(A, b, k, sred, alpha_sc);
+        phase_D2E_impl<T, S, false>(A, b, k, buf, sred, alpha_sc);
 }
 
 // Stats and the recycled-basis metadata for the next time step (CTA 0).

@@ -370,7 +370,8 @@ class Fewha:
         self._check(self.lib.fewha_set_timeout(self._h, int(ns)), "fewha_set_timeout")
 
     TRACE_TAGS = {1: "R1 wfs(rhs)", 2: "R2 gather(rhs)", 3: "R3 fdwt(rhs)", 4: "gram", 5: "init",
-                  10: "U update", 11: "A idwt", 12: "B wfs", 13: "C gather", 14: "D fdwt", 15: "E axpy"}
+                  10: "UA1 update+idwt", 16: "A2 idwt fine", 12: "B wfs", 13: "C gather",
+                  14: "D1 fdwt fine", 15: "D2E fdwt+axpy"}
 
     def set_trace(self, buf):
         """Enables the phase trace into a CUDA uint64/int64 tensor of shape (cap, 4), or None."""
