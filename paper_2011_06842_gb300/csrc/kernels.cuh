@@ -336,6 +336,7 @@ __device__ void solve_body(const Args<T, S> &A, Scal &sc, double *sred)
         return ok;
     };
     int K = A.max_iter;
+    const bool split = split_levels(A);  // uniform over the instance's CTAs
     do {
         wfs_phase<T, S, true>(A, sm);
         if (b.kv > 0) phase_gram<T, S>(A, b, sm, (int)(A.smem_bytes / sizeof(T)));
@@ -357,8 +358,10 @@ __device__ void solve_body(const Args<T, S> &A, Scal &sc, double *sred)
                 break;
             }
             if (!sync(10)) break;
-            phase_A2<T, S>(A, b, k, sm);
-            if (!sync(16)) break;
+            if (split) {
+                phase_A2<T, S>(A, b, k, sm);
+                if (!sync(16)) break;
+            }
             {
                 typename AccT<T>::type acc[1] = {wfs_phase<T, S, false>(A, sm)};
                 const int slots[1] = {kSlotB + (k & 1)};
@@ -370,8 +373,10 @@ __device__ void solve_body(const Args<T, S> &A, Scal &sc, double *sred)
                 break;
             }
             if (!sync(13)) break;
-            phase_D1<T, S>(A, sm);
-            if (!sync(14)) break;
+            if (split) {
+                phase_D1<T, S>(A, sm);
+                if (!sync(14)) break;
+            }
             phase_D2E<T, S>(A, b, k, sm, sred, &sc.alpha);
             if (!sync(15)) break;
         }

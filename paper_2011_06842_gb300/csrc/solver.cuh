@@ -268,13 +268,19 @@ __device__ __forceinline__ void for_detail_vectors(const Geo<T> &G, long lo, lon
     }
 }
 
-// CTAs that own a layer and take no detail coefficients: the first L when
-// there are at least twice as many CTAs as layers (the layers' transforms are
-// then the critical path), else none (every CTA takes its share).
+// Two ways to run the layers' transforms, chosen per instance:
+//   split (at least twice as many CTAs as layers): the finest level is tiled
+//     over all CTAs (A2, D1); the first L CTAs own one layer's (n/2)^2 block
+//     each, run its coarser levels in shared memory and take no detail
+//     coefficients (the block transforms are then the critical path);
+//   whole (fewer CTAs, e.g. the small instances of a batch): each layer's CTA
+//     updates the whole layer, runs every level in shared memory and updates
+//     the layer again after the forward transform; A2 and D1 are empty, so an
+//     iteration has four grid barriers instead of six.
 template <typename T, typename S>
-__device__ __forceinline__ int layer_ctas(const Args<T, S> &A)
+__device__ __forceinline__ bool split_levels(const Args<T, S> &A)
 {
-    return A.ncta >= 2 * A.geo.L ? A.geo.L : 0;
+    return A.ncta >= 2 * A.geo.L;
 }
 
 // body(global element, index in the (n/2)^2 block), one W-vector per call
@@ -410,31 +416,54 @@ __device__ __noinline__ bool phase_UA1(const Args<T, S> &A, const Basis &b, int 
         vst(pk + e, p);  // p_k into its basis slot
     };
     const Geo<T> &G = A.geo;
+    const bool split = split_levels(A);
     for (int l = A.vrank(); l < G.L; l += A.ncta) {
-        const int h = G.lay_n[l] >> 1, lgh = G.lay_lg[l] - 1;
-        for_block_vectors(G, l, [&](long e, int be) {
-            T p[W];
-            update(e, p);
-            const int s0 = spad(be, lgh);
+        if (split) {
+            const int h = G.lay_n[l] >> 1, lgh = G.lay_lg[l] - 1;
+            for_block_vectors(G, l, [&](long e, int be) {
+                T p[W];
+                update(e, p);
+                const int s0 = spad(be, lgh);
 #pragma unroll
-            for (int i = 0; i < W; i++) buf[s0 + i] = p[i];
-        });
-        __syncthreads();
-        idwt2<T>(buf, G.pingpong ? buf + h * (h + 1) : buf, lgh, G.lay_J[l] - 1, G);
-        T *ll = A.ll + G.ll_off[l];
-        for (int v = threadIdx.x; v < h * h / W; v += blockDim.x) {
-            const int be = v * W, s0 = spad(be, lgh);
-            T x[W];
+                for (int i = 0; i < W; i++) buf[s0 + i] = p[i];
+            });
+            __syncthreads();
+            idwt2<T>(buf, G.pingpong ? buf + h * (h + 1) : buf, lgh, G.lay_J[l] - 1, G);
+            T *ll = A.ll + G.ll_off[l];
+            for (int v = threadIdx.x; v < h * h / W; v += blockDim.x) {
+                const int be = v * W, s0 = spad(be, lgh);
+                T x[W];
 #pragma unroll
-            for (int i = 0; i < W; i++) x[i] = buf[s0 + i];
-            vst(ll + be, x);
+                for (int i = 0; i < W; i++) x[i] = buf[s0 + i];
+                vst(ll + be, x);
+            }
+        } else {
+            // whole layer: p_k into shared memory, all levels, nodal = W^{-1} p_k
+            const int n = G.lay_n[l], lgn = G.lay_lg[l], nv = n * n / W;
+            const long off = G.lay_off[l];
+            for (int v = threadIdx.x; v < nv; v += blockDim.x) {
+                T p[W];
+                update(off + (long)v * W, p);
+                const int s0 = spad(v * W, lgn);
+#pragma unroll
+                for (int i = 0; i < W; i++) buf[s0 + i] = p[i];
+            }
+            __syncthreads();
+            idwt2<T>(buf, G.pingpong ? buf + n * (n + 1) : buf, lgn, G.lay_J[l], G);
+            const T sc = G.inv_delta[l];
+            for (int v = threadIdx.x; v < nv; v += blockDim.x) {
+                T x[W];
+                const int s0 = spad(v * W, lgn);
+#pragma unroll
+                for (int i = 0; i < W; i++) x[i] = buf[s0 + i] * sc;
+                vst(A.nodal + off + (long)v * W, x);
+            }
         }
         __syncthreads();
     }
-    const int nl = layer_ctas(A);
-    if (A.vrank() >= nl) {
+    if (split && A.vrank() >= G.L) {
         long lo, hi;
-        cta_range_vec(G.n, W, A.vrank() - nl, A.ncta - nl, lo, hi);
+        cta_range_vec(G.n, W, A.vrank() - G.L, A.ncta - G.L, lo, hi);
         for_detail_vectors(G, lo, hi, [&](long e) {
             T p[W];
             update(e, p);
@@ -646,6 +675,7 @@ __device__ void fine_synthesis(const Args<T, S> &A, const T *pk, T *sm)
 template <typename T, typename S>
 __device__ __noinline__ void phase_A2(const Args<T, S> &A, const Basis &b, int k, T *sm)
 {
+    if (!split_levels(A)) return;
     const T *pk = newP(A, b, k);
     switch (A.geo.n_taps) {
     case 2: fine_synthesis<T, S, 2>(A, pk, sm); break;
@@ -659,6 +689,7 @@ __device__ __noinline__ void phase_A2(const Args<T, S> &A, const Basis &b, int k
 template <typename T, typename S>
 __device__ __noinline__ void phase_D1(const Args<T, S> &A, T *sm)
 {
+    if (!split_levels(A)) return;
     switch (A.geo.n_taps) {
     case 2: fine_analysis<T, S, 2>(A, sm); break;
     case 4: fine_analysis<T, S, 4>(A, sm); break;
@@ -690,10 +721,9 @@ __device__ __noinline__ void phase_D2E_impl(const Args<T, S> &A, const Basis &b,
     constexpr int NA = ALL ? 4 + 2 * kK : 4;
     Acc acc[NA];
     for (int i = 0; i < NA; i++) acc[i] = 0;
-    auto update = [&](long e) {
-        T p[W], wq[W], ad[W], c[W], r[W], jv[W], q[W], z[W];
+    auto update_w = [&](long e, const T (&wq)[W]) {
+        T p[W], ad[W], c[W], r[W], jv[W], q[W], z[W];
         vld_cg(pk + e, p);
-        vld_cg(A.wq + e, wq);
         vld_nc(A.geo.alpha_d + e, ad);
         vld_cg(A.c + e, c);
         vld_cg(A.r + e, r);
@@ -734,10 +764,42 @@ __device__ __noinline__ void phase_D2E_impl(const Args<T, S> &A, const Basis &b,
             }
         }
     };
-    // the layer's CTA: coarser analysis levels of the approximation block (from
-    // D1_k) -> wq, then the update on that block
+    auto update = [&](long e) {
+        T wq[W];
+        vld_cg(A.wq + e, wq);
+        update_w(e, wq);
+    };
     const Geo<T> &G = A.geo;
-    for (int l = A.vrank(); l < G.L; l += A.ncta) {
+    if (!split_levels(A)) {
+        // whole layer: W^{-T} u / delta in shared memory, then the update of the
+        // layer with wq read from there
+        for (int l = A.vrank(); l < G.L; l += A.ncta) {
+            const int n = G.lay_n[l], lgn = G.lay_lg[l], nv = n * n / W;
+            const long off = G.lay_off[l];
+#pragma unroll 2
+            for (int v = threadIdx.x; v < nv; v += blockDim.x) {
+                T x[W];
+                vld_cg(A.u + off + (long)v * W, x);
+                const int s0 = spad(v * W, lgn);
+#pragma unroll
+                for (int i = 0; i < W; i++) buf[s0 + i] = x[i];
+            }
+            __syncthreads();
+            fdwt2<T>(buf, G.pingpong ? buf + n * (n + 1) : buf, lgn, G.lay_J[l], G);
+            const T sc = G.inv_delta[l];
+            for (int v = threadIdx.x; v < nv; v += blockDim.x) {
+                T wq[W];
+                const int s0 = spad(v * W, lgn);
+#pragma unroll
+                for (int i = 0; i < W; i++) wq[i] = buf[s0 + i] * sc;
+                update_w(off + (long)v * W, wq);
+            }
+            __syncthreads();
+        }
+    }
+    // split: the layer's CTA runs the coarser analysis levels of the
+    // approximation block (from D1_k) -> wq, then the update on that block
+    for (int l = split_levels(A) ? A.vrank() : G.L; l < G.L; l += A.ncta) {
         const int n = G.lay_n[l], h = n >> 1, lgh = G.lay_lg[l] - 1, nv = h * h / W;
         const T *ll = A.ll + G.ll_off[l];
 #pragma unroll 4
@@ -762,10 +824,9 @@ __device__ __noinline__ void phase_D2E_impl(const Args<T, S> &A, const Basis &b,
         for_block_vectors(G, l, [&](long e, int) { update(e); });
         __syncthreads();
     }
-    const int nl = layer_ctas(A);
-    if (A.vrank() >= nl) {
+    if (split_levels(A) && A.vrank() >= G.L) {
         long lo, hi;
-        cta_range_vec(G.n, W, A.vrank() - nl, A.ncta - nl, lo, hi);
+        cta_range_vec(G.n, W, A.vrank() - G.L, A.ncta - G.L, lo, hi);
         for_detail_vectors(G, lo, hi, update);
     }
     const int e0 = kSlotE + (k & 1) * kSlotEStride;

@@ -29,8 +29,15 @@ def lib():
 @pytest.mark.parametrize("prec,tol,ctas,rounds", [("f64", 1e-10, None, None), ("f32", 1e-5, None, None),
                                                  ("f64", 1e-10, [1, 3, 2, 5, 4], None),
                                                  ("f64", 1e-10, [1, 3, 2, 5, 9], [1, 1, 0, 1, 0]),
-                                                 ("f32", 1e-5, None, [2, 0, 1, 2, 0])])
+                                                 ("f32", 1e-5, None, [2, 0, 1, 2, 0]),
+                                                 ("f64", 1e-10, [4, 3, 6, 1, 10], None),
+                                                 ("f32", 1e-5, [4, 3, 6, 1, 10], None)])
 def test_batched_matches_oracle(lib, prec, tol, ctas, rounds):
+    """Each instance of a batch equals the oracle.  An instance with at least
+    twice as many CTAs as layers splits the finest wavelet level off and tiles
+    it over its CTAs; one with fewer runs whole-layer transforms: the
+    [4, 3, 6, 1, 10] split covers both kinds in one launch (tiny and mixed
+    and medium split, micro and the second tiny whole)."""
     names = ["tiny", "micro", "mixed", "tiny", "medium"]
     frames = 3
     inst = []
