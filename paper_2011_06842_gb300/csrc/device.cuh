@@ -433,11 +433,19 @@ __device__ __forceinline__ unsigned int ld_acquire_gpu(const unsigned int *p)
 // (after the block barrier, publishing the CTA's writes) and waits with
 // acquire loads until the counter reaches the next multiple of nctas.  Returns false (and the CTA must
 // return) when any CTA has recorded an error or the wait ran past timeout_ns.
+// When this CTA passed its previous barrier (phase trace); trace_begin()
+// stamps the start of the solve.
+static __shared__ unsigned long long t_pass;
+
+__device__ __forceinline__ void trace_begin(bool tracing)
+{
+    if (threadIdx.x == 0) t_pass = tracing ? gtimer() : 0ull;
+}
+
 __device__ inline bool grid_sync(Record *rec, unsigned long long timeout_ns, int nctas, int rank,
                                  unsigned long long *trace_slot = nullptr)
 {
     __shared__ int ok;
-    __shared__ unsigned long long t_pass;  // when this CTA passed its previous barrier
     __syncthreads();
     if (threadIdx.x == 0) {
         ok = 1;

@@ -337,6 +337,7 @@ __device__ void solve_body(const Args<T, S> &A, Scal &sc, double *sred)
     };
     int K = A.max_iter;
     const bool split = split_levels(A);  // uniform over the instance's CTAs
+    trace_begin(A.trace != nullptr);
     do {
         wfs_phase<T, S, true>(A, sm);
         if (b.kv > 0) phase_gram<T, S>(A, b, sm, (int)(A.smem_bytes / sizeof(T)));

@@ -59,6 +59,19 @@ __device__ __forceinline__ T *newQ(const Args<T, S> &A, const Basis &b, int k)
     return A.Q + ((size_t)b.nb * A.kcap + (k % A.kcap)) * A.geo.n;
 }
 
+// Addresses of the old basis directions p_j, q_j (j < kv) in shared memory, so
+// that loops over j can have all their loads in flight at once (one DRAM round
+// trip instead of kv: the basis is cold after the previous frame).
+template <typename T, typename S>
+__device__ __forceinline__ void basis_table(const Args<T, S> &A, const Basis &b, const T **sp, const T **sq)
+{
+    if (threadIdx.x < b.kv) {
+        sp[threadIdx.x] = oldP(A, b, threadIdx.x);
+        sq[threadIdx.x] = oldQ(A, b, threadIdx.x);
+    }
+    __syncthreads();
+}
+
 // Shared scalars of a phase (every CTA derives them from the same partials).
 struct Scal {
     double red[2 * kK + 16];       // reduced partials
@@ -94,16 +107,32 @@ __device__ __noinline__ void phase_gram(const Args<T, S> &A, const Basis &b, T *
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int kv = b.kv, nslot = kv * kv, nvec = 2 * kv;
     const int CH = (sm_elems / nvec) / W * W;  // elements of the slice staged at once
+    __shared__ const T *sp[kK], *sq[kK];
+    basis_table(A, b, sp, sq);
     Acc acc[(kK * kK + 31) / 32];
     for (int i = 0; i < (kK * kK + 31) / 32; i++) acc[i] = 0;
     for (long c0 = lo; c0 < hi; c0 += CH) {
         const int len = (int)min((long)CH, hi - c0);
-        for (int v = threadIdx.x; v < nvec * (len / W); v += blockDim.x) {
-            const int vec = v / (len / W), o = (v - vec * (len / W)) * W;
-            const T *src = vec < kv ? oldP(A, b, vec) : oldQ(A, b, vec - kv);
-            T x[W];
-            vld_nc(src + c0 + o, x);
-            vst(sm + vec * CH + o, x);
+        const int nv = len / W, total = nvec * nv;
+        constexpr int U = 4;  // vectors in flight per thread
+        for (int v0 = threadIdx.x; v0 < total; v0 += U * blockDim.x) {
+            T x[U][W];
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                const int v = v0 + u * blockDim.x;
+                if (v < total) {
+                    const int vec = v / nv, o = (v - vec * nv) * W;
+                    vld_nc((vec < kv ? sp[vec] : sq[vec - kv]) + c0 + o, x[u]);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                const int v = v0 + u * blockDim.x;
+                if (v < total) {
+                    const int vec = v / nv, o = (v - vec * nv) * W;
+                    vst(sm + vec * CH + o, x[u]);
+                }
+            }
         }
         __syncthreads();
         for (int s2 = warp, t = 0; s2 < nslot; s2 += nw, t++) {
@@ -168,25 +197,28 @@ __device__ __noinline__ void phase_rhs_fdwt(const Args<T, S> &A, T *sm, double *
     block_partials<2>(acc, A.part, slots, sred, A.vrank());
 }
 
-// INIT1: P^T r0 (Algorithm 2 initial projection), per CTA slice.
+// INIT1: P^T r0 (Algorithm 2 initial projection), per CTA slice, one element
+// per thread.
 template <typename T, typename S>
 __device__ __noinline__ void phase_ptr(const Args<T, S> &A, const Basis &b, double *sred)
 {
     typedef typename AccT<T>::type Acc;
     constexpr int W = VW<T>::W;
+    __shared__ const T *sp[kK], *sq[kK];
+    basis_table(A, b, sp, sq);
     long lo, hi;
     cta_range_vec(A.geo.n, W, A.vrank(), A.ncta, lo, hi);
+    const int kv = b.kv;
     Acc acc[kK];
-    for (int j = 0; j < kK; j++) acc[j] = 0;
-    for (long e = lo + (long)threadIdx.x * W; e < hi; e += (long)blockDim.x * W) {
-        T rv[W];
-        vld_cg(A.r + e, rv);
-        for (int j = 0; j < b.kv; j++) {
-            T pj[W];
-            vld_nc(oldP(A, b, j) + e, pj);
 #pragma unroll
-            for (int i = 0; i < W; i++) acc[j] += (Acc)pj[i] * (Acc)rv[i];
-        }
+    for (int j = 0; j < kK; j++) acc[j] = 0;
+    for (long e = lo + threadIdx.x; e < hi; e += blockDim.x) {
+        const T rv = ldcg(A.r + e);
+        T pj[kK];
+#pragma unroll
+        for (int j = 0; j < kK; j++) pj[j] = j < kv ? __ldg(sp[j] + e) : T(0);
+#pragma unroll
+        for (int j = 0; j < kK; j++) acc[j] += (Acc)pj[j] * (Acc)rv;
     }
     int slots[kK];
     for (int j = 0; j < kK; j++) slots[j] = kSlotGram + kK * kK + j;
@@ -205,41 +237,45 @@ __device__ __noinline__ void phase_init(const Args<T, S> &A, const Basis &b, Sca
     __syncthreads();
     typedef typename AccT<T>::type Acc;
     constexpr int W = VW<T>::W;
+    __shared__ const T *sp[kK], *sq[kK];
+    basis_table(A, b, sp, sq);
     long lo, hi;
     cta_range_vec(A.geo.n, W, A.vrank(), A.ncta, lo, hi);
     Acc acc[kK + 2];
-    for (int j = 0; j < kK + 2; j++) acc[j] = 0;
-    for (long e = lo + (long)threadIdx.x * W; e < hi; e += (long)blockDim.x * W) {
-        T cv[W], rv[W], jv[W];
-        vld(A.c + e, cv);
-        vld_cg(A.r + e, rv);
-        vld_nc(A.geo.invJ + e, jv);
-        for (int j = 0; j < kv; j++) {
-            const T sj = (T)sc.tau[j];
-            T pj[W], qj[W];
-            vld_nc(oldP(A, b, j) + e, pj);
-            vld_nc(oldQ(A, b, j) + e, qj);
 #pragma unroll
-            for (int i = 0; i < W; i++) {
-                cv[i] += sj * pj[i];
-                rv[i] -= sj * qj[i];
+    for (int j = 0; j < kK + 2; j++) acc[j] = 0;
+    constexpr int CJ = 8;  // directions loaded at once
+    for (long e = lo + threadIdx.x; e < hi; e += blockDim.x) {
+        T cv = A.c[e], rv = ldcg(A.r + e);
+        const T jv = __ldg(A.geo.invJ + e);
+        for (int j0 = 0; j0 < kv; j0 += CJ) {
+            T pj[CJ], qj[CJ];
+#pragma unroll
+            for (int t = 0; t < CJ; t++) {
+                const bool in = j0 + t < kv;
+                pj[t] = in ? __ldg(sp[j0 + t] + e) : T(0);
+                qj[t] = in ? __ldg(sq[j0 + t] + e) : T(0);
+            }
+#pragma unroll
+            for (int t = 0; t < CJ; t++) {
+                if (j0 + t < kv) {
+                    const T sj = (T)sc.tau[j0 + t];
+                    cv += sj * pj[t];
+                    rv -= sj * qj[t];
+                }
             }
         }
-        vst(A.c + e, cv);
-        vst(A.r + e, rv);
-        T z[W];
+        A.c[e] = cv;
+        A.r[e] = rv;
+        const T z = jv * rv;
+        acc[kK] += (Acc)rv * (Acc)z;
+        acc[kK + 1] += (Acc)rv * (Acc)rv;
+        // q_j again (now from L1)
+        T qj[kK];
 #pragma unroll
-        for (int i = 0; i < W; i++) {
-            z[i] = jv[i] * rv[i];
-            acc[kK] += (Acc)rv[i] * (Acc)z[i];
-            acc[kK + 1] += (Acc)rv[i] * (Acc)rv[i];
-        }
-        for (int j = 0; j < kv; j++) {
-            T qj[W];
-            vld_nc(oldQ(A, b, j) + e, qj);
+        for (int j = 0; j < kK; j++) qj[j] = j < kv ? __ldg(sq[j] + e) : T(0);
 #pragma unroll
-            for (int i = 0; i < W; i++) acc[j] += (Acc)qj[i] * (Acc)z[i];
-        }
+        for (int j = 0; j < kK; j++) acc[j] += (Acc)qj[j] * (Acc)z;
     }
     int slots[kK + 2];
     for (int j = 0; j < kK; j++) slots[j] = kSlotInit + j;
@@ -380,6 +416,8 @@ __device__ __noinline__ bool phase_UA1(const Args<T, S> &A, const Basis &b, int 
     const T *pprev = k > 0 ? newP(A, b, k - 1) : nullptr;
     const T *pm = kv > 0 ? oldP(A, b, kv - 1) : nullptr;
     const bool proj_all = (k == 0) || A.recycle_all;
+    __shared__ const T *sp[kK], *sq[kK];
+    if (proj_all && kv > 0) basis_table(A, b, sp, sq);
     typedef typename AccT<T>::type Acc;
     constexpr int W = VW<T>::W;
     Acc acc[2] = {0, 0};
@@ -396,7 +434,7 @@ __device__ __noinline__ bool phase_UA1(const Args<T, S> &A, const Basis &b, int 
                 for (int j = 0; j < kv; j++) {
                     T pj[W];
                     const T tj = (T)sc.tau[j];
-                    vld_nc(oldP(A, b, j) + e, pj);
+                    vld_nc(sp[j] + e, pj);
 #pragma unroll
                     for (int i = 0; i < W; i++) p[i] -= tj * pj[i];
                 }

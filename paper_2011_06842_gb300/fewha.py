@@ -369,7 +369,7 @@ class Fewha:
         """Time limit of the solver's device-side waits (ns)."""
         self._check(self.lib.fewha_set_timeout(self._h, int(ns)), "fewha_set_timeout")
 
-    TRACE_TAGS = {1: "R1 wfs(rhs)", 2: "R2 gather(rhs)", 3: "R3 fdwt(rhs)", 4: "gram", 5: "init",
+    TRACE_TAGS = {1: "R1 wfs(rhs)", 2: "R2 gather(rhs)", 3: "R3 fdwt(rhs)", 4: "P^T r0", 5: "init",
                   10: "UA1 update+idwt", 16: "A2 idwt fine", 12: "B wfs", 13: "C gather",
                   14: "D1 fdwt fine", 15: "D2E fdwt+axpy"}
 
