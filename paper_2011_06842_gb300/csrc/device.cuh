@@ -712,7 +712,7 @@ __device__ void layer_idwt(const Args<T, S> &A, T *buf, Load load)
 //   both    : psi_g = Gamma^T (weighted slopes) on the tile's nodes.
 // ---------------------------------------------------------------------------
 template <typename T, typename S, bool RHS>
-__device__ __noinline__ typename AccT<T>::type wfs_phase(const Args<T, S> &A, T *sm)
+__device__ __forceinline__ typename AccT<T>::type wfs_phase(const Args<T, S> &A, T *sm)
 {
     typedef typename AccT<T>::type Acc;
     const Geo<T> &G = A.geo;
@@ -817,7 +817,7 @@ __device__ __noinline__ typename AccT<T>::type wfs_phase(const Args<T, S> &A, T 
 // Thread (a - a0, b) owns output u[a][b]; no atomics, fixed summation order.
 // ---------------------------------------------------------------------------
 template <typename T, typename S>
-__device__ __noinline__ void band_gather(const Args<T, S> &A, T *sm)
+__device__ __forceinline__ void band_gather(const Args<T, S> &A, T *sm)
 {
     const Geo<T> &G = A.geo;
     const int m = G.m, RC = G.rows_chunk, NB = G.nbands;

@@ -98,7 +98,7 @@ __device__ void load_factor(const Args<T, S> &A, int kv, Scal &sc)
 // latency round), then one warp per entry sums it.
 // ---------------------------------------------------------------------------
 template <typename T, typename S>
-__device__ __noinline__ void phase_gram(const Args<T, S> &A, const Basis &b, T *sm, int sm_elems)
+__device__ __forceinline__ void phase_gram(const Args<T, S> &A, const Basis &b, T *sm, int sm_elems)
 {
     typedef typename AccT<T>::type Acc;
     constexpr int W = VW<T>::W;
@@ -153,7 +153,7 @@ __device__ __noinline__ void phase_gram(const Args<T, S> &A, const Basis &b, T *
 // R2 side task of the last CTA: Cholesky factor of G (symmetrised) and
 // 1/(p_m, q_m), into the record.
 template <typename T, typename S>
-__device__ __noinline__ void phase_factor(const Args<T, S> &A, const Basis &b, Scal &sc)
+__device__ __forceinline__ void phase_factor(const Args<T, S> &A, const Basis &b, Scal &sc)
 {
     const int kv = b.kv;
     reduce_ranges(A.part, A.ncta, {kSlotGram, kv * kv, sc.gram});
@@ -175,7 +175,7 @@ __device__ __noinline__ void phase_factor(const Args<T, S> &A, const Basis &b, S
 // r0 = (b - b_prev) + r_prev;  b_prev <- b.
 // ---------------------------------------------------------------------------
 template <typename T, typename S>
-__device__ __noinline__ void phase_rhs_fdwt(const Args<T, S> &A, T *sm, double *sred)
+__device__ __forceinline__ void phase_rhs_fdwt(const Args<T, S> &A, T *sm, double *sred)
 {
     typedef typename AccT<T>::type Acc;
     constexpr int W = VW<T>::W;
@@ -200,7 +200,7 @@ __device__ __noinline__ void phase_rhs_fdwt(const Args<T, S> &A, T *sm, double *
 // INIT1: P^T r0 (Algorithm 2 initial projection), per CTA slice, one element
 // per thread.
 template <typename T, typename S>
-__device__ __noinline__ void phase_ptr(const Args<T, S> &A, const Basis &b, double *sred)
+__device__ __forceinline__ void phase_ptr(const Args<T, S> &A, const Basis &b, double *sred)
 {
     typedef typename AccT<T>::type Acc;
     constexpr int W = VW<T>::W;
@@ -228,7 +228,7 @@ __device__ __noinline__ void phase_ptr(const Args<T, S> &A, const Basis &b, doub
 // INIT2: c += P sigma, r -= Q sigma with sigma = G^{-1} P^T r0; then the
 // partial sums (q_j, z), (r, z), (r, r) with z = J^{-1} r.
 template <typename T, typename S>
-__device__ __noinline__ void phase_init(const Args<T, S> &A, const Basis &b, Scal &sc, double *sred)
+__device__ __forceinline__ void phase_init(const Args<T, S> &A, const Basis &b, Scal &sc, double *sred)
 {
     const int kv = b.kv;
     reduce_ranges(A.part, A.ncta, {kSlotGram + kK * kK, kv, sc.red});
@@ -345,7 +345,7 @@ __device__ __forceinline__ void for_block_vectors(const Geo<T> &G, int l, F body
 // approximations go to A.ll for A2_k.
 // ---------------------------------------------------------------------------
 template <typename T, typename S>
-__device__ __noinline__ bool phase_UA1(const Args<T, S> &A, const Basis &b, int k, T *buf, Scal &sc,
+__device__ __forceinline__ bool phase_UA1(const Args<T, S> &A, const Basis &b, int k, T *buf, Scal &sc,
                                        double *sred, bool scalars_in_sc = false)
 {
     const int kv = b.kv;
@@ -520,7 +520,7 @@ __device__ __noinline__ bool phase_UA1(const Args<T, S> &A, const Basis &b, int 
 // (converged) or breakdown; CTA 0 records alpha_k, 1/rz_k and (p_k, q_k).
 // ---------------------------------------------------------------------------
 template <typename T, typename S>
-__device__ __noinline__ bool phase_C(const Args<T, S> &A, const Basis &b, int k, T *sm, Scal &sc,
+__device__ __forceinline__ bool phase_C(const Args<T, S> &A, const Basis &b, int k, T *sm, Scal &sc,
                                      bool rz_in_sc = false)
 {
     double *red = sc.red;  // [0] ws, [1] pd, [2] rz0 (k = 0)
@@ -711,7 +711,7 @@ __device__ void fine_synthesis(const Args<T, S> &A, const T *pk, T *sm)
 
 // A2_k: the finest synthesis level, tiled over all CTAs: nodal = W^{-1} p_k.
 template <typename T, typename S>
-__device__ __noinline__ void phase_A2(const Args<T, S> &A, const Basis &b, int k, T *sm)
+__device__ __forceinline__ void phase_A2(const Args<T, S> &A, const Basis &b, int k, T *sm)
 {
     if (!split_levels(A)) return;
     const T *pk = newP(A, b, k);
@@ -725,7 +725,7 @@ __device__ __noinline__ void phase_A2(const Args<T, S> &A, const Basis &b, int k
 
 // D1_k: the finest analysis level of u, tiled over all CTAs.
 template <typename T, typename S>
-__device__ __noinline__ void phase_D1(const Args<T, S> &A, T *sm)
+__device__ __forceinline__ void phase_D1(const Args<T, S> &A, T *sm)
 {
     if (!split_levels(A)) return;
     switch (A.geo.n_taps) {
@@ -743,7 +743,7 @@ __device__ __noinline__ void phase_D1(const Args<T, S> &A, T *sm)
 // r -= alpha q with the inner products of the next step (element-parallel;
 // each layer's block by its CTA right after its transform).
 template <typename T, typename S, bool ALL>
-__device__ __noinline__ void phase_D2E_impl(const Args<T, S> &A, const Basis &b, int k, T *buf, double *sred,
+__device__ __forceinline__ void phase_D2E_impl(const Args<T, S> &A, const Basis &b, int k, T *buf, double *sred,
                                            const double *alpha_sc)
 {
     const T alpha = (T)(alpha_sc ? *alpha_sc : ldcgd(A.rec->alpha + k));
@@ -885,7 +885,7 @@ __device__ void phase_D2E(const Args<T, S> &A, const Basis &b, int k, T *buf, do
 
 // Stats and the recycled-basis metadata for the next time step (CTA 0).
 template <typename T, typename S>
-__device__ __noinline__ void phase_finish(const Args<T, S> &A, const Basis &b, int K, Scal &sc)
+__device__ __forceinline__ void phase_finish(const Args<T, S> &A, const Basis &b, int K, Scal &sc)
 {
     double *red = sc.red;  // [0] bb, [1] rr (R3), [2] rz, [3] rr (last E or INIT2)
     if (K > 0)
