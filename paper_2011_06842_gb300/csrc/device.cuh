@@ -89,6 +89,10 @@ struct Geo {
     int nbands;                 // P^T work items (layer, band of rows)
     const int *band_layer, *band_row0, *band_rows;  // [nbands]
     const int *band_ilo, *band_ihi;  // [G][nbands] pupil rows the band touches
+    // guide stars of a band in groups whose pupil rows fit rows_chunk staged
+    // rows: [G][nbands] end of the guide star's group, and psi elements staged
+    // before it within the group
+    const int *band_gend, *band_gc;
     int rows_chunk;             // pupil rows staged per pass of band_gather
     int stage_tab;              // band_gather also stages its P^T weight tables in shared memory
     int pingpong;               // layer phases have a second n x n shared buffer
@@ -821,8 +825,8 @@ __device__ __forceinline__ void band_gather(const Args<T, S> &A, T *sm)
 {
     const Geo<T> &G = A.geo;
     const int m = G.m, RC = G.rows_chunk, NB = G.nbands;
-    __shared__ int s_cum[FEWHA_MAX_GS + 1], s_base[FEWHA_MAX_GS + 1], s_ng;
-    __shared__ int s_ilo[FEWHA_MAX_GS], s_ihi[FEWHA_MAX_GS];
+    __shared__ int s_cum[FEWHA_MAX_GS + 1], s_base[FEWHA_MAX_GS + 1];
+    __shared__ int s_ilo[FEWHA_MAX_GS], s_ihi[FEWHA_MAX_GS], s_gend[FEWHA_MAX_GS], s_gc[FEWHA_MAX_GS];
     __shared__ long s_off[FEWHA_MAX_GS];  // psi element = s_off[q] + staged index
     for (int w = A.vrank(); w < NB; w += A.ncta) {
         const int l = __ldg(G.band_layer + w), a0 = __ldg(G.band_row0 + w), BR = __ldg(G.band_rows + w);
@@ -831,39 +835,32 @@ __device__ __forceinline__ void band_gather(const Args<T, S> &A, T *sm)
         T acc = 0;
         T *ps = sm;           // [RC][m] staged psi rows
         T *Tb = sm + RC * m;  // [RC][n] their x-contraction
-        // pupil rows [ilo, ihi) of every guide star for this band, one load each
-        // in parallel (the grouping below reads them from shared memory)
+        // pupil rows [ilo, ihi) of every guide star for this band and its
+        // group (precomputed on the host), one load each in parallel
         if (threadIdx.x < G.G) {
-            s_ilo[threadIdx.x] = __ldg(G.band_ilo + threadIdx.x * NB + w);
-            s_ihi[threadIdx.x] = __ldg(G.band_ihi + threadIdx.x * NB + w);
+            const int i = threadIdx.x * NB + w;
+            s_ilo[threadIdx.x] = __ldg(G.band_ilo + i);
+            s_ihi[threadIdx.x] = __ldg(G.band_ihi + i);
+            s_gend[threadIdx.x] = __ldg(G.band_gend + i);
+            s_gc[threadIdx.x] = __ldg(G.band_gc + i);
         }
         __syncthreads();
         // guide stars in groups whose pupil rows fit the RC staged rows
         for (int g0 = 0, g1; g0 < G.G; g0 = g1) {
-            int rows_tot = 0;
-            for (g1 = g0; g1 < G.G; g1++) {
-                const int r = s_ihi[g1] - s_ilo[g1];
-                if (rows_tot + r > RC) break;
-                rows_tot += r;
-            }
-            if (g1 == g0) g1 = g0 + 1;  // unreachable: the host sizes RC >= the rows of any one guide star
+            g1 = s_gend[g0];
+            const int ng = g1 - g0;
             // stage psi rows of the group's guide stars, flattened so that each
-            // thread has all of its loads in flight at once (one latency round)
-            if (threadIdx.x == 0) {
-                int c = 0;
-                for (int g = g0; g < g1; g++) {
-                    const int ilo = s_ilo[g], rows = s_ihi[g] - ilo;
-                    s_off[g - g0] = (long)g * m * m + (long)ilo * m - c;
-                    s_base[g - g0] = c / m;
-                    c += rows * m;
-                    s_cum[g - g0 + 1] = c;
-                }
-                s_cum[0] = 0;
-                s_base[g1 - g0] = c / m;
-                s_ng = g1 - g0;
+            // thread has all of its loads in flight at once (one latency round);
+            // the staging offsets of the group are filled in parallel
+            if (threadIdx.x <= ng) {
+                const int q = threadIdx.x, g = g0 + q;
+                const int c = q < ng ? s_gc[g] : s_gc[g1 - 1] + (s_ihi[g1 - 1] - s_ilo[g1 - 1]) * m;
+                s_cum[q] = c;
+                s_base[q] = c / m;
+                if (q < ng) s_off[q] = (long)g * m * m + (long)s_ilo[g] * m - c;
             }
             __syncthreads();
-            const int ng = s_ng, nxt = ng << lgn, nyt = ng * BR;
+            const int nxt = ng << lgn, nyt = ng * BR;
             // weight tables of the group (x: per guide star and layer column,
             // y: per guide star and band row), loaded in the same latency round
             T *xw = Tb + RC * n;                          // [kAdjW][ng * n] (tap-major: no bank conflicts)

@@ -354,7 +354,9 @@ __device__ void solve_body(const Args<T, S> &A, Scal &sc, double *sred)
             if (!sync(5)) break;
         }
         for (int k = 0; k < A.max_iter; k++) {
-            if (!phase_UA1<T, S>(A, b, k, sm, sc, sred, true)) {
+            // UA1's partial sums join the WFS phase's block reduction
+            typename AccT<T>::type ua[2];
+            if (!phase_UA1<T, S>(A, b, k, sm, sc, sred, true, ua)) {
                 K = k;
                 break;
             }
@@ -364,9 +366,9 @@ __device__ void solve_body(const Args<T, S> &A, Scal &sc, double *sred)
                 if (!sync(16)) break;
             }
             {
-                typename AccT<T>::type acc[1] = {wfs_phase<T, S, false>(A, sm)};
-                const int slots[1] = {kSlotB + (k & 1)};
-                block_partials<1>(acc, A.part, slots, sred, rank);
+                typename AccT<T>::type acc[3] = {wfs_phase<T, S, false>(A, sm), ua[0], ua[1]};
+                const int slots[3] = {kSlotB + (k & 1), kSlotA + (k & 1) * 2, kSlotA + (k & 1) * 2 + 1};
+                block_partials<3>(acc, A.part, slots, sred, rank);
             }
             if (!sync(12)) break;
             if (!phase_C<T, S>(A, b, k, sm, sc, true)) {
@@ -712,6 +714,28 @@ struct Impl : ImplBase {
         if (want > smem) smem = std::min(want, smem_cap);
         G.rows_chunk = (int)std::min<size_t>(max_rows_sum, smem / row_bytes);
         if (smem > smem_cap || G.rows_chunk < max_rows) return FEWHA_ERR_GEOMETRY;
+        {
+            // guide stars of each band in groups of consecutive guide stars whose
+            // pupil rows fit rows_chunk staged rows
+            std::vector<int> gend((size_t)P.G * G.nbands), gc((size_t)P.G * G.nbands);
+            for (int w = 0; w < G.nbands; w++)
+                for (int g0 = 0, g1; g0 < P.G; g0 = g1) {
+                    int rows_tot = 0;
+                    for (g1 = g0; g1 < P.G; g1++) {
+                        const size_t i = (size_t)g1 * G.nbands + w;
+                        if (rows_tot + bihi[i] - bilo[i] > G.rows_chunk) break;
+                        rows_tot += bihi[i] - bilo[i];
+                    }
+                    if (g1 == g0) return FEWHA_ERR_GEOMETRY;  // rows_chunk >= max_rows
+                    for (int g = g0, c = 0; g < g1; g++) {
+                        const size_t i = (size_t)g * G.nbands + w;
+                        gend[i] = g1;
+                        gc[i] = c;
+                        c += (bihi[i] - bilo[i]) * P.m;
+                    }
+                }
+            if ((st = up(gend, &G.band_gend)) || (st = up(gc, &G.band_gc))) return st;
+        }
         sm_fixed = std::max(sm_layer, std::min(want, smem_cap));
         // P^T weight tables of one band (all guide stars) staged beside the
         // psi rows when one thread per entry and the shared memory suffice

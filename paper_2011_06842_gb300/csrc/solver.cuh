@@ -346,8 +346,11 @@ __device__ __forceinline__ void for_block_vectors(const Geo<T> &G, int l, F body
 // ---------------------------------------------------------------------------
 template <typename T, typename S>
 __device__ __forceinline__ bool phase_UA1(const Args<T, S> &A, const Basis &b, int k, T *buf, Scal &sc,
-                                       double *sred, bool scalars_in_sc = false)
+                                       double *sred, bool scalars_in_sc = false,
+                                       typename AccT<T>::type *defer = nullptr)
 {
+    typedef typename AccT<T>::type Acc;
+    constexpr int W = VW<T>::W;
     const int kv = b.kv;
     double *red = sc.red;
     if (k == 0) {
@@ -400,8 +403,7 @@ __device__ __forceinline__ bool phase_UA1(const Args<T, S> &A, const Basis &b, i
             if (A.vrank() == 0) A.rec->rz[k] = rz;
         }
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 0) {  // the thread that set rr and bb
         sc.stop = (A.rtol > 0.0 && sc.rr <= A.rtol * A.rtol * sc.bb) ? 1 : 0;
         if (sc.stop && A.vrank() == 0) {
             A.rec->iters = k;
@@ -412,14 +414,14 @@ __device__ __forceinline__ bool phase_UA1(const Args<T, S> &A, const Basis &b, i
     if (sc.stop) return false;
 
     const T beta = (T)sc.beta, mu = (T)sc.mu;
+    const Geo<T> &G = A.geo;
+    const bool split = split_levels(A);
+    const bool proj_all = (k == 0) || A.recycle_all;
     T *pk = newP(A, b, k);
     const T *pprev = k > 0 ? newP(A, b, k - 1) : nullptr;
     const T *pm = kv > 0 ? oldP(A, b, kv - 1) : nullptr;
-    const bool proj_all = (k == 0) || A.recycle_all;
     __shared__ const T *sp[kK], *sq[kK];
     if (proj_all && kv > 0) basis_table(A, b, sp, sq);
-    typedef typename AccT<T>::type Acc;
-    constexpr int W = VW<T>::W;
     Acc acc[2] = {0, 0};
     auto update = [&](long e, T (&p)[W]) {
         T rv[W], jv[W], ad[W], pp[W];
@@ -453,8 +455,6 @@ __device__ __forceinline__ bool phase_UA1(const Args<T, S> &A, const Basis &b, i
         }
         vst(pk + e, p);  // p_k into its basis slot
     };
-    const Geo<T> &G = A.geo;
-    const bool split = split_levels(A);
     for (int l = A.vrank(); l < G.L; l += A.ncta) {
         if (split) {
             const int h = G.lay_n[l] >> 1, lgh = G.lay_lg[l] - 1;
@@ -507,8 +507,14 @@ __device__ __forceinline__ bool phase_UA1(const Args<T, S> &A, const Basis &b, i
             update(e, p);
         });
     }
-    const int slots[2] = {kSlotA + (k & 1) * 2, kSlotA + (k & 1) * 2 + 1};
-    block_partials<2>(acc, A.part, slots, sred, A.vrank());
+    if (defer) {
+        // the caller adds them to a later phase's block reduction
+        defer[0] = acc[0];
+        defer[1] = acc[1];
+    } else {
+        const int slots[2] = {kSlotA + (k & 1) * 2, kSlotA + (k & 1) * 2 + 1};
+        block_partials<2>(acc, A.part, slots, sred, A.vrank());
+    }
     return true;
 }
 
