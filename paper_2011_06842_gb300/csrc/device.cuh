@@ -33,8 +33,12 @@
 
 namespace fewha {
 
-constexpr int kThreads = 1024;     // threads of every CTA
-constexpr int kPairs = 8;          // DWT output pairs per thread: 128 * 64 / 1024 (in place)
+// 512 threads per CTA leave 128 registers per thread: with 1024 threads (64
+// registers) the fused phases spilled ~300 bytes per thread to local memory.
+constexpr int kThreads = 512;       // threads of every CTA
+constexpr int kBandOutputs = 1024;  // layer nodes of one P^T work item (band of rows)
+constexpr int kOutPT = (kBandOutputs + kThreads - 1) / kThreads;  // of them per thread
+constexpr int kTabPT = 2;           // P^T weight-table entries staged per thread
 constexpr int kMaxCtas = 1024;
 constexpr int kK = FEWHA_MAX_K;
 constexpr int kMaxT = 8;           // taps
@@ -500,7 +504,6 @@ __device__ inline bool grid_sync(Record *rec, unsigned long long timeout_ns, int
 // pairs of one line from a register window (each input loaded once per run).
 // ---------------------------------------------------------------------------
 constexpr int kRun = 4;                          // output pairs per run
-constexpr int kRuns = kPairs / kRun;             // runs per thread (128 x 64 pairs / 1024 threads)
 
 template <typename T, int L>
 struct Taps {
@@ -586,11 +589,13 @@ __device__ __forceinline__ void dwt_store(T *base, int es, int half, int run, in
 // One pass over the top-left N x N block from src to dst (pitch P).  Thread
 // idx takes line idx mod N and run idx / N: consecutive threads work on
 // consecutive rows (ROWS) or columns.  FP32: dst is the ping-pong buffer.
-// FP64 (a 128 x 129 layer fills 132 KB): in place, outputs held in registers
-// across a block barrier (src == dst).
+// FP64 (a 128 x 129 layer fills 132 KB): in place (src == dst), one warp per
+// line at a time.
 template <typename T, int L, bool ROWS, bool SYNTH>
-__device__ void dwt_pass(const T *src, T *dst, int P, int lgN, const Taps<T, L> &tp)
+__device__ void dwt_pass(const T *src, T *dst, int P, int lgN, const Geo<T> &G)
 {
+    // taps read here (shared memory), live only during the pass
+    const Taps<T, L> tp = load_taps<T, L>(G);
     const int N = 1 << lgN, half = N >> 1;
     const int run = half < kRun ? half : kRun;       // pairs per run
     const int total = N * (half / run);              // runs in the pass
@@ -605,23 +610,20 @@ __device__ void dwt_pass(const T *src, T *dst, int P, int lgN, const Taps<T, L> 
         }
         __syncthreads();
     } else {
-        T out[kRuns][2 * kRun];
-#pragma unroll
-        for (int t = 0; t < kRuns; t++) {
-            const int idx = threadIdx.x + t * blockDim.x;
-            if (idx < total) {
-                const int line = idx & (N - 1), m0 = (idx >> lgN) * run;
-                dwt_run<T, L, SYNTH>(src + line * ls, es, N, half, run, m0, tp, out[t]);
-            }
-        }
-        __syncthreads();
-#pragma unroll
-        for (int t = 0; t < kRuns; t++) {
-            const int idx = threadIdx.x + t * blockDim.x;
-            if (idx < total) {
-                const int line = idx & (N - 1), m0 = (idx >> lgN) * run;
-                dwt_store<SYNTH>(dst + line * ls, es, half, run, m0, out[t]);
-            }
+        // in place (FP64): a line's outputs overwrite only that line, so the
+        // lanes of one warp read the whole line into registers, synchronise
+        // and write it back; a warp takes 32 / (runs per line) lines at once
+        // (N <= FEWHA_MAX_GRID = 128: at most 16 runs of 4 pairs per line)
+        const int nr = half / run, lpw = 32 / nr;
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+        const int sub = lane / nr, m0 = (lane - sub * nr) * run;
+        for (int line0 = warp * lpw; line0 < N; line0 += nw * lpw) {
+            const int line = line0 + sub;
+            const bool act = line < N;
+            T out[2 * kRun];
+            if (act) dwt_run<T, L, SYNTH>(src + line * ls, es, N, half, run, m0, tp, out);
+            __syncwarp();
+            if (act) dwt_store<SYNTH>(dst + line * ls, es, half, run, m0, out);
         }
         __syncthreads();
     }
@@ -632,22 +634,20 @@ __device__ void dwt_pass(const T *src, T *dst, int P, int lgN, const Taps<T, L> 
 template <typename T, int L>
 __device__ void idwt2_L(T *buf, T *tmp, int lgn, int J, const Geo<T> &G)
 {
-    const Taps<T, L> tp = load_taps<T, L>(G);
     const int P = (1 << lgn) + 1;
     for (int t = J - 1; t >= 0; t--) {
-        dwt_pass<T, L, false, true>(buf, tmp, P, lgn - t, tp);
-        dwt_pass<T, L, true, true>(tmp, buf, P, lgn - t, tp);
+        dwt_pass<T, L, false, true>(buf, tmp, P, lgn - t, G);
+        dwt_pass<T, L, true, true>(tmp, buf, P, lgn - t, G);
     }
 }
 
 template <typename T, int L>
 __device__ void fdwt2_L(T *buf, T *tmp, int lgn, int J, const Geo<T> &G)
 {
-    const Taps<T, L> tp = load_taps<T, L>(G);
     const int P = (1 << lgn) + 1;
     for (int t = 0; t < J; t++) {
-        dwt_pass<T, L, true, false>(buf, tmp, P, lgn - t, tp);
-        dwt_pass<T, L, false, false>(tmp, buf, P, lgn - t, tp);
+        dwt_pass<T, L, true, false>(buf, tmp, P, lgn - t, G);
+        dwt_pass<T, L, false, false>(tmp, buf, P, lgn - t, G);
     }
 }
 
@@ -831,8 +831,10 @@ __device__ __forceinline__ void band_gather(const Args<T, S> &A, T *sm)
     for (int w = A.vrank(); w < NB; w += A.ncta) {
         const int l = __ldg(G.band_layer + w), a0 = __ldg(G.band_row0 + w), BR = __ldg(G.band_rows + w);
         const int n = G.lay_n[l], lgn = G.lay_lg[l], nout = BR << lgn;
-        const int oa = threadIdx.x >> lgn, ob = threadIdx.x & (n - 1);  // owned output (a0 + oa, ob)
-        T acc = 0;
+        // owned outputs o = threadIdx.x + j blockDim.x: layer node (a0 + (o >> lgn), o & (n - 1))
+        T acc[kOutPT];
+#pragma unroll
+        for (int j = 0; j < kOutPT; j++) acc[j] = 0;
         T *ps = sm;           // [RC][m] staged psi rows
         T *Tb = sm + RC * m;  // [RC][n] their x-contraction
         // pupil rows [ilo, ihi) of every guide star for this band and its
@@ -868,26 +870,31 @@ __device__ __forceinline__ void band_gather(const Args<T, S> &A, T *sm)
             int *xlo = reinterpret_cast<int *>(yw + (size_t)nyt * kAdjW), *xct = xlo + nxt;
             int *ylo = xct + nxt, *yct = ylo + nyt;
             const bool tab = G.stage_tab != 0;
-            int t_lo = 0, t_ct = 0;
-            T t_w[kAdjW];
-            const int tt = threadIdx.x;  // one table entry per thread (nxt + nyt <= blockDim.x)
-            if (tab && tt < nxt + nyt) {
-                int idx;
-                if (tt < nxt) {
-                    const int q = tt >> lgn, bcol = tt & (n - 1);
-                    idx = ((g0 + q) * G.L + l) * 2 * FEWHA_MAX_GRID + bcol;
-                } else {
-                    const int q = (tt - nxt) / BR, r = (tt - nxt) - q * BR;
-                    idx = (((g0 + q) * G.L + l) * 2 + 1) * FEWHA_MAX_GRID + a0 + r;
-                }
-                t_lo = __ldg(G.adj_lo + idx);
-                t_ct = __ldg(G.adj_cnt + idx);
+            // table entries tt = threadIdx.x + j blockDim.x (nxt + nyt <= kTabPT blockDim.x)
+            int t_lo[kTabPT], t_ct[kTabPT];
+            T t_w[kTabPT][kAdjW];
 #pragma unroll
-                for (int c = 0; c < kAdjW; c++) t_w[c] = __ldg(G.adj_w + (size_t)idx * kAdjW + c);
+            for (int j = 0; j < kTabPT; j++) {
+                const int tt = threadIdx.x + j * blockDim.x;
+                t_lo[j] = t_ct[j] = 0;
+                if (tab && tt < nxt + nyt) {
+                    int idx;
+                    if (tt < nxt) {
+                        const int q = tt >> lgn, bcol = tt & (n - 1);
+                        idx = ((g0 + q) * G.L + l) * 2 * FEWHA_MAX_GRID + bcol;
+                    } else {
+                        const int q = (tt - nxt) / BR, r = (tt - nxt) - q * BR;
+                        idx = (((g0 + q) * G.L + l) * 2 + 1) * FEWHA_MAX_GRID + a0 + r;
+                    }
+                    t_lo[j] = __ldg(G.adj_lo + idx);
+                    t_ct[j] = __ldg(G.adj_cnt + idx);
+#pragma unroll
+                    for (int c = 0; c < kAdjW; c++) t_w[j][c] = __ldg(G.adj_w + (size_t)idx * kAdjW + c);
+                }
             }
             {
                 const int total = s_cum[ng];
-                constexpr int U = 4;
+                constexpr int U = 8;
                 int q = 0;  // guide star of the staged index t (t only grows)
                 for (int t0 = threadIdx.x; t0 < total; t0 += U * blockDim.x) {
                     S v[U];
@@ -906,18 +913,22 @@ __device__ __forceinline__ void band_gather(const Args<T, S> &A, T *sm)
                     }
                 }
             }
-            if (tab && tt < nxt + nyt) {
-                if (tt < nxt) {
-                    xlo[tt] = t_lo;
-                    xct[tt] = t_ct;
 #pragma unroll
-                    for (int c = 0; c < kAdjW; c++) xw[(size_t)c * nxt + tt] = t_w[c];
-                } else {
-                    const int e = tt - nxt;
-                    ylo[e] = t_lo;
-                    yct[e] = t_ct;
+            for (int j = 0; j < kTabPT; j++) {
+                const int tt = threadIdx.x + j * blockDim.x;
+                if (tab && tt < nxt + nyt) {
+                    if (tt < nxt) {
+                        xlo[tt] = t_lo[j];
+                        xct[tt] = t_ct[j];
 #pragma unroll
-                    for (int c = 0; c < kAdjW; c++) yw[(size_t)e * kAdjW + c] = t_w[c];
+                        for (int c = 0; c < kAdjW; c++) xw[(size_t)c * nxt + tt] = t_w[j][c];
+                    } else {
+                        const int e = tt - nxt;
+                        ylo[e] = t_lo[j];
+                        yct[e] = t_ct[j];
+#pragma unroll
+                        for (int c = 0; c < kAdjW; c++) yw[(size_t)e * kAdjW + c] = t_w[j][c];
+                    }
                 }
             }
             __syncthreads();
@@ -975,32 +986,40 @@ __device__ __forceinline__ void band_gather(const Args<T, S> &A, T *sm)
                 }
             }
             __syncthreads();
-            // y-contraction into the owned output
-            if (oa < BR) {
-                const int a = a0 + oa;
-                for (int q = 0; q < ng; q++) {
-                    const int g = g0 + q;
-                    const int ilo = s_ilo[g];
-                    int ilo_a, cnt;
-                    const T *wt;
-                    if (tab) {
-                        const int ti = q * BR + oa;
-                        ilo_a = ylo[ti];
-                        cnt = yct[ti];
-                        wt = yw + (size_t)ti * kAdjW;
-                    } else {
-                        const int ty = ((g * G.L + l) * 2 + 1) * FEWHA_MAX_GRID + a;
-                        ilo_a = __ldg(G.adj_lo + ty);
-                        cnt = __ldg(G.adj_cnt + ty);
-                        wt = G.adj_w + (size_t)ty * kAdjW;
+            // y-contraction into the owned outputs
+#pragma unroll
+            for (int j = 0; j < kOutPT; j++) {
+                const int o = threadIdx.x + j * blockDim.x, oa = o >> lgn, ob = o & (n - 1);
+                if (o < nout) {
+                    const int a = a0 + oa;
+                    for (int q = 0; q < ng; q++) {
+                        const int g = g0 + q;
+                        const int ilo = s_ilo[g];
+                        int ilo_a, cnt;
+                        const T *wt;
+                        if (tab) {
+                            const int ti = q * BR + oa;
+                            ilo_a = ylo[ti];
+                            cnt = yct[ti];
+                            wt = yw + (size_t)ti * kAdjW;
+                        } else {
+                            const int ty = ((g * G.L + l) * 2 + 1) * FEWHA_MAX_GRID + a;
+                            ilo_a = __ldg(G.adj_lo + ty);
+                            cnt = __ldg(G.adj_cnt + ty);
+                            wt = G.adj_w + (size_t)ty * kAdjW;
+                        }
+                        const T *col = Tb + ((s_base[q] + ilo_a - ilo) << lgn) + ob;
+                        for (int c = 0; c < cnt; c++) acc[j] += wt[c] * col[c << lgn];  // cnt <= kAdjW
                     }
-                    const T *col = Tb + ((s_base[q] + ilo_a - ilo) << lgn) + ob;
-                    for (int c = 0; c < cnt; c++) acc += wt[c] * col[c << lgn];  // cnt <= kAdjW
                 }
             }
             __syncthreads();
         }
-        if (oa < BR && threadIdx.x < nout) A.u[G.lay_off[l] + ((long)(a0 + oa) << lgn) + ob] = acc;
+#pragma unroll
+        for (int j = 0; j < kOutPT; j++) {
+            const int o = threadIdx.x + j * blockDim.x;
+            if (o < nout) A.u[G.lay_off[l] + ((long)(a0 + (o >> lgn)) << lgn) + (o & (n - 1))] = acc[j];
+        }
     }
 }
 

@@ -615,7 +615,7 @@ struct Impl : ImplBase {
         if ((st = up(fw, &G.fw)) || (st = up(wm, &G.wmask)) || (st = up(ad, &G.alpha_d)) ||
             (st = up(one, &G.invJ)))
             return st;
-        // P^T work items: bands of rows with band_rows * n_l <= kThreads outputs;
+        // P^T work items: bands of rows with band_rows * n_l <= kBandOutputs outputs;
         // 8 rows, and 4 rows on layers smaller than the largest (their coarser
         // grid touches about twice as many pupil rows per layer row, so a
         // half-height band balances the staged work)
@@ -626,7 +626,7 @@ struct Impl : ImplBase {
             int n = P.geom.layers[l].n, lg = 0;
             while ((1 << lg) < n) lg++;
             G.lay_lg[l] = lg;
-            int BR = std::max(1, std::min(n, std::min(kThreads / n, n < n_largest ? 4 : 8)));
+            int BR = std::max(1, std::min(n, std::min(kBandOutputs / n, n < n_largest ? 4 : 8)));
             for (int a0 = 0; a0 < n; a0 += BR) {
                 bl.push_back(l);
                 br0.push_back(a0);
@@ -739,12 +739,12 @@ struct Impl : ImplBase {
         sm_fixed = std::max(sm_layer, std::min(want, smem_cap));
         // P^T weight tables of one band (all guide stars) staged beside the
         // psi rows when one thread per entry and the shared memory suffice
-        const int band_rows_max = std::min(nmax, std::min(kThreads / nmax, 8));
+        const int band_rows_max = std::min(nmax, std::min(kBandOutputs / nmax, 8));
         const size_t tab_entries = (size_t)P.G * (nmax + band_rows_max);
         const size_t tab_bytes = tab_entries * (kAdjW * sizeof(T) + 2 * sizeof(int));
         const size_t gather_bytes = (size_t)G.rows_chunk * row_bytes + tab_bytes;
         G.stage_tab = 0;
-        if (tab_entries <= (size_t)kThreads && gather_bytes <= smem_cap) {
+        if (tab_entries <= (size_t)kTabPT * kThreads && gather_bytes <= smem_cap) {
             G.stage_tab = 1;
             smem = std::max(smem, gather_bytes);
             sm_fixed = std::max(sm_fixed, gather_bytes);
