@@ -307,9 +307,9 @@ def run_batched(args, flush):
     """64 independent instances of uneven size (24 x tiny, 24 x medium, 16 x ELT
     geometry, each with its own seeded frozen-flow sequence), FP32, augmented
     PCG to the same relative residual, in ONE cooperative launch per step with
-    an autotuned split of the CTAs between instances (one round, or two rounds:
-    the 16 ELT instances first on many CTAs each, then the small instances on
-    the same CTAs, separated by a barrier over the launch)."""
+    an autotuned split of the CTAs between instances (one round, or two or
+    three rounds: the ELT instances first on many CTAs each, then the small
+    instances on the same CTAs, separated by a barrier over the launch)."""
     import numpy as np
     import torch
     from paper_2011_06842_gb300 import Fewha, FewhaBatch, autotune_batch, workload
@@ -332,14 +332,19 @@ def run_batched(args, flush):
                 args.max_iter, rtol=args.rtol, augmented=not args.plain)
         frame[0] = (t + 1) % 4  # the autotuner reuses the first frames
 
-    # candidates: one round (the library's work-proportional split), and two
-    # rounds (the 16 ELT instances on 8-9 CTAs each, then the small ones)
+    # candidates: one round (the library's work-proportional split); two
+    # rounds (the 16 ELT instances on 8-9 CTAs each, then the small ones); three
+    # rounds (8 ELT instances at a time on 18-19 CTAs each, enough for the
+    # split transforms, then the small ones)
     two = [0 if k == "elt" else 1 for k in kinds]
+    elt_ids = [i for i, k in enumerate(kinds) if k == "elt"]
+    three = [(0 if elt_ids.index(i) < 8 else 1) if k == "elt" else 2 for i, k in enumerate(kinds)]
 
     def split(elt, med, tiny):
         return [elt if k == "elt" else med if k == "medium" else tiny for k in kinds]
 
-    cands = [None, (split(9, 4, 1), two), (split(9, 5, 1), two), (split(8, 5, 1), two)]
+    cands = [None, (split(9, 4, 1), two), (split(9, 5, 1), two), (split(8, 5, 1), two),
+             (split(19, 4, 1), three), (split(18, 5, 1), three)]
     best, timings = autotune_batch(fewhas, step, candidates=cands, reps=2)
     for x in inst:  # fresh states after tuning
         x["st"] = x["f"].new_state(args.k)
