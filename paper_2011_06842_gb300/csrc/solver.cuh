@@ -352,6 +352,14 @@ __device__ __forceinline__ bool phase_UA1(const Args<T, S> &A, const Basis &b, i
     typedef typename AccT<T>::type Acc;
     constexpr int W = VW<T>::W;
     const int kv = b.kv;
+    const Geo<T> &G = A.geo;
+    const bool split = split_levels(A);
+    const bool proj_all = (k == 0) || A.recycle_all;
+    // The first vector this thread updates (split form, k > 0, last-direction
+    // projection) has its operands loaded before the reduction below, which
+    // hides their latency.
+    long pe = -1;
+    T pr[W], pj[W], pa[W], ppp[W], ppm[W];
     double *red = sc.red;
     if (k == 0) {
         // red: [0] bb, [1] rr (R3), [2..2+kv) Q^T z, [2+kv] rz, [3+kv] rr (INIT2)
@@ -373,6 +381,23 @@ __device__ __forceinline__ bool phase_UA1(const Args<T, S> &A, const Basis &b, i
         }
     } else {
         // red: [0] rz, [1] zq, [2] rp, [3] rr (E_{k-1}); [4..4+kv) Q^T z, [4+kK..) P^T r
+        if (split && !A.recycle_all) {
+            if (A.vrank() < G.L) {
+                const int l = A.vrank(), h = G.lay_n[l] >> 1, lgh = G.lay_lg[l] - 1, be = threadIdx.x * W;
+                if (be < h * h) pe = G.lay_off[l] + (long)(be >> lgh) * G.lay_n[l] + (be & (h - 1));
+            } else {
+                long lo, hi;
+                cta_range_vec(G.n, W, A.vrank() - G.L, A.ncta - G.L, lo, hi);
+                if (lo + (long)threadIdx.x * W < hi) pe = lo + (long)threadIdx.x * W;
+            }
+            if (pe >= 0) {
+                vld_cg(A.r + pe, pr);
+                vld_nc(G.invJ + pe, pj);
+                vld_nc(G.alpha_d + pe, pa);
+                vld_cg(newP(A, b, k - 1) + pe, ppp);
+                if (kv > 0) vld_nc(oldP(A, b, kv - 1) + pe, ppm);
+            }
+        }
         const int e0 = kSlotE + ((k - 1) & 1) * kSlotEStride;
         if (A.recycle_all && kv > 0)
             reduce_ranges(A.part, A.ncta, {e0, 4, red}, {e0 + 4, kv, red + 4}, {e0 + 4 + kK, kv, red + 4 + kK});
@@ -414,21 +439,32 @@ __device__ __forceinline__ bool phase_UA1(const Args<T, S> &A, const Basis &b, i
     if (sc.stop) return false;
 
     const T beta = (T)sc.beta, mu = (T)sc.mu;
-    const Geo<T> &G = A.geo;
-    const bool split = split_levels(A);
-    const bool proj_all = (k == 0) || A.recycle_all;
     T *pk = newP(A, b, k);
-    const T *pprev = k > 0 ? newP(A, b, k - 1) : nullptr;
-    const T *pm = kv > 0 ? oldP(A, b, kv - 1) : nullptr;
     __shared__ const T *sp[kK], *sq[kK];
     if (proj_all && kv > 0) basis_table(A, b, sp, sq);
     Acc acc[2] = {0, 0};
-    auto update = [&](long e, T (&p)[W]) {
-        T rv[W], jv[W], ad[W], pp[W];
-        vld_cg(A.r + e, rv);
-        vld_nc(A.geo.invJ + e, jv);
-        vld_nc(A.geo.alpha_d + e, ad);
-        if (k > 0) vld_cg(pprev + e, pp);
+    const T *pprev = k > 0 ? newP(A, b, k - 1) : nullptr;
+    const T *pm = kv > 0 ? oldP(A, b, kv - 1) : nullptr;
+    // PF: the call may take the prefetched operands (split form only, so that
+    // the whole-layer loop does not keep them live across its transforms)
+    auto update_t = [&](bool use_pf, long e, T (&p)[W]) {
+        T rv[W], jv[W], ad[W], pp[W], pmv[W];
+        if (use_pf && e == pe) {
+#pragma unroll
+            for (int i = 0; i < W; i++) {
+                rv[i] = pr[i];
+                jv[i] = pj[i];
+                ad[i] = pa[i];
+                pp[i] = ppp[i];
+                pmv[i] = ppm[i];
+            }
+        } else {
+            vld_cg(A.r + e, rv);
+            vld_nc(G.invJ + e, jv);
+            vld_nc(G.alpha_d + e, ad);
+            if (k > 0) vld_cg(pprev + e, pp);
+            if (kv > 0 && !proj_all) vld_nc(pm + e, pmv);
+        }
 #pragma unroll
         for (int i = 0; i < W; i++) p[i] = jv[i] * rv[i];
         if (kv > 0) {
@@ -441,8 +477,6 @@ __device__ __forceinline__ bool phase_UA1(const Args<T, S> &A, const Basis &b, i
                     for (int i = 0; i < W; i++) p[i] -= tj * pj[i];
                 }
             } else {
-                T pmv[W];
-                vld_nc(pm + e, pmv);
 #pragma unroll
                 for (int i = 0; i < W; i++) p[i] -= mu * pmv[i];
             }
@@ -455,9 +489,12 @@ __device__ __forceinline__ bool phase_UA1(const Args<T, S> &A, const Basis &b, i
         }
         vst(pk + e, p);  // p_k into its basis slot
     };
-    for (int l = A.vrank(); l < G.L; l += A.ncta) {
-        if (split) {
-            const int h = G.lay_n[l] >> 1, lgh = G.lay_lg[l] - 1;
+    auto update = [&](long e, T (&p)[W]) { update_t(true, e, p); };
+    auto update_np = [&](long e, T (&p)[W]) { update_t(false, e, p); };
+    if (split) {
+        // one layer per layer CTA (ncta >= 2L); the others take the details
+        if (A.vrank() < G.L) {
+            const int l = A.vrank(), h = G.lay_n[l] >> 1, lgh = G.lay_lg[l] - 1;
             for_block_vectors(G, l, [&](long e, int be) {
                 T p[W];
                 update(e, p);
@@ -475,13 +512,23 @@ __device__ __forceinline__ bool phase_UA1(const Args<T, S> &A, const Basis &b, i
                 for (int i = 0; i < W; i++) x[i] = buf[s0 + i];
                 vst(ll + be, x);
             }
+            __syncthreads();
         } else {
+            long lo, hi;
+            cta_range_vec(G.n, W, A.vrank() - G.L, A.ncta - G.L, lo, hi);
+            for_detail_vectors(G, lo, hi, [&](long e) {
+                T p[W];
+                update(e, p);
+            });
+        }
+    } else {
+        for (int l = A.vrank(); l < G.L; l += A.ncta) {
             // whole layer: p_k into shared memory, all levels, nodal = W^{-1} p_k
             const int n = G.lay_n[l], lgn = G.lay_lg[l], nv = n * n / W;
             const long off = G.lay_off[l];
             for (int v = threadIdx.x; v < nv; v += blockDim.x) {
                 T p[W];
-                update(off + (long)v * W, p);
+                update_np(off + (long)v * W, p);
                 const int s0 = spad(v * W, lgn);
 #pragma unroll
                 for (int i = 0; i < W; i++) buf[s0 + i] = p[i];
@@ -496,16 +543,8 @@ __device__ __forceinline__ bool phase_UA1(const Args<T, S> &A, const Basis &b, i
                 for (int i = 0; i < W; i++) x[i] = buf[s0 + i] * sc;
                 vst(A.nodal + off + (long)v * W, x);
             }
+            __syncthreads();
         }
-        __syncthreads();
-    }
-    if (split && A.vrank() >= G.L) {
-        long lo, hi;
-        cta_range_vec(G.n, W, A.vrank() - G.L, A.ncta - G.L, lo, hi);
-        for_detail_vectors(G, lo, hi, [&](long e) {
-            T p[W];
-            update(e, p);
-        });
     }
     if (defer) {
         // the caller adds them to a later phase's block reduction
