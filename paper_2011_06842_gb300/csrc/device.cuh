@@ -104,6 +104,12 @@ struct Geo {
     // adj_cnt - 1 with weights adj_w[..][0 .. adj_cnt), index ((g*L + l)*2 + axis)*FEWHA_MAX_GRID + k
     const int *adj_lo, *adj_cnt;
     const T *adj_w;             // [..][kAdjW]
+    // y-contraction of a band as one list per (band, group, band row): staged
+    // psi row and weight of every tap of every guide star of the group, in
+    // guide-star then tap order; index ((w * G + g0) * ybr + r) (* ymax + t)
+    const int *band_ycnt, *band_yrow;
+    const T *band_yw;
+    int ybr, ymax;
 };
 
 enum Mode { kApply = 0, kRhs = 1, kSolve = 2 };
@@ -862,30 +868,22 @@ __device__ __forceinline__ void band_gather(const Args<T, S> &A, T *sm)
                 if (q < ng) s_off[q] = (long)g * m * m + (long)s_ilo[g] * m - c;
             }
             __syncthreads();
-            const int nxt = ng << lgn, nyt = ng * BR;
-            // weight tables of the group (x: per guide star and layer column,
-            // y: per guide star and band row), loaded in the same latency round
+            const int nxt = ng << lgn;
+            // x weight tables of the group (per guide star and layer column),
+            // loaded in the same latency round as the psi rows
             T *xw = Tb + RC * n;                          // [kAdjW][ng * n] (tap-major: no bank conflicts)
-            T *yw = xw + (size_t)nxt * kAdjW;             // [ng][BR][kAdjW]
-            int *xlo = reinterpret_cast<int *>(yw + (size_t)nyt * kAdjW), *xct = xlo + nxt;
-            int *ylo = xct + nxt, *yct = ylo + nyt;
+            int *xlo = reinterpret_cast<int *>(xw + (size_t)nxt * kAdjW), *xct = xlo + nxt;
             const bool tab = G.stage_tab != 0;
-            // table entries tt = threadIdx.x + j blockDim.x (nxt + nyt <= kTabPT blockDim.x)
+            // table entries tt = threadIdx.x + j blockDim.x (nxt <= kTabPT blockDim.x)
             int t_lo[kTabPT], t_ct[kTabPT];
             T t_w[kTabPT][kAdjW];
 #pragma unroll
             for (int j = 0; j < kTabPT; j++) {
                 const int tt = threadIdx.x + j * blockDim.x;
                 t_lo[j] = t_ct[j] = 0;
-                if (tab && tt < nxt + nyt) {
-                    int idx;
-                    if (tt < nxt) {
-                        const int q = tt >> lgn, bcol = tt & (n - 1);
-                        idx = ((g0 + q) * G.L + l) * 2 * FEWHA_MAX_GRID + bcol;
-                    } else {
-                        const int q = (tt - nxt) / BR, r = (tt - nxt) - q * BR;
-                        idx = (((g0 + q) * G.L + l) * 2 + 1) * FEWHA_MAX_GRID + a0 + r;
-                    }
+                if (tab && tt < nxt) {
+                    const int q = tt >> lgn, bcol = tt & (n - 1);
+                    const int idx = ((g0 + q) * G.L + l) * 2 * FEWHA_MAX_GRID + bcol;
                     t_lo[j] = __ldg(G.adj_lo + idx);
                     t_ct[j] = __ldg(G.adj_cnt + idx);
 #pragma unroll
@@ -916,19 +914,11 @@ __device__ __forceinline__ void band_gather(const Args<T, S> &A, T *sm)
 #pragma unroll
             for (int j = 0; j < kTabPT; j++) {
                 const int tt = threadIdx.x + j * blockDim.x;
-                if (tab && tt < nxt + nyt) {
-                    if (tt < nxt) {
-                        xlo[tt] = t_lo[j];
-                        xct[tt] = t_ct[j];
+                if (tab && tt < nxt) {
+                    xlo[tt] = t_lo[j];
+                    xct[tt] = t_ct[j];
 #pragma unroll
-                        for (int c = 0; c < kAdjW; c++) xw[(size_t)c * nxt + tt] = t_w[j][c];
-                    } else {
-                        const int e = tt - nxt;
-                        ylo[e] = t_lo[j];
-                        yct[e] = t_ct[j];
-#pragma unroll
-                        for (int c = 0; c < kAdjW; c++) yw[(size_t)e * kAdjW + c] = t_w[j][c];
-                    }
+                    for (int c = 0; c < kAdjW; c++) xw[(size_t)c * nxt + tt] = t_w[j][c];
                 }
             }
             __syncthreads();
@@ -986,31 +976,18 @@ __device__ __forceinline__ void band_gather(const Args<T, S> &A, T *sm)
                 }
             }
             __syncthreads();
-            // y-contraction into the owned outputs
+            // y-contraction into the owned outputs: the band row's tap list of
+            // this group (staged row, weight), the same for the lanes of a warp
 #pragma unroll
             for (int j = 0; j < kOutPT; j++) {
-                const int o = threadIdx.x + j * blockDim.x, oa = o >> lgn, ob = o & (n - 1);
+                const int o = threadIdx.x + j * blockDim.x;
                 if (o < nout) {
-                    const int a = a0 + oa;
-                    for (int q = 0; q < ng; q++) {
-                        const int g = g0 + q;
-                        const int ilo = s_ilo[g];
-                        int ilo_a, cnt;
-                        const T *wt;
-                        if (tab) {
-                            const int ti = q * BR + oa;
-                            ilo_a = ylo[ti];
-                            cnt = yct[ti];
-                            wt = yw + (size_t)ti * kAdjW;
-                        } else {
-                            const int ty = ((g * G.L + l) * 2 + 1) * FEWHA_MAX_GRID + a;
-                            ilo_a = __ldg(G.adj_lo + ty);
-                            cnt = __ldg(G.adj_cnt + ty);
-                            wt = G.adj_w + (size_t)ty * kAdjW;
-                        }
-                        const T *col = Tb + ((s_base[q] + ilo_a - ilo) << lgn) + ob;
-                        for (int c = 0; c < cnt; c++) acc[j] += wt[c] * col[c << lgn];  // cnt <= kAdjW
-                    }
+                    const size_t e = ((size_t)w * G.G + g0) * G.ybr + (o >> lgn);
+                    const int cnt = __ldg(G.band_ycnt + e);
+                    const int *yr = G.band_yrow + e * G.ymax;
+                    const T *yv = G.band_yw + e * G.ymax;
+                    const T *col = Tb + (o & (n - 1));
+                    for (int t = 0; t < cnt; t++) acc[j] += __ldg(yv + t) * col[__ldg(yr + t) << lgn];
                 }
             }
             __syncthreads();

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <utility>
 #include <cstddef>
 #include <cstring>
 #include <vector>
@@ -735,12 +736,53 @@ struct Impl : ImplBase {
                     }
                 }
             if ((st = up(gend, &G.band_gend)) || (st = up(gc, &G.band_gc))) return st;
+            // y-contraction lists: for band row r of band w and the group that
+            // starts at g0, the staged row (gc/m + pupil row - ilo) and weight of
+            // each tap, guide star after guide star
+            int ybr = 1, ymax = 1;
+            for (int w = 0; w < G.nbands; w++) ybr = std::max(ybr, brs[w]);
+            auto ytaps = [&](int w, int g, int r, std::vector<std::pair<int, double>> *out) {
+                const size_t t = ((size_t)g * P.L + bl[w]) * 2 + 1;
+                const int a = br0[w] + r, lo = P.alo[t * FEWHA_MAX_GRID + a], hi = P.ahi[t * FEWHA_MAX_GRID + a];
+                const size_t i = (size_t)g * G.nbands + w;
+                int cnt = 0;
+                for (int j = lo; j < hi; j++, cnt++) {
+                    if (!out) continue;
+                    const double w0 = P.fw[t * P.m + j];
+                    out->push_back({gc[i] / P.m + (j - bilo[i]), P.fk[t * P.m + j] == a ? 1.0 - w0 : w0});
+                }
+                return cnt;
+            };
+            for (int w = 0; w < G.nbands; w++)
+                for (int g0 = 0; g0 < P.G; g0 = gend[(size_t)g0 * G.nbands + w])
+                    for (int r = 0; r < brs[w]; r++) {
+                        int c = 0;
+                        for (int g = g0; g < gend[(size_t)g0 * G.nbands + w]; g++) c += ytaps(w, g, r, nullptr);
+                        ymax = std::max(ymax, c);
+                    }
+            std::vector<int> ycnt((size_t)G.nbands * P.G * ybr, 0), yrow(ycnt.size() * ymax, 0);
+            std::vector<T> yw(ycnt.size() * ymax, T(0));
+            for (int w = 0; w < G.nbands; w++)
+                for (int g0 = 0; g0 < P.G; g0 = gend[(size_t)g0 * G.nbands + w])
+                    for (int r = 0; r < brs[w]; r++) {
+                        std::vector<std::pair<int, double>> taps;
+                        for (int g = g0; g < gend[(size_t)g0 * G.nbands + w]; g++) ytaps(w, g, r, &taps);
+                        const size_t e = ((size_t)w * P.G + g0) * ybr + r;
+                        ycnt[e] = (int)taps.size();
+                        for (size_t t = 0; t < taps.size(); t++) {
+                            yrow[e * ymax + t] = taps[t].first;
+                            yw[e * ymax + t] = (T)taps[t].second;
+                        }
+                    }
+            G.ybr = ybr;
+            G.ymax = ymax;
+            if ((st = up(ycnt, &G.band_ycnt)) || (st = up(yrow, &G.band_yrow)) || (st = up(yw, &G.band_yw)))
+                return st;
         }
         sm_fixed = std::max(sm_layer, std::min(want, smem_cap));
-        // P^T weight tables of one band (all guide stars) staged beside the
-        // psi rows when one thread per entry and the shared memory suffice
-        const int band_rows_max = std::min(nmax, std::min(kBandOutputs / nmax, 8));
-        const size_t tab_entries = (size_t)P.G * (nmax + band_rows_max);
+        // P^T x weight tables of one band (all guide stars) staged beside the
+        // psi rows when kTabPT entries per thread and the shared memory suffice
+        const size_t tab_entries = (size_t)P.G * nmax;
         const size_t tab_bytes = tab_entries * (kAdjW * sizeof(T) + 2 * sizeof(int));
         const size_t gather_bytes = (size_t)G.rows_chunk * row_bytes + tab_bytes;
         G.stage_tab = 0;
