@@ -927,27 +927,26 @@ __device__ __forceinline__ void band_gather(const Args<T, S> &A, T *sm)
                 const int total = s_base[ng];  // staged rows
                 int q = 0;                     // guide star of the staged row (rows only grow)
                 if (tab && (int)blockDim.x % n == 0) {
-                    // each thread keeps one column b; its weights stay in registers
-                    // until the guide star changes
-                    const int bcol = threadIdx.x & (n - 1), rstep = blockDim.x >> lgn;
-                    int qc = -1, jlo = 0, cnt = 0;
-                    T wr[kAdjW];
-                    for (int row = threadIdx.x >> lgn; row < total; row += rstep) {
-                        while (row >= s_base[q + 1]) q++;
-                        if (q != qc) {
-                            const int ti = (q << lgn) + bcol;
-                            jlo = xlo[ti];
-                            cnt = xct[ti];
+                    // each thread keeps one column b and the rows r0 + k rstep;
+                    // guide star after guide star, its weights in registers and
+                    // the taps unrolled up to the warp's largest count
+                    const int bcol = threadIdx.x & (n - 1), r0 = threadIdx.x >> lgn, rstep = blockDim.x >> lgn;
+                    for (q = 0; q < ng; q++) {
+                        const int ti = (q << lgn) + bcol;
+                        const int jlo = xlo[ti], cnt = xct[ti];
+                        const int cmax = __reduce_max_sync(0xffffffffu, (unsigned)cnt);
+                        T wr[kAdjW];
 #pragma unroll
-                            for (int c = 0; c < kAdjW; c++) wr[c] = c < cnt ? xw[(size_t)c * nxt + ti] : T(0);
-                            qc = q;
+                        for (int c = 0; c < kAdjW; c++) wr[c] = c < cnt ? xw[(size_t)c * nxt + ti] : T(0);
+                        const int rb = s_base[q], re = s_base[q + 1];
+                        for (int row = rb + ((r0 - rb) % rstep + rstep) % rstep; row < re; row += rstep) {
+                            const T *rowp = ps + row * m + jlo;
+                            T v = 0;
+#pragma unroll
+                            for (int c = 0; c < kAdjW; c++)
+                                if (c < cmax && c < cnt) v += wr[c] * rowp[c];
+                            Tb[(row << lgn) + bcol] = v;
                         }
-                        const T *rowp = ps + row * m + jlo;
-                        T v = 0;
-#pragma unroll
-                        for (int c = 0; c < kAdjW; c++)
-                            if (c < cnt) v += wr[c] * rowp[c];
-                        Tb[(row << lgn) + bcol] = v;
                     }
                 } else {
                     for (int e = threadIdx.x; e < (total << lgn); e += blockDim.x) {
