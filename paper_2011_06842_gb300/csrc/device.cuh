@@ -729,7 +729,7 @@ __device__ __forceinline__ typename AccT<T>::type wfs_phase(const Args<T, S> &A,
     const int TY = G.tile_y, TX = G.tile_x, HY = TY + 2, HX = TX + 2, SY = TY + 1, SX = TX + 1;
     const int m = G.m, ns = G.ns;
     const int per_g = G.tiles_y * G.tiles_x, total = G.G * per_g;
-    T *phi = sm;                          // [L][HY*HX] per-layer contributions (OP)
+    T *phi = sm;                          // [HY*HX] sum over layers (OP)
     T *sx = sm + (size_t)G.L * HY * HX;   // [SY*SX]
     T *sy = sx + SY * SX;
     Acc ws = 0;
@@ -737,42 +737,36 @@ __device__ __forceinline__ typename AccT<T>::type wfs_phase(const Args<T, S> &A,
         const int g = w / per_g, tt = w - g * per_g;
         const int i0 = (tt / G.tiles_x) * TY, j0 = (tt % G.tiles_x) * TX;
         if (!RHS) {
-            // per (layer, halo node) bilinear value; U items per thread with all
-            // of their loads in flight before the shared-memory stores
-            const int tot = G.L * HY * HX;
-            constexpr int U = 3;
-            for (int e0 = threadIdx.x; e0 < tot; e0 += U * blockDim.x) {
-                T v[U];
+            // phi at each halo node: the sum over layers of the bilinear value of
+            // the layer at the node's projection (layer after layer, from 0),
+            // with the loads of kLC layers in flight at once
+            constexpr int kLC = 9;
+            for (int loc = threadIdx.x; loc < HY * HX; loc += blockDim.x) {
+                const int i = i0 - 1 + loc / HX, j = j0 - 1 + loc % HX;
+                T sum = 0;
+                if (i >= 0 && i < m && j >= 0 && j < m) {
+                    for (int l0 = 0; l0 < G.L; l0 += kLC) {
+                        T v[kLC];
 #pragma unroll
-                for (int u = 0; u < U; u++) {
-                    const int e = e0 + u * blockDim.x;
-                    v[u] = 0;
-                    if (e < tot) {
-                        const int l = e / (HY * HX), loc = e - l * HY * HX;
-                        const int i = i0 - 1 + loc / HX, j = j0 - 1 + loc % HX;
-                        if (i >= 0 && i < m && j >= 0 && j < m) {
-                            const int bx = ((g * G.L + l) * 2 + 0) * m, by = ((g * G.L + l) * 2 + 1) * m;
-                            const int kx = __ldg(G.fk + bx + j), ky = __ldg(G.fk + by + i);
-                            const T wx = __ldg(G.fw + bx + j), wy = __ldg(G.fw + by + i);
-                            const int n = G.lay_n[l];
-                            const S *Lp = A.nodal + G.lay_off[l] + (long)ky * n + kx;
-                            const T v00 = Cv<S>::ld(ldcg(Lp)), v01 = Cv<S>::ld(ldcg(Lp + 1));
-                            const T v10 = Cv<S>::ld(ldcg(Lp + n)), v11 = Cv<S>::ld(ldcg(Lp + n + 1));
-                            v[u] = (T(1) - wy) * ((T(1) - wx) * v00 + wx * v01) + wy * ((T(1) - wx) * v10 + wx * v11);
+                        for (int u = 0; u < kLC; u++) {
+                            const int l = l0 + u;
+                            v[u] = 0;
+                            if (l < G.L) {
+                                const int bx = ((g * G.L + l) * 2 + 0) * m, by = ((g * G.L + l) * 2 + 1) * m;
+                                const int kx = __ldg(G.fk + bx + j), ky = __ldg(G.fk + by + i);
+                                const T wx = __ldg(G.fw + bx + j), wy = __ldg(G.fw + by + i);
+                                const int n = G.lay_n[l];
+                                const S *Lp = A.nodal + G.lay_off[l] + (long)ky * n + kx;
+                                const T v00 = Cv<S>::ld(ldcg(Lp)), v01 = Cv<S>::ld(ldcg(Lp + 1));
+                                const T v10 = Cv<S>::ld(ldcg(Lp + n)), v11 = Cv<S>::ld(ldcg(Lp + n + 1));
+                                v[u] = (T(1) - wy) * ((T(1) - wx) * v00 + wx * v01) + wy * ((T(1) - wx) * v10 + wx * v11);
+                            }
                         }
+#pragma unroll
+                        for (int u = 0; u < kLC; u++) sum += v[u];
                     }
                 }
-#pragma unroll
-                for (int u = 0; u < U; u++) {
-                    const int e = e0 + u * blockDim.x;
-                    if (e < tot) phi[e] = v[u];
-                }
-            }
-            __syncthreads();
-            for (int loc = threadIdx.x; loc < HY * HX; loc += blockDim.x) {
-                T s = 0;
-                for (int l = 0; l < G.L; l++) s += phi[l * HY * HX + loc];
-                phi[loc] = s;
+                phi[loc] = sum;
             }
             __syncthreads();
         }
