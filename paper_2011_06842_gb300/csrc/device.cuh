@@ -820,8 +820,31 @@ __device__ __forceinline__ typename AccT<T>::type wfs_phase(const Args<T, S> &A,
 // with psi rows staged in shared memory in chunks of rows_chunk rows.
 // Thread (a - a0, b) owns output u[a][b]; no atomics, fixed summation order.
 // ---------------------------------------------------------------------------
+// Header of a P^T work item for guide star threadIdx.x (< G): pupil rows and
+// group of the band, loaded ahead of time by band_header().
+struct BandHdr {
+    int ilo, ihi, gend, gc;
+};
+
 template <typename T, typename S>
-__device__ __forceinline__ void band_gather(const Args<T, S> &A, T *sm)
+__device__ __forceinline__ BandHdr band_header(const Args<T, S> &A, int w)
+{
+    BandHdr h = {0, 0, 0, 0};
+    const Geo<T> &G = A.geo;
+    if (threadIdx.x < G.G && w < G.nbands) {
+        const int i = threadIdx.x * G.nbands + w;
+        h.ilo = __ldg(G.band_ilo + i);
+        h.ihi = __ldg(G.band_ihi + i);
+        h.gend = __ldg(G.band_gend + i);
+        h.gc = __ldg(G.band_gc + i);
+    }
+    return h;
+}
+
+// pre: the header of the CTA's first work item (w = A.vrank()), when the
+// caller loaded it before other work to hide its latency
+template <typename T, typename S>
+__device__ __forceinline__ void band_gather(const Args<T, S> &A, T *sm, const BandHdr *pre = nullptr)
 {
     const Geo<T> &G = A.geo;
     const int m = G.m, RC = G.rows_chunk, NB = G.nbands;
@@ -840,11 +863,11 @@ __device__ __forceinline__ void band_gather(const Args<T, S> &A, T *sm)
         // pupil rows [ilo, ihi) of every guide star for this band and its
         // group (precomputed on the host), one load each in parallel
         if (threadIdx.x < G.G) {
-            const int i = threadIdx.x * NB + w;
-            s_ilo[threadIdx.x] = __ldg(G.band_ilo + i);
-            s_ihi[threadIdx.x] = __ldg(G.band_ihi + i);
-            s_gend[threadIdx.x] = __ldg(G.band_gend + i);
-            s_gc[threadIdx.x] = __ldg(G.band_gc + i);
+            const BandHdr h = (pre && w == A.vrank()) ? *pre : band_header(A, w);
+            s_ilo[threadIdx.x] = h.ilo;
+            s_ihi[threadIdx.x] = h.ihi;
+            s_gend[threadIdx.x] = h.gend;
+            s_gc[threadIdx.x] = h.gc;
         }
         __syncthreads();
         // guide stars in groups whose pupil rows fit the RC staged rows

@@ -569,6 +569,7 @@ __device__ __forceinline__ bool phase_C(const Args<T, S> &A, const Basis &b, int
                                      bool rz_in_sc = false)
 {
     double *red = sc.red;  // [0] ws, [1] pd, [2] rz0 (k = 0)
+    const BandHdr hdr = band_header(A, A.vrank());  // in flight during the reduction
     reduce_ranges(A.part, A.ncta, {kSlotB + (k & 1), 1, red}, {kSlotA + (k & 1) * 2, k == 0 ? 2 : 1, red + 1});
     if (threadIdx.x == 0) {
         // rz_k: from U_k in this CTA's shared memory (persistent kernel) or the record
@@ -601,7 +602,7 @@ __device__ __forceinline__ bool phase_C(const Args<T, S> &A, const Basis &b, int
     }
     __syncthreads();
     if (sc.stop) return false;
-    band_gather<T, S>(A, sm);
+    band_gather<T, S>(A, sm, &hdr);
     return true;
 }
 
@@ -806,12 +807,12 @@ __device__ __forceinline__ void phase_D2E_impl(const Args<T, S> &A, const Basis 
     for (int i = 0; i < NA; i++) acc[i] = 0;
     auto update_w = [&](long e, const T (&wq)[W]) {
         T p[W], ad[W], c[W], r[W], jv[W], q[W], z[W];
+        T pmv[W], qmv[W];
         vld_cg(pk + e, p);
         vld_nc(A.geo.alpha_d + e, ad);
         vld_cg(A.c + e, c);
         vld_cg(A.r + e, r);
         vld_nc(A.geo.invJ + e, jv);
-        T pmv[W], qmv[W];
         if (last) {
             vld_nc(pm + e, pmv);
             vld_nc(qm + e, qmv);
@@ -881,36 +882,37 @@ __device__ __forceinline__ void phase_D2E_impl(const Args<T, S> &A, const Basis 
         }
     }
     // split: the layer's CTA runs the coarser analysis levels of the
-    // approximation block (from D1_k) -> wq, then the update on that block
-    for (int l = split_levels(A) ? A.vrank() : G.L; l < G.L; l += A.ncta) {
-        const int n = G.lay_n[l], h = n >> 1, lgh = G.lay_lg[l] - 1, nv = h * h / W;
-        const T *ll = A.ll + G.ll_off[l];
+    // approximation block (from D1_k), then the update on that block with
+    // W^{-T} u / delta taken from shared memory; the other CTAs update the
+    // detail coefficients (their wq from D1_k)
+    if (split_levels(A)) {
+        if (A.vrank() < G.L) {
+            const int l = A.vrank(), n = G.lay_n[l], h = n >> 1, lgh = G.lay_lg[l] - 1, nv = h * h / W;
+            const T *ll = A.ll + G.ll_off[l];
 #pragma unroll 4
-        for (int v = threadIdx.x; v < nv; v += blockDim.x) {
-            T x[W];
-            vld_cg(ll + (long)v * W, x);
-            const int s0 = spad(v * W, lgh);
+            for (int v = threadIdx.x; v < nv; v += blockDim.x) {
+                T x[W];
+                vld_cg(ll + (long)v * W, x);
+                const int s0 = spad(v * W, lgh);
 #pragma unroll
-            for (int i = 0; i < W; i++) buf[s0 + i] = x[i];
+                for (int i = 0; i < W; i++) buf[s0 + i] = x[i];
+            }
+            __syncthreads();
+            fdwt2<T>(buf, G.pingpong ? buf + h * (h + 1) : buf, lgh, G.lay_J[l] - 1, G);
+            const T sc = G.inv_delta[l];
+            for_block_vectors(G, l, [&](long e, int be) {
+                T wq[W];
+                const int s0 = spad(be, lgh);
+#pragma unroll
+                for (int i = 0; i < W; i++) wq[i] = buf[s0 + i] * sc;
+                update_w(e, wq);
+            });
+            __syncthreads();
+        } else {
+            long lo, hi;
+            cta_range_vec(G.n, W, A.vrank() - G.L, A.ncta - G.L, lo, hi);
+            for_detail_vectors(G, lo, hi, update);
         }
-        __syncthreads();
-        fdwt2<T>(buf, G.pingpong ? buf + h * (h + 1) : buf, lgh, G.lay_J[l] - 1, G);
-        const T sc = G.inv_delta[l];
-        for_block_vectors(G, l, [&](long e, int be) {
-            T x[W];
-            const int s0 = spad(be, lgh);
-#pragma unroll
-            for (int i = 0; i < W; i++) x[i] = buf[s0 + i] * sc;
-            vst(A.wq + e, x);
-        });
-        __syncthreads();
-        for_block_vectors(G, l, [&](long e, int) { update(e); });
-        __syncthreads();
-    }
-    if (split_levels(A) && A.vrank() >= G.L) {
-        long lo, hi;
-        cta_range_vec(G.n, W, A.vrank() - G.L, A.ncta - G.L, lo, hi);
-        for_detail_vectors(G, lo, hi, update);
     }
     const int e0 = kSlotE + (k & 1) * kSlotEStride;
     int slots[NA];
