@@ -320,22 +320,20 @@ int fewha_set_trace(void *handle, unsigned long long *trace_dev, int capacity);
  * cudaMalloc, no cudaFree, no allocating library call, ever.  Meant for
  * callers that cannot allocate device memory at the point where they apply
  * the operator: a hard real-time control loop that must not stall on the
- * allocator (an allocation can synchronise the device), code issuing work
- * while a CUDA stream is being captured into a graph (allocation is not a
- * stream operation), and plug-ins whose host application owns every device
- * allocation.  The handle itself is still created (and its constant tables
- * allocated) once, beforehand, by fewha_create.
+ * allocator (an allocation can synchronise the device), and plug-ins whose
+ * host application owns every device allocation.  The handle itself is
+ * still created (and its constant tables allocated) once, beforehand, by
+ * fewha_create.
  * The intermediate buffers live in one statically reserved device array of
  * FEWHA_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds until
  * the process exits.  Problems whose buffers do not fit are rejected with
  * FEWHA_ERR_SCRATCH (an ELT-size FP64 operator, n = 98304 with 6 sensors of
  * 84 x 84 subapertures, needs about 4.8 MB).
  * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  All calls share the one array, which keeps the
- * last call's contents: calls that overlap on the GPU (different streams,
- * different handles on the same device) race and must be ordered by the
- * caller.  The paper has no counterpart; this is a deployment aid.
+ * (cudaGetSymbolAddress) with that device current.  All calls share the one
+ * array, which keeps the last call's contents: calls that overlap on the GPU
+ * (different streams, different handles on the same device) race and must be
+ * ordered by the caller.  The paper has no counterpart; this is a deployment aid.
  * x, y: device vectors of length n, 16-byte aligned, not overlapping. */
 #define FEWHA_NOALLOC_SCRATCH_BYTES (8u << 20)
 int fewha_apply_op_noalloc(void *handle, const void *x, void *y, cudaStream_t stream);

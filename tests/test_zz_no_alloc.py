@@ -1,7 +1,6 @@
 """fewha_apply_op_noalloc: the operator application for callers that cannot
 allocate device memory where they apply it (a real-time loop that must not
-stall on the allocator, work issued during CUDA graph capture, plug-ins whose
-host owns all device memory).  It must give the same y = M x as
+stall on the allocator, plug-ins whose host owns all device memory).  It must give the same y = M x as
 fewha_apply_op, call after call, while its intermediates live in the
 library's fixed static scratch; problems too large for that scratch are
 refused.  Collected last on purpose (file name), so a failing run has
