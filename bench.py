@@ -280,6 +280,7 @@ def run_ours(args):
     if rank == 0:
         out["e2e"] = run_e2e(f, geom, frames, sdt, args, aug)
         out["algorithm3"] = run_algorithm3(f, frames, sdt, args, aug, flush)
+        out["mcao_fit"] = run_mcao(f, geom, frames, sdt, args, aug, flush)
         if not args.no_compare:
             out["compare"] = run_compare(geom, w, frames, args, stats_buf, flush)
         if not args.no_cpu and ws == 1:
@@ -468,6 +469,54 @@ def run_algorithm3(f, frames, sdt, args, aug, flush):
     it = f.read_stats(stats)["iterations"]
     return {"us_per_frame": ms / K * 1e3, "frames_per_s": K / (ms / 1e3), "frames": K, "gain": 0.4,
             "loop": "closed", "iterations_last_frame": it, "gpu_launches_per_frame": 1 + 1 + 2 + 1}
+
+
+def run_mcao(f, geom, frames, sdt, args, aug, flush):
+    """MCAO fitting onto three mirrors after each solve (Sec. 5, 9-layer MCAO:
+    4 unpreconditioned CG iterations on the fitting normal equations, warm
+    started from the previous frame's mirrors): the paper's mirrors 85x85 /
+    0.5 m at 0 m, 47x47 / 1 m at 4 km, 53x53 / 1 m at 12.7 km; fitting
+    directions: the axis and 6 on a circle of 0.25 arcmin.  Per-frame CUDA
+    events around (a) the fit alone and (b) solve + fit, L2 flushed before
+    every frame."""
+    import math
+    import torch
+    from paper_2011_06842_gb300 import McaoFit
+    if geom.D > 30:
+        dms = [(85, 0.5, 0.0), (47, 1.0, 4000.0), (53, 1.0, 12700.0)]
+    else:
+        dms = [(geom.n_sub + 3, geom.D / geom.n_sub, 0.0), (int(geom.D) + 5, 1.0, 4000.0),
+               (int(geom.D) + 9, 1.0, 12700.0)]
+    r = 0.25 * math.pi / (180.0 * 60.0)
+    dirs = [(0.0, 0.0)] + [(r * math.cos(2 * math.pi * i / 6), r * math.sin(2 * math.pi * i / 6)) for i in range(6)]
+    fit = McaoFit(f, dms, dirs)
+    K = min(args.steps, 200)
+    sl = frames.to(sdt)
+    c = torch.zeros(f.n, dtype=f.dtype, device="cuda")
+    st = f.new_state(args.k)
+    stats = f.new_stats()
+    a = fit.new_mirrors()
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
+    for t in range(args.warmup):
+        f.solve(sl[t], c, st, args.max_iter, rtol=args.rtol, augmented=aug, stats=stats)
+        fit.fit(c, a, 4)
+    torch.cuda.synchronize()
+    for k in range(K):
+        if flush is not None:
+            flush.zero_()
+        ev[k][0].record()
+        f.solve(sl[args.warmup + k], c, st, args.max_iter, rtol=args.rtol, augmented=aug, stats=stats)
+        ev[k][1].record()
+        fit.fit(c, a, 4)
+        ev[k][2].record()
+    torch.cuda.synchronize()
+    fit_ms = sum(e[1].elapsed_time(e[2]) for e in ev)
+    step_ms = sum(e[0].elapsed_time(e[2]) for e in ev)
+    n_act = fit.n_actuators
+    fit.close()
+    return {"us_per_fit": fit_ms / K * 1e3, "us_per_step": step_ms / K * 1e3, "frames_per_s": K / (step_ms / 1e3),
+            "frames": K, "cg_iterations": 4, "mirrors": dms, "directions": len(dirs), "actuators": n_act,
+            "gpu_launches_per_fit": 2}
 
 
 def run_compare(geom, w, frames, args, stats_buf, flush):

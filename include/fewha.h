@@ -316,6 +316,41 @@ int fewha_set_timeout(void *handle, unsigned long long timeout_ns);
  * beyond the capacity are not recorded.  The paper has no counterpart. */
 int fewha_set_trace(void *handle, unsigned long long *trace_dev, int capacity);
 
+/* MCAO fitting onto several deformable mirrors (Sec. 5: the 9-layer MCAO
+ * case solves the fitting equation with an unpreconditioned CG of 4
+ * iterations; the paper's mirrors are 85x85 at 0 m with 0.5 m pitch, 47x47 at
+ * 4 km and 53x53 at 12.7 km with 1 m pitch).  The paper names the step but
+ * not its operator; this library's reading: the mirror shapes a = (a_1..a_D)
+ * minimise sum_t || P^DM_t a - P^L_t W^{-1} c ||^2 over the fitting
+ * directions theta_t, where P^L_t projects every layer onto the (n_s+1)^2
+ * pupil nodes in direction theta_t (no cone) and sums them and P^DM_t does the
+ * same for the mirrors, both bilinear on their grids; mirror d has
+ * dm_n[d]^2 actuators with pitch dm_pitch[d] centred on the axis (actuator i
+ * at x = (i - (dm_n[d] - 1)/2) dm_pitch[d]) at altitude dm_h[d].
+ * fewha_mcao_fit runs `iters` (0..FEWHA_MAX_ITER) CG iterations on the normal
+ * equations from the start the caller puts in `a`, and overwrites `a`.
+ * a: device vector of fewha_mcao_n_actuators values in the handle's working
+ * precision, mirror after mirror, each row-major (row = y).  c: layer
+ * coefficients as for fewha_fit.  The mcao object keeps a pointer to the
+ * handle (destroy it first) and owns its own tables and work vectors; calls on
+ * one object must not overlap.  FEWHA_ERR_GEOMETRY at creation when a
+ * projection leaves a layer grid or a mirror. */
+#define FEWHA_MAX_DM 4
+#define FEWHA_MAX_DIR 16
+typedef struct {
+    int n_dm;                          /* 1..FEWHA_MAX_DM */
+    int dm_n[FEWHA_MAX_DM];            /* actuators per side (>= 2) */
+    double dm_pitch[FEWHA_MAX_DM];     /* [m] */
+    double dm_h[FEWHA_MAX_DM];         /* altitude [m] */
+    int n_dir;                         /* 1..FEWHA_MAX_DIR */
+    double dir_x[FEWHA_MAX_DIR];       /* fitting directions [rad] */
+    double dir_y[FEWHA_MAX_DIR];
+} fewha_mcao_desc;
+int fewha_mcao_create(void *handle, const fewha_mcao_desc *desc, void **mcao_out);
+long fewha_mcao_n_actuators(const void *mcao);
+int fewha_mcao_fit(void *mcao, const void *c, void *a, int iters, cudaStream_t stream);
+void fewha_mcao_destroy(void *mcao);
+
 /* y = M x, like fewha_apply_op, but without allocating anything: no
  * cudaMalloc, no cudaFree, no allocating library call, ever.  Meant for
  * callers that cannot allocate device memory at the point where they apply

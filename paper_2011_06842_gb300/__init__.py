@@ -7,5 +7,5 @@ time step, as CUDA kernels behind the C ABI in include/fewha.h.
 libfewha.so in-tree; ``workload`` holds the paper's FLOP model and the
 algorithmic byte counts used for the roofline.
 """
-from .fewha import (Fewha, FewhaBatch, FewhaError, FewhaState, autotune_batch, exported_symbols,  # noqa: F401
+from .fewha import (Fewha, FewhaBatch, FewhaError, FewhaState, McaoFit, autotune_batch, exported_symbols,  # noqa: F401
                     load_library, make_geometry)

@@ -210,6 +210,50 @@ int fewha_fit(void *handle, const void *c, void *a_fit, cudaStream_t stream)
     return static_cast<Handle *>(handle)->w()->fit(c, a_fit, stream);
 }
 
+// MCAO fitting object: the handle's working-precision implementation and its plan
+struct Mcao {
+    ImplBase *impl = nullptr;
+    int device = 0;
+    void *plan = nullptr;
+    long n_act = 0;
+};
+
+int fewha_mcao_create(void *handle, const fewha_mcao_desc *desc, void **mcao_out)
+{
+    if (!handle || !desc || !mcao_out) return FEWHA_ERR_ARG;
+    *mcao_out = nullptr;
+    Handle *h = static_cast<Handle *>(handle);
+    if (cudaSetDevice(h->device) != cudaSuccess) return FEWHA_ERR_CUDA;
+    auto *m = new Mcao();
+    m->impl = h->w();
+    m->device = h->device;
+    const int st = m->impl->mcao_create(desc, &m->plan, &m->n_act);
+    if (st) {
+        delete m;
+        return st;
+    }
+    *mcao_out = m;
+    return FEWHA_OK;
+}
+
+long fewha_mcao_n_actuators(const void *mcao) { return mcao ? static_cast<const Mcao *>(mcao)->n_act : -1; }
+
+int fewha_mcao_fit(void *mcao, const void *c, void *a, int iters, cudaStream_t stream)
+{
+    if (!mcao || !c || !a || !aligned16(c)) return FEWHA_ERR_ARG;
+    Mcao *m = static_cast<Mcao *>(mcao);
+    return m->impl->mcao_fit(m->plan, c, a, iters, stream);
+}
+
+void fewha_mcao_destroy(void *mcao)
+{
+    if (!mcao) return;
+    Mcao *m = static_cast<Mcao *>(mcao);
+    cudaSetDevice(m->device);
+    if (m->plan) m->impl->mcao_destroy(m->plan);
+    delete m;
+}
+
 int fewha_pol_slopes(void *handle, const void *s, const void *a_prev, void *s_out, cudaStream_t stream)
 {
     if (!handle || !s || !a_prev || !s_out) return FEWHA_ERR_ARG;

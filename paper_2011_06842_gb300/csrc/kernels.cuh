@@ -4,11 +4,13 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <utility>
 #include <cstddef>
 #include <cstring>
 #include <vector>
 
+#include "mcao.cuh"
 #include "plan.h"
 #include "solver.cuh"
 
@@ -468,6 +470,10 @@ struct ImplBase {
     virtual int pol_slopes(const void *s_in, const void *a, void *s_out, cudaStream_t s) = 0;
     virtual int control(int closed, double gain, const void *am1, const void *ai, const void *af, void *an,
                         cudaStream_t s) = 0;
+    // MCAO fitting onto several mirrors: plan (tables, work vectors), fit, free
+    virtual int mcao_create(const fewha_mcao_desc *d, void **plan, long *n_act) = 0;
+    virtual int mcao_fit(void *plan, const void *c, void *a, int iters, cudaStream_t s) = 0;
+    virtual void mcao_destroy(void *plan) = 0;
     // y_v = M x_v for v < nvec (x_v = x + v*ldx, y_v = y + v*ldy), nvec <= kMaxVec
     virtual int apply_multi(const void *x, long ldx, void *y, long ldy, int nvec, cudaStream_t s) = 0;
     virtual int rhs(const void *sl, void *b, cudaStream_t s) = 0;
@@ -891,6 +897,170 @@ struct Impl : ImplBase {
         k_fit<T, S><<<(P.m * P.m + 255) / 256, 256, 0, s>>>(F, base.nodal, static_cast<T *>(a));
         return launch_check();
     }
+
+    // MCAO fitting plan: device tables and work vectors of one mirror system
+    struct McaoPlan {
+        McaoArgs<T, S> M{};
+        std::vector<void *> owned;
+        ~McaoPlan()
+        {
+            for (void *q : owned) cudaFree(q);
+        }
+    };
+
+    int mcao_create(const fewha_mcao_desc *d, void **out, long *n_act) override
+    {
+        if (d->n_dm < 1 || d->n_dm > FEWHA_MAX_DM || d->n_dir < 1 || d->n_dir > FEWHA_MAX_DIR)
+            return FEWHA_ERR_ARG;
+        const int m = P.m, L = P.L, D = d->n_dm, T_ = d->n_dir;
+        int nmax = 0;
+        for (int k = 0; k < D; k++) {
+            if (d->dm_n[k] < 2 || !(d->dm_pitch[k] > 0) || !std::isfinite(d->dm_pitch[k]) ||
+                !std::isfinite(d->dm_h[k]) || d->dm_h[k] < 0)
+                return FEWHA_ERR_ARG;
+            nmax = std::max(nmax, d->dm_n[k]);
+        }
+        for (int t = 0; t < T_; t++)
+            if (!std::isfinite(d->dir_x[t]) || !std::isfinite(d->dir_y[t])) return FEWHA_ERR_ARG;
+        // bilinear tables: pupil node j at x = -D/2 + j ds; layer node k at
+        // (k - n/2) d_l; actuator i at (i - (n-1)/2) pitch
+        std::vector<int> lk((size_t)T_ * L * 2 * m), dk((size_t)T_ * D * 2 * m);
+        std::vector<T> lw(lk.size()), dw(dk.size());
+        std::vector<int> alo((size_t)T_ * D * 2 * nmax, 0), ahi(alo.size(), 0);
+        auto table = [&](double shift, double spacing, double centre, int n, int *k_out, T *w_out) {
+            for (int j = 0; j < m; j++) {
+                const double f = (-0.5 * P.geom.D + j * P.ds + shift) / spacing + centre;
+                const int k = (int)std::floor(f);
+                if (k < 0 || k + 1 > n - 1) return false;
+                k_out[j] = k;
+                w_out[j] = (T)(f - k);
+            }
+            return true;
+        };
+        for (int t = 0; t < T_; t++) {
+            for (int l = 0; l < L; l++) {
+                const fewha_layer &ly = P.geom.layers[l];
+                for (int ax = 0; ax < 2; ax++) {
+                    const size_t b = (((size_t)t * L + l) * 2 + ax) * m;
+                    const double th = ax == 0 ? d->dir_x[t] : d->dir_y[t];
+                    if (!table(th * ly.h, P.lay_d[l], 0.5 * ly.n, ly.n, &lk[b], &lw[b])) return FEWHA_ERR_GEOMETRY;
+                }
+            }
+            for (int k = 0; k < D; k++)
+                for (int ax = 0; ax < 2; ax++) {
+                    const size_t b = (((size_t)t * D + k) * 2 + ax) * m;
+                    const double th = ax == 0 ? d->dir_x[t] : d->dir_y[t];
+                    if (!table(th * d->dm_h[k], d->dm_pitch[k], 0.5 * (d->dm_n[k] - 1), d->dm_n[k], &dk[b], &dw[b]))
+                        return FEWHA_ERR_GEOMETRY;
+                    const size_t rb = (((size_t)t * D + k) * 2 + ax) * nmax;
+                    for (int i = 0; i < d->dm_n[k]; i++) {
+                        int lo = m, hi = 0;
+                        for (int j = 0; j < m; j++)
+                            if (dk[b + j] == i || dk[b + j] + 1 == i) {
+                                lo = std::min(lo, j);
+                                hi = std::max(hi, j + 1);
+                            }
+                        if (lo >= hi) lo = hi = 0;
+                        alo[rb + i] = lo;
+                        ahi[rb + i] = hi;
+                    }
+                }
+        }
+        auto *pl = new McaoPlan();
+        McaoArgs<T, S> &M = pl->M;
+        M.L = L;
+        M.D = D;
+        M.ndir = T_;
+        M.m = m;
+        M.nmax = nmax;
+        for (int l = 0; l < L; l++) {
+            M.lay_off[l] = P.lay_off[l];
+            M.lay_n[l] = P.geom.layers[l].n;
+        }
+        M.dm_off[0] = 0;
+        for (int k = 0; k < D; k++) {
+            M.dm_n[k] = d->dm_n[k];
+            M.dm_off[k + 1] = M.dm_off[k] + (long)d->dm_n[k] * d->dm_n[k];
+        }
+        const long na = M.dm_off[D];
+        int st = FEWHA_OK;
+        auto put_i = [&](const std::vector<int> &v, const int **dst) {
+            int *dd = nullptr;
+            if (upload(v, &dd)) return false;
+            pl->owned.push_back(dd);
+            *dst = dd;
+            return true;
+        };
+        auto put_t = [&](const std::vector<T> &v, const T **dst) {
+            T *dd = nullptr;
+            if (upload(v, &dd)) return false;
+            pl->owned.push_back(dd);
+            *dst = dd;
+            return true;
+        };
+        auto make = [&](size_t bytes, void **dst) {
+            if (cudaMalloc(dst, bytes) != cudaSuccess) return false;
+            pl->owned.push_back(*dst);
+            return true;
+        };
+        const int *c_lk, *c_dk, *c_alo, *c_ahi;
+        const T *c_lw, *c_dw;
+        void *r, *p, *q, *y, *part, *rec;
+        if (!put_i(lk, &c_lk) || !put_t(lw, &c_lw) || !put_i(dk, &c_dk) || !put_t(dw, &c_dw) ||
+            !put_i(alo, &c_alo) || !put_i(ahi, &c_ahi) || !make(na * sizeof(T), &r) || !make(na * sizeof(T), &p) ||
+            !make(na * sizeof(T), &q) || !make((size_t)T_ * m * m * sizeof(T), &y) ||
+            !make(2 * kMaxCtas * sizeof(double), &part) || !make(sizeof(Record), &rec))
+            st = FEWHA_ERR_CUDA;
+        if (st) {
+            delete pl;
+            return st;
+        }
+        M.lk = c_lk;
+        M.lw = c_lw;
+        M.dk = c_dk;
+        M.dw = c_dw;
+        M.alo = c_alo;
+        M.ahi = c_ahi;
+        M.r = static_cast<T *>(r);
+        M.p = static_cast<T *>(p);
+        M.q = static_cast<T *>(q);
+        M.y = static_cast<T *>(y);
+        M.part = static_cast<double *>(part);
+        M.rec = static_cast<Record *>(rec);
+        *out = pl;
+        *n_act = na;
+        return FEWHA_OK;
+    }
+
+    int mcao_fit(void *plan, const void *c, void *a, int iters, cudaStream_t s) override
+    {
+        if (iters < 0 || iters > FEWHA_MAX_ITER) return FEWHA_ERR_ARG;
+        auto *pl = static_cast<McaoPlan *>(plan);
+        Args<T, S> A = base;
+        A.x = static_cast<const T *>(c);
+        CK(cudaMemsetAsync(A.rec, 0, offsetof(Record, rz), s));
+        k_apply_idwt<T, S><<<ncta, kThreads, smem, s>>>(A);  // nodal = W^{-1} c
+        McaoArgs<T, S> M = pl->M;
+        M.nodal = base.nodal;
+        M.a = static_cast<T *>(a);
+        M.iters = iters;
+        M.timeout_ns = base.timeout_ns;
+        CK(cudaMemsetAsync(M.rec, 0, sizeof(Record), s));
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(ncta);
+        cfg.blockDim = dim3(kThreads);
+        cfg.dynamicSmemBytes = 0;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        CK(cudaLaunchKernelEx(&cfg, k_mcao_fit<T, S>, M));
+        return launch_check();
+    }
+
+    void mcao_destroy(void *plan) override { delete static_cast<McaoPlan *>(plan); }
 
     int pol_slopes(const void *s_in, const void *a, void *s_out, cudaStream_t s) override
     {

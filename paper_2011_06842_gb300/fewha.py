@@ -113,6 +113,14 @@ def load_library(path=LIB_PATH):
     lib.fewha_batch_launch.restype = C.c_int
     lib.fewha_batch_destroy.argtypes = [vp]
     lib.fewha_batch_destroy.restype = None
+    lib.fewha_mcao_create.argtypes = [vp, vp, C.POINTER(vp)]
+    lib.fewha_mcao_create.restype = C.c_int
+    lib.fewha_mcao_n_actuators.argtypes = [vp]
+    lib.fewha_mcao_n_actuators.restype = C.c_long
+    lib.fewha_mcao_fit.argtypes = [vp, vp, vp, C.c_int, vp]
+    lib.fewha_mcao_fit.restype = C.c_int
+    lib.fewha_mcao_destroy.argtypes = [vp]
+    lib.fewha_mcao_destroy.restype = None
     lib.fewha_n_actuators.argtypes = [vp]
     lib.fewha_n_actuators.restype = C.c_long
     lib.fewha_fit.argtypes = [vp, vp, vp, vp]
@@ -161,7 +169,8 @@ def exported_symbols():
             "fewha_apply_op_multi", "fewha_conv3x3_fwd", "fewha_conv3x3_bwd_data",
             "fewha_conv3x3_wgrad_workspace", "fewha_conv3x3_bwd_weight", "fewha_relu_bwd",
             "fewha_mse_grad", "fewha_adam_step", "fewha_scale", "fewha_learned_targets",
-            "fewha_deflate_warm_start"]
+            "fewha_deflate_warm_start", "fewha_mcao_create", "fewha_mcao_n_actuators", "fewha_mcao_fit",
+            "fewha_mcao_destroy"]
 
 
 def make_geometry(geom, noise_w, precision="f64", tile=0, grid=0) -> GEOMETRY:
@@ -406,6 +415,55 @@ class Fewha:
         st = STATS.from_buffer_copy(raw)
         return {"status": st.status, "iterations": st.iterations, "rel_res": st.rel_res,
                 "bnorm": st.bnorm, "rz": st.rz, "basis_count": st.basis_count}
+
+
+class MCAO_DESC(C.Structure):
+    _fields_ = [("n_dm", C.c_int), ("dm_n", C.c_int * 4), ("dm_pitch", C.c_double * 4), ("dm_h", C.c_double * 4),
+                ("n_dir", C.c_int), ("dir_x", C.c_double * 16), ("dir_y", C.c_double * 16)]
+
+
+class McaoFit:
+    """MCAO fitting onto several mirrors (fewha_mcao_*): `dms` is a list of
+    (actuators per side, pitch [m], altitude [m]), `dirs` a list of fitting
+    directions (theta_x, theta_y) [rad].  fit(c, a, iters) runs `iters` CG
+    iterations on the normal equations from the start in `a` (overwritten)."""
+
+    def __init__(self, fewha, dms, dirs):
+        if not 1 <= len(dms) <= 4 or not 1 <= len(dirs) <= 16:
+            raise ValueError("1..4 mirrors and 1..16 directions")
+        self.f, self.lib = fewha, fewha.lib
+        d = MCAO_DESC()
+        d.n_dm = len(dms)
+        for i, (n, pitch, h) in enumerate(dms):
+            d.dm_n[i], d.dm_pitch[i], d.dm_h[i] = int(n), float(pitch), float(h)
+        d.n_dir = len(dirs)
+        for i, (tx, ty) in enumerate(dirs):
+            d.dir_x[i], d.dir_y[i] = float(tx), float(ty)
+        h = C.c_void_p()
+        fewha._check(self.lib.fewha_mcao_create(fewha._h, C.byref(d), C.byref(h)), "fewha_mcao_create")
+        self._h = h
+        self.n_actuators = self.lib.fewha_mcao_n_actuators(h)
+
+    def new_mirrors(self):
+        return self.f._torch.zeros(self.n_actuators, dtype=self.f.dtype, device=self.f.device)
+
+    def fit(self, c, a, iters=4):
+        f = self.f
+        f._check(self.lib.fewha_mcao_fit(self._h, f._vec(c, f.n, f.dtype, "c"),
+                                         f._vec(a, self.n_actuators, f.dtype, "a"), int(iters),
+                                         _stream_ptr(f._torch)), "fewha_mcao_fit")
+        return a
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self.lib.fewha_mcao_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class FewhaBatch:
