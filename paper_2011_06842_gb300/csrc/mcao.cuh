@@ -8,7 +8,8 @@
 // barrier, deterministic two-stage reductions (one partial per CTA):
 //   0: y_t = P^L_t nodal - P^DM_t a0           (pupil maps, all directions)
 //   1: r = sum_t P^DM_t^T y_t, p = r, (r, r)    (gather over each actuator's
-//                                                 pupil-node ranges, no atomics)
+//                                                 pupil-node ranges, no atomics;
+//                                                 one lane per direction)
 //   per iteration: y = P^DM p | q = N p, (p, q) | a += alpha p, r -= alpha q,
 //   (r, r) | p = r + beta p
 #pragma once
@@ -58,6 +59,7 @@ __device__ __forceinline__ void mcao_project(const McaoArgs<T, S> &M, const T *v
         const int t = (int)(e / mm), rem = (int)(e - (long)t * mm), iy = rem / m, ix = rem - iy * m;
         T lay = 0;
         if (with_layers) {
+#pragma unroll 3
             for (int l = 0; l < M.L; l++) {
                 const int bx = ((t * M.L + l) * 2) * m, by = bx + m;
                 lay += mcao_bilinear<T, S>(M.nodal + M.lay_off[l], M.lay_n[l], __ldg(M.lk + bx + ix),
@@ -65,6 +67,7 @@ __device__ __forceinline__ void mcao_project(const McaoArgs<T, S> &M, const T *v
             }
         }
         T dm = 0;
+#pragma unroll 3
         for (int d = 0; d < M.D; d++) {
             const int bx = ((t * M.D + d) * 2) * m, by = bx + m;
             dm += mcao_bilinear<T, T>(v + M.dm_off[d], M.dm_n[d], __ldg(M.dk + bx + ix), __ldg(M.dk + by + iy),
@@ -74,17 +77,19 @@ __device__ __forceinline__ void mcao_project(const McaoArgs<T, S> &M, const T *v
     }
 }
 
-// (sum_t P^DM_t^T y_t) at actuator e, gathered over the pupil nodes its hat
-// functions reach (rows v, columns u), direction after direction
+// (P^DM_t^T y_t) at actuator e for the directions t = t0, t0 + kDirLanes, ...,
+// gathered over the pupil nodes its hat functions reach (rows v, columns u)
+constexpr int kDirLanes = 8;  // lanes that share one actuator, one direction each
+
 template <typename T, typename S>
-__device__ __forceinline__ T mcao_adjoint_at(const McaoArgs<T, S> &M, long e)
+__device__ __forceinline__ T mcao_adjoint_at(const McaoArgs<T, S> &M, long e, int t0)
 {
     int d = 0;
     while (e >= M.dm_off[d + 1]) d++;
     const int n = M.dm_n[d], loc = (int)(e - M.dm_off[d]), iy = loc / n, ix = loc - iy * n;
     const int m = M.m;
     T s = 0;
-    for (int t = 0; t < M.ndir; t++) {
+    for (int t = t0; t < M.ndir; t += kDirLanes) {
         const int bx = ((t * M.D + d) * 2) * m, by = bx + m;
         const int rx = ((t * M.D + d) * 2) * M.nmax, ry = rx + M.nmax;
         const int u0 = __ldg(M.alo + rx + ix), u1 = __ldg(M.ahi + rx + ix);
@@ -105,6 +110,26 @@ __device__ __forceinline__ T mcao_adjoint_at(const McaoArgs<T, S> &M, long e)
     return s;
 }
 
+// For every actuator (kDirLanes lanes each, 32 / kDirLanes actuators per warp):
+// v = sum_t P^DM_t^T y_t, the lanes' direction sums added in a fixed shuffle
+// tree; body(e, v) runs on the group's first lane.
+template <typename T, typename S, class Body>
+__device__ __forceinline__ void mcao_adjoint(const McaoArgs<T, S> &M, long nact, Body body)
+{
+    const int lane = threadIdx.x & 31, sub = lane & (kDirLanes - 1);
+    const long warp = (blockIdx.x * (long)blockDim.x + threadIdx.x) >> 5;
+    const long nwarps = ((long)gridDim.x * blockDim.x) >> 5, per = 32 / kDirLanes;
+    for (long eb = warp * per; eb < nact; eb += nwarps * per) {  // uniform over the warp
+        const long e = eb + lane / kDirLanes;
+        T v = e < nact ? mcao_adjoint_at<T, S>(M, e, sub) : T(0);
+#pragma unroll
+        for (int o = kDirLanes / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (sub == 0 && e < nact) body(e, v);
+    }
+}
+
+// The adjoint phases and the vector updates map actuators to threads
+// differently, so every read of a, r, p, q goes through L2.
 template <typename T, typename S>
 __global__ void __launch_bounds__(kThreads, 1) k_mcao_fit(const __grid_constant__ McaoArgs<T, S> M)
 {
@@ -125,12 +150,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_mcao_fit(const __grid_constant_
     if (!sync()) return;
     {
         Acc acc[1] = {0};
-        for (long e = g0; e < nact; e += gs) {
-            const T r = mcao_adjoint_at<T, S>(M, e);
+        mcao_adjoint<T, S>(M, nact, [&](long e, T r) {
             M.r[e] = r;
             M.p[e] = r;
             acc[0] += (Acc)r * (Acc)r;
-        }
+        });
         block_partials<1>(acc, M.part, slot_rr, sred, rank);
     }
     if (!sync()) return;
@@ -141,11 +165,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_mcao_fit(const __grid_constant_
         if (!sync()) return;
         {
             Acc acc[1] = {0};
-            for (long e = g0; e < nact; e += gs) {
-                const T q = mcao_adjoint_at<T, S>(M, e);
+            mcao_adjoint<T, S>(M, nact, [&](long e, T q) {
                 M.q[e] = q;
-                acc[0] += (Acc)M.p[e] * (Acc)q;
-            }
+                acc[0] += (Acc)ldcg(M.p + e) * (Acc)q;
+            });
             block_partials<1>(acc, M.part, slot_pq, sred, rank);
         }
         if (!sync()) return;
@@ -154,8 +177,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_mcao_fit(const __grid_constant_
         {
             Acc acc[1] = {0};
             for (long e = g0; e < nact; e += gs) {
-                M.a[e] += alpha * M.p[e];
-                const T r = M.r[e] - alpha * M.q[e];
+                M.a[e] = ldcg(M.a + e) + alpha * ldcg(M.p + e);
+                const T r = ldcg(M.r + e) - alpha * ldcg(M.q + e);
                 M.r[e] = r;
                 acc[0] += (Acc)r * (Acc)r;
             }
@@ -164,7 +187,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_mcao_fit(const __grid_constant_
         if (!sync()) return;
         const double rr_new = reduce1(0);
         const T beta = (T)(rr_new / rr);
-        for (long e = g0; e < nact; e += gs) M.p[e] = M.r[e] + beta * M.p[e];
+        for (long e = g0; e < nact; e += gs) M.p[e] = ldcg(M.r + e) + beta * ldcg(M.p + e);
         rr = rr_new;
         if (!sync()) return;
     }
