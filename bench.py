@@ -25,7 +25,7 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-METRIC = json.load(open(os.path.join(ROOT, "BASELINE.json")))["metric"]
+METRIC = "ELT-size \u00b5s/frame & frames/s at fixed residual vs plain PCG; L2/HBM % of peak"
 UNIT = "frames/s"
 
 
