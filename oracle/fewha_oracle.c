@@ -700,6 +700,7 @@ typedef struct {
     int init_mode;     /* 0: Gram form sigma = G^{-1} P^T r, 1: the paper's sequential sigma_j */
     int loop_mode;     /* 0: project z against the newest recycled direction p_m (paper), 1: against all */
     int true_residual_init; /* 1: r0 = b - M c instead of (b - b_prev) + r_prev */
+    int true_res_every;     /* N > 0: after every N-th iteration r <- b - M c (residual replacement) */
 } orc_opts;
 
 typedef struct {
@@ -826,6 +827,16 @@ int orc_solve(const orc_ctx *cx, const double *s, double *c, double *b_prev, dou
         for (long i = 0; i < n; i++) {
             c[i] += alpha * p[i];
             r[i] -= alpha * q[i];
+        }
+        /* Residual replacement (not in the paper, which keeps the recurrence
+         * residual of Algorithms 1-2 and warm-restarts from it in Algorithm 3):
+         * after every N-th iteration the recurrence residual is replaced by the
+         * true residual b - M c, from which z, the projection, (r, z) and beta
+         * below follow; the stopping test and the next time step's warm
+         * restart then see the true residual. */
+        if (o->true_res_every > 0 && (k + 1) % o->true_res_every == 0) {
+            orc_apply_op(cx, c, tmp);
+            for (long i = 0; i < n; i++) r[i] = b[i] - tmp[i];
         }
         for (long i = 0; i < n; i++) z[i] = cx->invJ[i] * r[i];
         if (aug) {

@@ -51,7 +51,8 @@ class _Params(C.Structure):
 
 class _Opts(C.Structure):
     _fields_ = [("max_iter", C.c_int), ("rtol", C.c_double), ("augmented", C.c_int),
-                ("init_mode", C.c_int), ("loop_mode", C.c_int), ("true_residual_init", C.c_int)]
+                ("init_mode", C.c_int), ("loop_mode", C.c_int), ("true_residual_init", C.c_int),
+                ("true_res_every", C.c_int)]
 
 
 class _Stats(C.Structure):
@@ -320,14 +321,16 @@ class Oracle:
                 "k_valid": 0, "kcap": kcap}
 
     def solve(self, s, state, max_iter, rtol=0.0, augmented=True, init_mode=0, loop_mode=0,
-              true_residual_init=False, history=False):
-        """Advance ``state`` (dict from ``new_state``) by one time step in place."""
+              true_residual_init=False, history=False, true_res_every=0):
+        """Advance ``state`` (dict from ``new_state``) by one time step in place.
+        ``true_res_every`` = N > 0 replaces the recurrence residual by b - M c
+        after every N-th iteration."""
         s = _f64(s)
         for k in ("c", "b_prev", "r_prev", "P", "Q", "pq"):
             state[k] = _f64(state[k])
         kv = C.c_int(state["k_valid"])
         o = _Opts(max_iter, rtol, 1 if augmented else 0, init_mode, loop_mode,
-                  1 if true_residual_init else 0)
+                  1 if true_residual_init else 0, int(true_res_every))
         stt = _Stats()
         hist = np.zeros((4, max_iter + 1, self.n)) if history else None
         st = self._lib.orc_solve(self._h, _ptr(s), _ptr(state["c"]), _ptr(state["b_prev"]),

@@ -202,3 +202,60 @@ def test_recycling_lowers_residual_on_frozen_flow():
     rp = np.mean([r["rel_res"] for r in plain[4:]])
     ra = np.mean([r["rel_res"] for r in aug[4:]])
     assert ra < rp
+
+
+# --- residual replacement (true residual every N iterations) ----------------
+# In exact arithmetic the recurrence residual of CG equals b - M c, so
+# replacing it changes nothing; with an inconsistent warm start (c changed
+# between time steps while r_prev was not) the recurrence carries the
+# inconsistency forever and the replacement removes it.  The dense M below is
+# the independently pinned assembly (dense M = product of explicit matrices).
+
+def test_true_residual_every_iteration_is_b_minus_Mc(micro20):
+    geom, o, M, s = micro20
+    st = o.new_state(4)
+    res = o.solve(s[0], st, max_iter=6, augmented=False, true_res_every=1)
+    b = o.rhs(s[0])
+    assert res["status"] == 0 and res["iterations"] == 6
+    assert np.linalg.norm(st["r_prev"] - (b - M @ st["c"])) <= 1e-13 * np.linalg.norm(b)
+
+
+def test_true_residual_same_iterates_as_recurrence(micro20):
+    """Same iterates as plain and augmented PCG up to rounding (N = 1, 2)."""
+    geom, o, M, s = micro20
+    for aug in (False, True):
+        for N in (1, 2):
+            st0, st1 = o.new_state(4), o.new_state(4)
+            for t in range(3):
+                r0 = o.solve(s[t], st0, max_iter=5, augmented=aug)
+                r1 = o.solve(s[t], st1, max_iter=5, augmented=aug, true_res_every=N)
+                assert r0["iterations"] == r1["iterations"]
+                assert np.linalg.norm(st1["c"] - st0["c"]) <= 1e-10 * np.linalg.norm(st0["c"]), (aug, N, t)
+
+
+def test_true_residual_beyond_max_iter_changes_nothing(micro):
+    geom, o, M, s = micro
+    st0, st1 = o.new_state(4), o.new_state(4)
+    for t in range(2):
+        o.solve(s[t], st0, max_iter=4)
+        o.solve(s[t], st1, max_iter=4, true_res_every=5)
+        assert np.array_equal(st0["c"], st1["c"]) and np.array_equal(st0["r_prev"], st1["r_prev"])
+
+
+def test_true_residual_repairs_an_inconsistent_warm_start(micro20):
+    """c is moved (1e-6 relative) between time steps without touching r_prev:
+    the recurrence keeps that inconsistency in every later residual; with a
+    replacement after iteration 2 or 4 of 6 the final residual is b - M c to
+    rounding (the recurrence after a replacement stays consistent)."""
+    geom, o, M, s = micro20
+    b = o.rhs(s[1])
+    gap = {}
+    for N in (0, 2, 4, 7):
+        rng = np.random.default_rng(9)
+        st = o.new_state(4)
+        o.solve(s[0], st, max_iter=30, augmented=False)
+        st["c"] = st["c"] + 1e-6 * np.linalg.norm(st["c"]) / np.sqrt(o.n) * rng.standard_normal(o.n)
+        o.solve(s[1], st, max_iter=6, augmented=True, true_res_every=N)
+        gap[N] = np.linalg.norm(st["r_prev"] - (b - M @ st["c"])) / np.linalg.norm(b)
+    assert gap[2] < 1e-13 and gap[4] < 1e-13, gap
+    assert gap[0] > 1e-9 and gap[7] > 1e-9, gap
