@@ -119,7 +119,15 @@ typedef struct {
     int augmented;        /* 0: PCG (Algorithm 1); 1: augmented PCG (Algorithm 2) */
     int recycle_mode;     /* FEWHA_RECYCLE_LAST (paper) or FEWHA_RECYCLE_ALL */
     int launch_mode;      /* FEWHA_LAUNCH_PERSISTENT (one kernel) or FEWHA_LAUNCH_PHASES */
-    int reserved;
+    /* N > 0: residual replacement.  After every N-th iteration (the last one
+     * included) the recurrence residual r is replaced by the true residual
+     * b - M c, computed with one more operator application whose
+     * intermediates are stored in the working precision (FP32 also for
+     * FEWHA_BF16S); z = J^{-1} r, the projection, (r, z) and beta of the next
+     * iteration, the stopping test and the next time step's warm restart
+     * then see the true residual.  0 = off (the paper: Algorithms 1-3 keep
+     * the recurrence residual).  0..FEWHA_MAX_ITER. */
+    int true_res_every;
 } fewha_solve_opts;
 
 /* Written on the device at the end of fewha_solve. */
@@ -139,6 +147,20 @@ typedef struct {
  * entries of M).  Uses the current CUDA device.  Blocking. */
 int fewha_create(const fewha_geometry *geom, void **handle_out);
 
+/* Noise weights C_eta^{-1} (Sec. 3, Eq. M: the diagonal of C_eta^{-1} is
+ * weight[g] = 1/sigma_g^2 on the lit subapertures of guide star g, 0
+ * elsewhere), for g = 0..n_gs-1: finite and >= 0 (FEWHA_ERR_ARG otherwise).
+ * Replaces the weights given at fewha_create in the operator M and the
+ * right-hand side of every later call.  The modified Jacobi preconditioner J
+ * (Sec. 4) depends on them through its data term: with refresh_precond != 0
+ * it is rebuilt from sampled diagonal entries of the new M (the same
+ * FP64 sampling as fewha_create, several hundred operator applications);
+ * with 0 it keeps the values computed for the earlier weights (still a valid
+ * SPD preconditioner, only less well matched).  Waits for the device to be
+ * idle before it writes the tables and again at the end (blocking): call it
+ * between time steps, never while a solve on this handle is in flight. */
+int fewha_set_noise(void *handle, const double *weight, int refresh_precond);
+
 /* Frees the handle and its device memory (synchronises the device). */
 void fewha_destroy(void *handle);
 
@@ -146,6 +168,27 @@ void fewha_destroy(void *handle);
 long fewha_n_unknowns(const void *handle);
 long fewha_n_slopes(const void *handle);
 double fewha_layer_spacing(const void *handle, int layer);
+
+/* Launch shape of the handle's single-instance kernels (working precision),
+ * as chosen at creation for the current GPU: CTAs (one per SM unless the
+ * geometry's `grid` fixed them), threads per CTA, dynamic shared memory, and
+ * which forms of the operator phases run: split_levels = 1 when the finest
+ * wavelet level is tiled over all CTAs and only the coarser levels stay on
+ * one CTA per layer (at least twice as many CTAs as layers), 0 when each
+ * layer's CTA runs every level; staged_tables = 1 when the P_g^T gather
+ * stages its interpolation-weight tables in shared memory beside the adjoint
+ * wavefront rows, 0 when it reads them from global memory; the WFS tile
+ * shape; the P_g^T work items (bands of layer rows) and the adjoint wavefront
+ * rows staged per pass.  Host only, no device work.  The paper has no
+ * counterpart. */
+typedef struct {
+    int ctas, threads;
+    long smem_bytes;
+    int split_levels, staged_tables;
+    int wfs_tile_y, wfs_tile_x;
+    int pt_bands, pt_rows_chunk;
+} fewha_launch_info;
+int fewha_get_launch_info(const void *handle, fewha_launch_info *out);
 
 /* Copies the diagonal of alpha*D (Sec. 3) or of J^{-1} (Sec. 4) to host memory (n doubles). */
 int fewha_get_prior(const void *handle, double *alpha_d_host);
@@ -360,15 +403,20 @@ void fewha_mcao_destroy(void *mcao);
  * still created (and its constant tables allocated) once, beforehand, by
  * fewha_create.
  * The intermediate buffers live in one statically reserved device array of
- * FEWHA_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds until
- * the process exits.  Problems whose buffers do not fit are rejected with
- * FEWHA_ERR_SCRATCH (an ELT-size FP64 operator, n = 98304 with 6 sensors of
- * 84 x 84 subapertures, needs about 4.8 MB).
- * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current.  All calls share the one
- * array, which keeps the last call's contents: calls that overlap on the GPU
- * (different streams, different handles on the same device) race and must be
- * ordered by the caller.  The paper has no counterpart; this is a deployment aid.
+ * FEWHA_NOALLOC_SCRATCH_BYTES per GPU, held until the process exits.  With
+ * CUDA's lazy module loading (the default) the array is reserved on a GPU
+ * when the first handle is created there: fewha_create looks up the array's
+ * device address (cudaGetSymbolAddress) with the handle's device current,
+ * which loads the module holding it, so no later call of this entry point
+ * loads anything.  Every call looks the address up again on the current
+ * device (no cached pointer outlives a device reset); the current device must
+ * be the handle's (FEWHA_ERR_ARG otherwise).  Problems whose buffers do not
+ * fit are rejected with FEWHA_ERR_SCRATCH (an ELT-size FP64 operator, n =
+ * 98304 with 6 sensors of 84 x 84 subapertures, needs about 4.8 MB).
+ * All calls share the one array, which keeps the last call's contents: calls
+ * that overlap on the GPU (different streams, different handles on the same
+ * device) race and must be ordered by the caller.  The paper has no
+ * counterpart; this is a deployment aid.
  * x, y: device vectors of length n, 16-byte aligned, not overlapping. */
 #define FEWHA_NOALLOC_SCRATCH_BYTES (8u << 20)
 int fewha_apply_op_noalloc(void *handle, const void *x, void *y, cudaStream_t stream);

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <memory>
 #include <new>
@@ -25,6 +26,7 @@ struct Handle {
 static bool aligned16(const void *p) { return ((size_t)p & 15) == 0; }
 
 ImplBase *handle_impl(void *handle) { return handle ? static_cast<Handle *>(handle)->w() : nullptr; }
+int handle_device(const void *handle) { return handle ? static_cast<const Handle *>(handle)->device : -1; }
 
 // A batch: many instances (handles of one precision on one device) run by one
 // cooperative launch, each by its own group of CTAs.
@@ -36,6 +38,7 @@ struct Batch {
     void *d_args = nullptr;
     void *d_bound = nullptr;  // argument table of fewha_batch_bind (fixed buffers, graph replay)
     bool bound = false;
+    int bound_true_res = 0;  // the bound options ask for the residual replacement
     int *d_map = nullptr;                 // [nrounds][total] instance of each CTA, -1 idle
     Record *d_brec = nullptr;             // barrier between rounds
     static constexpr int kRing = 4;  // pinned staging copies of the argument table
@@ -128,6 +131,10 @@ int fewha_create(const fewha_geometry *geom, void **out)
     if (st == FEWHA_OK) st = build_precond(*h, invJ);
     if (st == FEWHA_OK) st = h->f64->set_invJ(invJ);
     if (st == FEWHA_OK && h->work) st = h->work->set_invJ(invJ);
+    // loads the module of fewha_apply_op_noalloc's static scratch on this
+    // device now, while creating a handle may allocate (lazy module loading
+    // would otherwise reserve it at the first allocation-free call)
+    if (st == FEWHA_OK) st = noalloc_prepare();
     if (st == FEWHA_OK && cudaDeviceSynchronize() != cudaSuccess) st = FEWHA_ERR_CUDA;
     if (st != FEWHA_OK) {
         delete h;
@@ -135,6 +142,26 @@ int fewha_create(const fewha_geometry *geom, void **out)
     }
     *out = h;
     return FEWHA_OK;
+}
+
+int fewha_set_noise(void *handle, const double *weight, int refresh_precond)
+{
+    if (!handle || !weight) return FEWHA_ERR_ARG;
+    Handle *h = static_cast<Handle *>(handle);
+    for (int g = 0; g < h->plan.G; g++)
+        if (!std::isfinite(weight[g]) || !(weight[g] >= 0.0)) return FEWHA_ERR_ARG;
+    if (cudaSetDevice(h->device) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) return FEWHA_ERR_CUDA;
+    for (int g = 0; g < h->plan.G; g++) h->plan.geom.gs[g].weight = weight[g];
+    int st = h->f64->set_weights();
+    if (st == FEWHA_OK && h->work) st = h->work->set_weights();
+    if (st == FEWHA_OK && refresh_precond) {
+        std::vector<double> invJ;
+        st = build_precond(*h, invJ);
+        if (st == FEWHA_OK) st = h->f64->set_invJ(invJ);
+        if (st == FEWHA_OK && h->work) st = h->work->set_invJ(invJ);
+    }
+    if (st == FEWHA_OK && cudaDeviceSynchronize() != cudaSuccess) st = FEWHA_ERR_CUDA;
+    return st;
 }
 
 void fewha_destroy(void *handle)
@@ -161,6 +188,14 @@ double fewha_layer_spacing(const void *handle, int layer)
     if (!handle) return -1.0;
     const Plan &p = static_cast<const Handle *>(handle)->plan;
     return (layer >= 0 && layer < p.L) ? p.lay_d[layer] : -1.0;
+}
+
+int fewha_get_launch_info(const void *handle, fewha_launch_info *out)
+{
+    if (!handle || !out) return FEWHA_ERR_ARG;
+    const Handle *h = static_cast<const Handle *>(handle);
+    (h->work ? h->work.get() : h->f64.get())->launch_info(out);
+    return FEWHA_OK;
 }
 
 int fewha_get_prior(const void *handle, double *out)
@@ -284,6 +319,7 @@ int fewha_solve(void *handle, const void *s, void *c, const fewha_state *st, con
         return FEWHA_ERR_ARG;
     if (st->k_cap < 1 || st->k_cap > FEWHA_MAX_K) return FEWHA_ERR_ARG;
     if (o->max_iter < 1 || o->max_iter > FEWHA_MAX_ITER || !(o->rtol >= 0)) return FEWHA_ERR_ARG;
+    if (o->true_res_every < 0 || o->true_res_every > FEWHA_MAX_ITER) return FEWHA_ERR_ARG;
     if (o->launch_mode != FEWHA_LAUNCH_PERSISTENT && o->launch_mode != FEWHA_LAUNCH_PHASES) return FEWHA_ERR_ARG;
     if (o->recycle_mode != FEWHA_RECYCLE_LAST && o->recycle_mode != FEWHA_RECYCLE_ALL) return FEWHA_ERR_ARG;
     return static_cast<Handle *>(handle)->w()->solve(s, c, st, o, stats, stream);
@@ -397,6 +433,7 @@ int fewha_batch_solve(void *batch, const void *const *slopes, void *const *c, co
     if (!batch || !slopes || !c || !states || !opts) return FEWHA_ERR_ARG;
     Batch *b = static_cast<Batch *>(batch);
     if (opts->max_iter < 1 || opts->max_iter > FEWHA_MAX_ITER || !(opts->rtol >= 0)) return FEWHA_ERR_ARG;
+    if (opts->true_res_every < 0 || opts->true_res_every > FEWHA_MAX_ITER) return FEWHA_ERR_ARG;
     if (opts->recycle_mode != FEWHA_RECYCLE_LAST && opts->recycle_mode != FEWHA_RECYCLE_ALL) return FEWHA_ERR_ARG;
     const int slot = b->next;
     b->next = (b->next + 1) % Batch::kRing;
@@ -417,7 +454,8 @@ int fewha_batch_solve(void *batch, const void *const *slopes, void *const *c, co
     if (cudaMemcpyAsync(b->d_args, h, b->asz * b->n, cudaMemcpyHostToDevice, stream) != cudaSuccess)
         return FEWHA_ERR_CUDA;
     if (cudaEventRecord(b->ev[slot], stream) != cudaSuccess) return FEWHA_ERR_CUDA;
-    return b->impl[0]->launch_batched(b->d_args, b->d_map, b->n, b->total, b->smem, b->nrounds, b->d_brec, stream);
+    return b->impl[0]->launch_batched(b->d_args, b->d_map, b->n, b->total, b->smem, b->nrounds, b->d_brec,
+                                      opts->true_res_every > 0, stream);
 }
 
 int fewha_batch_bind(void *batch, const void *const *slopes, void *const *c, const fewha_state *states,
@@ -426,6 +464,7 @@ int fewha_batch_bind(void *batch, const void *const *slopes, void *const *c, con
     if (!batch || !slopes || !c || !states || !opts) return FEWHA_ERR_ARG;
     Batch *b = static_cast<Batch *>(batch);
     if (opts->max_iter < 1 || opts->max_iter > FEWHA_MAX_ITER || !(opts->rtol >= 0)) return FEWHA_ERR_ARG;
+    if (opts->true_res_every < 0 || opts->true_res_every > FEWHA_MAX_ITER) return FEWHA_ERR_ARG;
     if (opts->recycle_mode != FEWHA_RECYCLE_LAST && opts->recycle_mode != FEWHA_RECYCLE_ALL) return FEWHA_ERR_ARG;
     std::vector<unsigned char> h(b->asz * b->n);
     for (int i = 0; i < b->n; i++) {
@@ -444,6 +483,7 @@ int fewha_batch_bind(void *batch, const void *const *slopes, void *const *c, con
     if (!b->d_bound && cudaMalloc(&b->d_bound, b->asz * b->n) != cudaSuccess) return FEWHA_ERR_NOMEM;
     if (cudaMemcpy(b->d_bound, h.data(), b->asz * b->n, cudaMemcpyHostToDevice) != cudaSuccess) return FEWHA_ERR_CUDA;
     b->bound = true;
+    b->bound_true_res = opts->true_res_every > 0;
     return FEWHA_OK;
 }
 
@@ -453,7 +493,7 @@ int fewha_batch_launch(void *batch, cudaStream_t stream)
     Batch *b = static_cast<Batch *>(batch);
     if (!b->bound) return FEWHA_ERR_ARG;
     return b->impl[0]->launch_batched(b->d_bound, b->d_map, b->n, b->total, b->smem, b->nrounds, b->d_brec,
-                                      stream);
+                                      b->bound_true_res, stream);
 }
 
 void fewha_batch_destroy(void *batch)

@@ -123,6 +123,10 @@ struct __align__(16) Args {
     T *u;            // [n]  P^T psi (layer nodal adjoint)
     T *wq;           // [n]  W^{-T} u / delta (operator output before + alpha D p)
     T *ll;           // [sum (n_l/2)^2] level-1 approximation of each layer (split transforms)
+    // working-precision (T) buffers of the residual replacement's operator
+    // application: the nodal layers and adjoint wavefronts are stored in T
+    // there even when S is narrower (== nodal / psi when S is T)
+    T *nodal_t, *psi_t;
     const T *x;      // apply: input
     T *y;            // apply / rhs: output
     const S *slopes; // rhs / solve: measured slopes
@@ -133,6 +137,7 @@ struct __align__(16) Args {
     int *meta;
     int kcap;
     int max_iter, augmented, recycle_all;
+    int true_res_every;  // N > 0: r <- b - M c after every N-th iteration (residual replacement)
     double rtol;
     fewha_stats *stats;
     double *part;    // kSlots * kMaxCtas

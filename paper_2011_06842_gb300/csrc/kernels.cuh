@@ -8,6 +8,7 @@
 #include <utility>
 #include <cstddef>
 #include <cstring>
+#include <type_traits>
 #include <vector>
 
 #include "mcao.cuh"
@@ -309,6 +310,56 @@ __global__ void __launch_bounds__(kThreads, 1) k_D2E(const __grid_constant__ Arg
     phase_D2E<T, S>(A, b, k, dyn_smem<T>(), sred);
 }
 
+// residual replacement after iteration k (phases TU, TA2, TB, TC, TD1, TE)
+template <typename T, typename S>
+__global__ void __launch_bounds__(kThreads, 1) k_TU(const __grid_constant__ Args<T, S> Ap)
+{
+    FEWHA_PHASE_GUARD
+    (void)sc;
+    phase_TU<T>(*TrView<T, S>::get(A), dyn_smem<T>());
+}
+
+template <typename T, typename S>
+__global__ void __launch_bounds__(kThreads, 1) k_TA2(const __grid_constant__ Args<T, S> Ap)
+{
+    FEWHA_PHASE_GUARD
+    (void)sc;
+    const Args<T, T> &V = *TrView<T, S>::get(A);
+    phase_fine_synth<T, T>(V, V.c, dyn_smem<T>());
+}
+
+template <typename T, typename S>
+__global__ void __launch_bounds__(kThreads, 1) k_TB(const __grid_constant__ Args<T, S> Ap)
+{
+    FEWHA_PHASE_GUARD
+    (void)sc;
+    wfs_phase<T, T, false>(*TrView<T, S>::get(A), dyn_smem<T>());
+}
+
+template <typename T, typename S>
+__global__ void __launch_bounds__(kThreads, 1) k_TC(const __grid_constant__ Args<T, S> Ap)
+{
+    FEWHA_PHASE_GUARD
+    (void)sc;
+    band_gather<T, T>(*TrView<T, S>::get(A), dyn_smem<T>());
+}
+
+template <typename T, typename S>
+__global__ void __launch_bounds__(kThreads, 1) k_TD1(const __grid_constant__ Args<T, S> Ap)
+{
+    FEWHA_PHASE_GUARD
+    (void)sc;
+    phase_D1<T, T>(*TrView<T, S>::get(A), dyn_smem<T>());
+}
+
+template <typename T, typename S>
+__global__ void __launch_bounds__(kThreads, 1) k_TE(const __grid_constant__ Args<T, S> Ap, int k)
+{
+    FEWHA_PHASE_GUARD
+    (void)sc;
+    phase_TE<T>(*TrView<T, S>::get(A), b, k, dyn_smem<T>(), sred);
+}
+
 template <typename T, typename S>
 __global__ void __launch_bounds__(kThreads, 1) k_finish(const __grid_constant__ Args<T, S> Ap)
 {
@@ -321,8 +372,44 @@ __global__ void __launch_bounds__(kThreads, 1) k_finish(const __grid_constant__ 
     phase_finish<T, S>(A, b, K, sc);
 }
 
+// Residual replacement after iteration k inside the persistent kernel (phases
+// TU, TA2, TB, TC, TD1, TE, each followed by the group's barrier); false when a
+// barrier reports an error.  ti: trace slot of the next barrier.
+template <typename T>
+__device__ __forceinline__ bool true_residual_phases(const Args<T, T> &V, const Basis &b, int k, double *sred,
+                                                     int rank, int &ti)
+{
+    T *sm = dyn_smem<T>();
+    const bool split = split_levels(V);
+    auto sync = [&](int tag) -> bool {
+        unsigned long long *slot = (V.trace && ti < V.trace_cap) ? V.trace + 4 * ti : nullptr;
+        if (slot && rank == 0 && threadIdx.x == 0) slot[3] = (unsigned long long)tag;
+        ti++;
+        return grid_sync(V.rec, V.timeout_ns, V.ncta, rank, slot);
+    };
+    phase_TU<T>(V, sm);
+    if (!sync(20)) return false;
+    if (split) {
+        phase_fine_synth<T, T>(V, V.c, sm);
+        if (!sync(21)) return false;
+    }
+    wfs_phase<T, T, false>(V, sm);
+    if (!sync(22)) return false;
+    band_gather<T, T>(V, sm);
+    if (!sync(23)) return false;
+    if (split) {
+        phase_D1<T, T>(V, sm);
+        if (!sync(24)) return false;
+    }
+    phase_TE<T>(V, b, k, sm, sred);
+    return sync(25);
+}
+
 // --- the whole time step of one instance, run by its group of CTAs ----------
-template <typename T, typename S>
+// TR: the kernel variant with the residual replacement (fewha_solve_opts.
+// true_res_every > 0); the variant without it carries none of its code, so
+// the iteration's register allocation is the same as without the option.
+template <typename T, typename S, bool TR>
 __device__ void solve_body(const Args<T, S> &A, Scal &sc, double *sred)
 {
     T *sm = dyn_smem<T>();
@@ -340,6 +427,8 @@ __device__ void solve_body(const Args<T, S> &A, Scal &sc, double *sred)
     };
     int K = A.max_iter;
     const bool split = split_levels(A);  // uniform over the instance's CTAs
+    const Args<T, T> *V = nullptr;  // residual replacement's view of the arguments
+    if constexpr (TR) V = TrView<T, S>::get(A);
     trace_begin(A.trace != nullptr);
     do {
         wfs_phase<T, S, true>(A, sm);
@@ -385,6 +474,11 @@ __device__ void solve_body(const Args<T, S> &A, Scal &sc, double *sred)
             }
             phase_D2E<T, S>(A, b, k, sm, sred, &sc.alpha);
             if (!sync(15)) break;
+            // residual replacement: r = b - M c, then iteration k+1's scalars
+            // come from it
+            if constexpr (TR) {
+                if ((k + 1) % A.true_res_every == 0 && !true_residual_phases<T>(*V, b, k, sred, rank, ti)) break;
+            }
         }
     } while (0);
     // on a device-side error the stats carry the status; the other fields are
@@ -393,19 +487,19 @@ __device__ void solve_body(const Args<T, S> &A, Scal &sc, double *sred)
 }
 
 // One instance on the whole grid (cooperative launch).
-template <typename T, typename S>
+template <typename T, typename S, bool TR>
 __global__ void __launch_bounds__(kThreads, 1) k_solve_persistent(const __grid_constant__ Args<T, S> Ap)
 {
     __shared__ Scal sc;
     __shared__ double sred[kSred];
     __shared__ __align__(16) Args<T, S> A;
     args_to_smem(Ap, A);
-    solve_body<T, S>(A, sc, sred);
+    solve_body<T, S, TR>(A, sc, sred);
 }
 
 // Many instances in one cooperative launch: CTA c runs instance cta_inst[c]
 // with the group of CTAs [inst.cta0, inst.cta0 + inst.ncta).
-template <typename T, typename S>
+template <typename T, typename S, bool TR>
 __global__ void __launch_bounds__(kThreads, 1) k_solve_batched(const Args<T, S> *inst, const int *cta_inst,
                                                               int nrounds, int total, Record *brec,
                                                               unsigned long long timeout_ns)
@@ -420,7 +514,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_solve_batched(const Args<T, S> 
         const int i = cta_inst[r * total + blockIdx.x];
         if (i >= 0) {
             args_to_smem(inst[i], A);
-            solve_body<T, S>(A, sc, sred);
+            solve_body<T, S, TR>(A, sc, sred);
         }
         if (r + 1 < nrounds && !grid_sync(brec, timeout_ns, total, blockIdx.x)) return;
     }
@@ -480,6 +574,8 @@ struct ImplBase {
     virtual int solve(const void *sl, void *c, const fewha_state *st, const fewha_solve_opts *o,
                       fewha_stats *stats, cudaStream_t s) = 0;
     virtual int set_invJ(const std::vector<double> &invJ) = 0;
+    // C_eta^{-1}: weight of guide star g on its lit subapertures (plan.geom.gs[g].weight)
+    virtual int set_weights() = 0;
     virtual void set_trace(unsigned long long *buf, int cap) = 0;
     virtual void set_timeout(unsigned long long ns) = 0;
     // --- batched launch support (many instances, one cooperative kernel) ---
@@ -494,10 +590,11 @@ struct ImplBase {
     // CTAs that can be co-resident for the batched kernel with `smem` bytes
     virtual int batch_capacity(size_t smem, int *max_ctas) const = 0;
     virtual int launch_batched(const void *d_args, const int *d_map, int n, int total, size_t smem, int nrounds,
-                               Record *brec, cudaStream_t s) const = 0;
+                               Record *brec, int true_res, cudaStream_t s) const = 0;
     // y = M x with every scratch buffer carved from caller-provided device
     // memory (no allocation); FEWHA_ERR_SCRATCH if `bytes` is too small.
     virtual int apply_in_scratch(const void *x, void *y, void *scratch, size_t bytes, cudaStream_t s) = 0;
+    virtual void launch_info(fewha_launch_info *out) const = 0;
 };
 
 template <typename T, typename S>
@@ -613,13 +710,9 @@ struct Impl : ImplBase {
         int st;
         if ((st = up(P.fk, &G.fk)) || (st = up(P.alo, &G.alo)) || (st = up(P.ahi, &G.ahi))) return st;
         std::vector<T> fw(P.fw.begin(), P.fw.end());
-        std::vector<T> wm((size_t)P.G * P.ns * P.ns);
-        for (int g = 0; g < P.G; g++)
-            for (int i = 0; i < P.ns * P.ns; i++)
-                wm[(size_t)g * P.ns * P.ns + i] = P.mask[i] ? (T)P.geom.gs[g].weight : T(0);
         std::vector<T> ad(P.alpha_d.begin(), P.alpha_d.end());
         std::vector<T> one(P.n, T(1));
-        if ((st = up(fw, &G.fw)) || (st = up(wm, &G.wmask)) || (st = up(ad, &G.alpha_d)) ||
+        if ((st = up(fw, &G.fw)) || (st = up(weight_table(), &G.wmask)) || (st = up(ad, &G.alpha_d)) ||
             (st = up(one, &G.invJ)))
             return st;
         // P^T work items: bands of rows with band_rows * n_l <= kBandOutputs outputs;
@@ -693,6 +786,13 @@ struct Impl : ImplBase {
             (st = alloc((size_t)P.G * P.m * P.m, &base.psi)) || (st = alloc((size_t)P.n / 4 + 1, &base.ll)) ||
             (st = alloc((size_t)kSlots * kMaxCtas, &base.part)) || (st = alloc((size_t)1, &base.rec)))
             return st;
+        if constexpr (std::is_same<T, S>::value) {
+            base.nodal_t = base.nodal;
+            base.psi_t = base.psi;
+        } else {  // BF16 storage: the residual replacement stores its intermediates in T
+            if ((st = alloc((size_t)P.n, &base.nodal_t)) || (st = alloc((size_t)P.G * P.m * P.m, &base.psi_t)))
+                return st;
+        }
         // launch geometry: dynamic shared memory = max over phases
         int nmax = 0;
         for (int l = 0; l < P.L; l++) nmax = std::max(nmax, P.geom.layers[l].n);
@@ -821,15 +921,31 @@ struct Impl : ImplBase {
         CK(setattr((const void *)k_D1<T, S>));
         CK(setattr((const void *)k_D2E<T, S>));
         CK(setattr((const void *)k_finish<T, S>));
-        CK(setattr((const void *)k_solve_persistent<T, S>));
-        CK(cudaFuncSetAttribute((const void *)k_solve_batched<T, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        CK(setattr((const void *)k_TU<T, S>));
+        CK(setattr((const void *)k_TA2<T, S>));
+        CK(setattr((const void *)k_TB<T, S>));
+        CK(setattr((const void *)k_TC<T, S>));
+        CK(setattr((const void *)k_TD1<T, S>));
+        CK(setattr((const void *)k_TE<T, S>));
+        CK(setattr((const void *)k_solve_persistent<T, S, false>));
+        CK(setattr((const void *)k_solve_persistent<T, S, true>));
+        CK(cudaFuncSetAttribute((const void *)k_solve_batched<T, S, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                200 * 1024));
+        CK(cudaFuncSetAttribute((const void *)k_solve_batched<T, S, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 200 * 1024));
         for (const void *f : {(const void *)k_multi_idwt<T, S>, (const void *)k_multi_wfs<T, S>,
                               (const void *)k_multi_gather<T, S>, (const void *)k_multi_fdwt<T, S>})
             CK(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
         int per_sm = 0;
-        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve_persistent<T, S>, kThreads, smem));
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve_persistent<T, S, false>, kThreads, smem));
         if (per_sm < 1) return FEWHA_ERR_CUDA;
+        {
+            int per_sm_tr = 0;
+            CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_tr, k_solve_persistent<T, S, true>, kThreads,
+                                                             smem));
+            per_sm = std::min(per_sm, per_sm_tr);
+            if (per_sm < 1) return FEWHA_ERR_CUDA;
+        }
         ncta = grid > 0 ? grid : nsm;
         if (ncta > nsm * per_sm) ncta = nsm * per_sm;
         if (ncta > kMaxCtas) ncta = kMaxCtas;
@@ -840,11 +956,41 @@ struct Impl : ImplBase {
         return FEWHA_OK;
     }
 
+    void launch_info(fewha_launch_info *out) const override
+    {
+        out->ctas = ncta;
+        out->threads = kThreads;
+        out->smem_bytes = (long)smem;
+        out->split_levels = ncta >= 2 * P.L ? 1 : 0;
+        out->staged_tables = base.geo.stage_tab;
+        out->wfs_tile_y = base.geo.tile_y;
+        out->wfs_tile_x = base.geo.tile_x;
+        out->pt_bands = base.geo.nbands;
+        out->pt_rows_chunk = base.geo.rows_chunk;
+    }
+
     int get_invJ(double *host) const override
     {
         std::vector<T> v(P.n);
         CK(cudaMemcpy(v.data(), base.geo.invJ, P.n * sizeof(T), cudaMemcpyDeviceToHost));
         for (long i = 0; i < P.n; i++) host[i] = (double)v[i];
+        return FEWHA_OK;
+    }
+
+    // C_eta^{-1} per slope: 1/sigma_g^2 on lit subapertures, 0 elsewhere
+    std::vector<T> weight_table() const
+    {
+        std::vector<T> wm((size_t)P.G * P.ns * P.ns);
+        for (int g = 0; g < P.G; g++)
+            for (int i = 0; i < P.ns * P.ns; i++)
+                wm[(size_t)g * P.ns * P.ns + i] = P.mask[i] ? (T)P.geom.gs[g].weight : T(0);
+        return wm;
+    }
+
+    int set_weights() override
+    {
+        const std::vector<T> wm = weight_table();
+        CK(cudaMemcpy(const_cast<T *>(base.geo.wmask), wm.data(), wm.size() * sizeof(T), cudaMemcpyHostToDevice));
         return FEWHA_OK;
     }
 
@@ -1185,6 +1331,7 @@ struct Impl : ImplBase {
         A.rtol = o->rtol;
         A.augmented = o->augmented ? 1 : 0;
         A.recycle_all = o->recycle_mode == FEWHA_RECYCLE_ALL ? 1 : 0;
+        A.true_res_every = o->true_res_every;
         A.stats = stats;
         return A;
     }
@@ -1211,13 +1358,15 @@ struct Impl : ImplBase {
         int dev, nsm, per_sm = 0;
         CK(cudaGetDevice(&dev));
         CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve_batched<T, S>, kThreads, sm));
-        *max_ctas = std::min(nsm * per_sm, kMaxCtas);
+        int per_sm_tr = 0;
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve_batched<T, S, false>, kThreads, sm));
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_tr, k_solve_batched<T, S, true>, kThreads, sm));
+        *max_ctas = std::min(nsm * std::min(per_sm, per_sm_tr), kMaxCtas);
         return FEWHA_OK;
     }
 
     int launch_batched(const void *d_args, const int *d_map, int n, int total, size_t sm, int nrounds,
-                       Record *brec, cudaStream_t s) const override
+                       Record *brec, int true_res, cudaStream_t s) const override
     {
         const Args<T, S> *args = static_cast<const Args<T, S> *>(d_args);
         k_batch_reset<T, S><<<(n + 255) / 256, 256, 0, s>>>(args, n, brec);
@@ -1233,7 +1382,10 @@ struct Impl : ImplBase {
         cfg.numAttrs = 1;
         // a round may run as long as one time step of its slowest instance
         const unsigned long long to = base.timeout_ns * 4;
-        CK(cudaLaunchKernelEx(&cfg, k_solve_batched<T, S>, args, d_map, nrounds, total, brec, to));
+        if (true_res)
+            CK(cudaLaunchKernelEx(&cfg, k_solve_batched<T, S, true>, args, d_map, nrounds, total, brec, to));
+        else
+            CK(cudaLaunchKernelEx(&cfg, k_solve_batched<T, S, false>, args, d_map, nrounds, total, brec, to));
         return cudaGetLastError() == cudaSuccess ? FEWHA_OK : FEWHA_ERR_CUDA;
     }
 
@@ -1255,7 +1407,10 @@ struct Impl : ImplBase {
             attr[0].val.cooperative = 1;
             cfg.attrs = attr;
             cfg.numAttrs = 1;
-            CK(cudaLaunchKernelEx(&cfg, k_solve_persistent<T, S>, A));
+            if (A.true_res_every > 0)
+                CK(cudaLaunchKernelEx(&cfg, k_solve_persistent<T, S, true>, A));
+            else
+                CK(cudaLaunchKernelEx(&cfg, k_solve_persistent<T, S, false>, A));
             return launch_check();
         }
         k_rhs_wfs<T, S><<<ncta, kThreads, smem, s>>>(A);
@@ -1270,6 +1425,14 @@ struct Impl : ImplBase {
             k_C<T, S><<<ncta, kThreads, smem, s>>>(A, k);
             k_D1<T, S><<<ncta, kThreads, smem, s>>>(A, k);
             k_D2E<T, S><<<ncta, kThreads, smem, s>>>(A, k);
+            if (A.true_res_every > 0 && (k + 1) % A.true_res_every == 0) {
+                k_TU<T, S><<<ncta, kThreads, smem, s>>>(A);
+                k_TA2<T, S><<<ncta, kThreads, smem, s>>>(A);
+                k_TB<T, S><<<ncta, kThreads, smem, s>>>(A);
+                k_TC<T, S><<<ncta, kThreads, smem, s>>>(A);
+                k_TD1<T, S><<<ncta, kThreads, smem, s>>>(A);
+                k_TE<T, S><<<ncta, kThreads, smem, s>>>(A, k);
+            }
         }
         k_finish<T, S><<<1, kThreads, smem, s>>>(A);
         return launch_check();
@@ -1278,8 +1441,13 @@ struct Impl : ImplBase {
 
 
 ImplBase *make_impl_f64(const Plan &p);
-// Working-precision implementation of a handle (defined with the C ABI).
+// Working-precision implementation of a handle and the device it was created
+// on (defined with the C ABI).
 ImplBase *handle_impl(void *handle);
+int handle_device(const void *handle);
+// Device address of the allocation-free entry point's static scratch on the
+// current device; the first call on a device loads the module that holds it.
+int noalloc_prepare();
 ImplBase *make_impl_f32(const Plan &p);
 ImplBase *make_impl_bf16(const Plan &p);
 

@@ -755,18 +755,24 @@ __device__ void fine_synthesis(const Args<T, S> &A, const T *pk, T *sm)
     }
 }
 
+// The finest synthesis level of vector x, tiled over all CTAs (split form).
+template <typename T, typename S>
+__device__ __forceinline__ void phase_fine_synth(const Args<T, S> &A, const T *x, T *sm)
+{
+    if (!split_levels(A)) return;
+    switch (A.geo.n_taps) {
+    case 2: fine_synthesis<T, S, 2>(A, x, sm); break;
+    case 4: fine_synthesis<T, S, 4>(A, x, sm); break;
+    case 6: fine_synthesis<T, S, 6>(A, x, sm); break;
+    default: fine_synthesis<T, S, 8>(A, x, sm); break;
+    }
+}
+
 // A2_k: the finest synthesis level, tiled over all CTAs: nodal = W^{-1} p_k.
 template <typename T, typename S>
 __device__ __forceinline__ void phase_A2(const Args<T, S> &A, const Basis &b, int k, T *sm)
 {
-    if (!split_levels(A)) return;
-    const T *pk = newP(A, b, k);
-    switch (A.geo.n_taps) {
-    case 2: fine_synthesis<T, S, 2>(A, pk, sm); break;
-    case 4: fine_synthesis<T, S, 4>(A, pk, sm); break;
-    case 6: fine_synthesis<T, S, 6>(A, pk, sm); break;
-    default: fine_synthesis<T, S, 8>(A, pk, sm); break;
-    }
+    phase_fine_synth(A, newP(A, b, k), sm);
 }
 
 // D1_k: the finest analysis level of u, tiled over all CTAs.
@@ -788,13 +794,18 @@ __device__ __forceinline__ void phase_D1(const Args<T, S> &A, T *sm)
 // q_k = wq + alpha D p_k (stored in the basis slot), c += alpha p,
 // r -= alpha q with the inner products of the next step (element-parallel;
 // each layer's block by its CTA right after its transform).
-template <typename T, typename S, bool ALL>
+//
+// TR = true (residual replacement after iteration k, same layer transforms):
+// with u = P^T Gamma^T C Gamma P W^{-1} c from the preceding phases, the true
+// residual r = b - (W^{-T} u / delta + alpha D c) replaces r (b is in b_prev
+// since R3), and the same partial sums of the next step are taken from it.
+template <typename T, typename S, bool ALL, bool TR = false>
 __device__ __forceinline__ void phase_D2E_impl(const Args<T, S> &A, const Basis &b, int k, T *buf, double *sred,
                                            const double *alpha_sc)
 {
-    const T alpha = (T)(alpha_sc ? *alpha_sc : ldcgd(A.rec->alpha + k));
-    const T *pk = newP(A, b, k);
-    T *qk = newQ(A, b, k);
+    const T alpha = TR ? T(0) : (T)(alpha_sc ? *alpha_sc : ldcgd(A.rec->alpha + k));
+    const T *pk = TR ? nullptr : newP(A, b, k);
+    T *qk = TR ? nullptr : newQ(A, b, k);
     const int kv = b.kv;
     const T *pm = kv > 0 ? oldP(A, b, kv - 1) : nullptr;
     const T *qm = kv > 0 ? oldQ(A, b, kv - 1) : nullptr;
@@ -808,10 +819,14 @@ __device__ __forceinline__ void phase_D2E_impl(const Args<T, S> &A, const Basis 
     auto update_w = [&](long e, const T (&wq)[W]) {
         T p[W], ad[W], c[W], r[W], jv[W], q[W], z[W];
         T pmv[W], qmv[W];
-        vld_cg(pk + e, p);
+        if constexpr (TR) {
+            vld_cg(A.b_prev + e, r);  // b of this time step
+        } else {
+            vld_cg(pk + e, p);
+            vld_cg(A.r + e, r);
+        }
         vld_nc(A.geo.alpha_d + e, ad);
         vld_cg(A.c + e, c);
-        vld_cg(A.r + e, r);
         vld_nc(A.geo.invJ + e, jv);
         if (last) {
             vld_nc(pm + e, pmv);
@@ -819,9 +834,13 @@ __device__ __forceinline__ void phase_D2E_impl(const Args<T, S> &A, const Basis 
         }
 #pragma unroll
         for (int i = 0; i < W; i++) {
-            q[i] = wq[i] + ad[i] * p[i];
-            c[i] += alpha * p[i];
-            r[i] -= alpha * q[i];
+            if constexpr (TR) {
+                r[i] -= wq[i] + ad[i] * c[i];  // b - M c
+            } else {
+                q[i] = wq[i] + ad[i] * p[i];
+                c[i] += alpha * p[i];
+                r[i] -= alpha * q[i];
+            }
             z[i] = jv[i] * r[i];
             acc[0] += (Acc)r[i] * (Acc)z[i];
             if (last) {
@@ -830,8 +849,10 @@ __device__ __forceinline__ void phase_D2E_impl(const Args<T, S> &A, const Basis 
             }
             acc[3] += (Acc)r[i] * (Acc)r[i];
         }
-        vst(qk + e, q);
-        vst(A.c + e, c);
+        if constexpr (!TR) {
+            vst(qk + e, q);
+            vst(A.c + e, c);
+        }
         vst(A.r + e, r);
         if constexpr (ALL) {
             if (all) {
@@ -929,6 +950,90 @@ __device__ void phase_D2E(const Args<T, S> &A, const Basis &b, int k, T *buf, do
     else
         phase_D2E_impl<T, S, false>(A, b, k, buf, sred, alpha_sc);
 }
+
+// ---------------------------------------------------------------------------
+// Residual replacement after iteration k (every true_res_every-th iteration;
+// not in the paper, whose Algorithms 1-3 keep the recurrence residual):
+// r <- b - M c with one operator application of c, run on the working-
+// precision view of the arguments (TrView below), phases
+//   TU   nodal = W^{-1} c: coarser levels of c's (n/2)^2 block on the layer
+//        CTAs into A.ll (split form), or every level per layer (whole form)
+//   TA2  the finest synthesis level tiled over all CTAs (split form)
+//   TB   WFS phase (P_g, Gamma, C_eta^{-1}, Gamma^T)
+//   TC   P^T gather
+//   TD1  the finest analysis level of u (split form)
+//   TE   the coarser analysis levels, then r = b - (W^{-T} u / delta + alpha D c),
+//        z = J^{-1} r and the partial sums of the next step (replacing D2E_k's)
+// Iteration k+1 then takes its scalars from the true residual.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void phase_TU(const Args<T, T> &A, T *buf)
+{
+    constexpr int W = VW<T>::W;
+    const Geo<T> &G = A.geo;
+    if (split_levels(A)) {
+        if (A.vrank() < G.L) {
+            const int l = A.vrank(), h = G.lay_n[l] >> 1, lgh = G.lay_lg[l] - 1;
+            for_block_vectors(G, l, [&](long e, int be) {
+                T x[W];
+                vld_cg(A.c + e, x);
+                const int s0 = spad(be, lgh);
+#pragma unroll
+                for (int i = 0; i < W; i++) buf[s0 + i] = x[i];
+            });
+            __syncthreads();
+            idwt2<T>(buf, G.pingpong ? buf + h * (h + 1) : buf, lgh, G.lay_J[l] - 1, G);
+            T *ll = A.ll + G.ll_off[l];
+            for (int v = threadIdx.x; v < h * h / W; v += blockDim.x) {
+                const int be = v * W, s0 = spad(be, lgh);
+                T x[W];
+#pragma unroll
+                for (int i = 0; i < W; i++) x[i] = buf[s0 + i];
+                vst(ll + be, x);
+            }
+            __syncthreads();
+        }
+    } else {
+        layer_idwt<T, T>(A, buf, [&](long e, T (&x)[W]) { vld_cg(A.c + e, x); });
+    }
+}
+
+template <typename T>
+__device__ void phase_TE(const Args<T, T> &A, const Basis &b, int k, T *buf, double *sred)
+{
+    if (A.recycle_all)
+        phase_D2E_impl<T, T, true, true>(A, b, k, buf, sred, nullptr);
+    else
+        phase_D2E_impl<T, T, false, true>(A, b, k, buf, sred, nullptr);
+}
+
+// The residual replacement's view of the arguments: the same arguments with
+// the operator's nodal layers and adjoint wavefronts in the working precision
+// T.  With S == T that is the arguments themselves; otherwise a copy in
+// shared memory whose nodal / psi point at the T-typed buffers.
+template <typename T, typename S>
+struct TrView {
+    __device__ static const Args<T, T> *get(const Args<T, S> &A)
+    {
+        static_assert(sizeof(Args<T, T>) == sizeof(Args<T, S>), "same layout");
+        __shared__ __align__(16) Args<T, T> V;
+        const int4 *src = reinterpret_cast<const int4 *>(&A);
+        int4 *dst = reinterpret_cast<int4 *>(&V);
+        for (int e = threadIdx.x; e < (int)(sizeof(V) / sizeof(int4)); e += blockDim.x) dst[e] = src[e];
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            V.nodal = A.nodal_t;
+            V.psi = A.psi_t;
+            V.slopes = nullptr;
+        }
+        __syncthreads();
+        return &V;
+    }
+};
+template <typename T>
+struct TrView<T, T> {
+    __device__ static const Args<T, T> *get(const Args<T, T> &A) { return &A; }
+};
 
 // Stats and the recycled-basis metadata for the next time step (CTA 0).
 template <typename T, typename S>

@@ -55,7 +55,13 @@ class STATE(C.Structure):
 
 class OPTS(C.Structure):
     _fields_ = [("max_iter", C.c_int), ("rtol", C.c_double), ("augmented", C.c_int),
-                ("recycle_mode", C.c_int), ("launch_mode", C.c_int), ("reserved", C.c_int)]
+                ("recycle_mode", C.c_int), ("launch_mode", C.c_int), ("true_res_every", C.c_int)]
+
+
+class LAUNCH_INFO(C.Structure):
+    _fields_ = [("ctas", C.c_int), ("threads", C.c_int), ("smem_bytes", C.c_long),
+                ("split_levels", C.c_int), ("staged_tables", C.c_int), ("wfs_tile_y", C.c_int),
+                ("wfs_tile_x", C.c_int), ("pt_bands", C.c_int), ("pt_rows_chunk", C.c_int)]
 
 
 class STATS(C.Structure):
@@ -87,6 +93,10 @@ def load_library(path=LIB_PATH):
     lib.fewha_n_slopes.restype = C.c_long
     lib.fewha_layer_spacing.argtypes = [vp, C.c_int]
     lib.fewha_layer_spacing.restype = C.c_double
+    lib.fewha_set_noise.argtypes = [vp, dp, C.c_int]
+    lib.fewha_set_noise.restype = C.c_int
+    lib.fewha_get_launch_info.argtypes = [vp, C.POINTER(LAUNCH_INFO)]
+    lib.fewha_get_launch_info.restype = C.c_int
     lib.fewha_get_prior.argtypes = [vp, dp]
     lib.fewha_get_precond.argtypes = [vp, dp]
     lib.fewha_apply_op.argtypes = [vp, vp, vp, vp]
@@ -170,7 +180,7 @@ def exported_symbols():
             "fewha_conv3x3_wgrad_workspace", "fewha_conv3x3_bwd_weight", "fewha_relu_bwd",
             "fewha_mse_grad", "fewha_adam_step", "fewha_scale", "fewha_learned_targets",
             "fewha_deflate_warm_start", "fewha_mcao_create", "fewha_mcao_n_actuators", "fewha_mcao_fit",
-            "fewha_mcao_destroy"]
+            "fewha_mcao_destroy", "fewha_get_launch_info", "fewha_set_noise"]
 
 
 def make_geometry(geom, noise_w, precision="f64", tile=0, grid=0) -> GEOMETRY:
@@ -261,6 +271,20 @@ class Fewha:
         out = np.empty(self.n)
         self._check(self.lib.fewha_get_prior(self._h, out.ctypes.data_as(C.POINTER(C.c_double))), "get_prior")
         return out
+
+    def set_noise(self, noise_w, refresh_precond=True):
+        """New noise weights 1/sigma_g^2 (C_eta^{-1}); refresh_precond rebuilds J's data term."""
+        w = np.ascontiguousarray(np.asarray(noise_w, dtype=np.float64))
+        if w.shape != (len(self._g.gs[:self._g.n_gs]),):
+            raise ValueError("one weight per guide star")
+        self._check(self.lib.fewha_set_noise(self._h, w.ctypes.data_as(C.POINTER(C.c_double)),
+                                              1 if refresh_precond else 0), "fewha_set_noise")
+
+    def launch_info(self):
+        """Launch shape chosen at creation (fewha_get_launch_info) as a dict."""
+        li = LAUNCH_INFO()
+        self._check(self.lib.fewha_get_launch_info(self._h, C.byref(li)), "get_launch_info")
+        return {k: getattr(li, k) for k, _ in LAUNCH_INFO._fields_}
 
     def precond(self):
         out = np.empty(self.n)
@@ -362,11 +386,13 @@ class Fewha:
         return self._torch.zeros(STATS_BYTES, dtype=self._torch.uint8, device=self.device)
 
     def solve(self, s, c, state, max_iter, rtol=0.0, augmented=True, recycle_all=False,
-              persistent=True, stats=None):
-        """One time step; c is updated in place.  Returns the device stats buffer."""
+              persistent=True, stats=None, true_res_every=0):
+        """One time step; c is updated in place.  Returns the device stats buffer.
+        true_res_every = N > 0 replaces the residual by b - M c after every N-th
+        iteration."""
         o = OPTS(int(max_iter), float(rtol), 1 if augmented else 0,
                  RECYCLE_ALL if recycle_all else RECYCLE_LAST,
-                 LAUNCH_PERSISTENT if persistent else LAUNCH_PHASES, 0)
+                 LAUNCH_PERSISTENT if persistent else LAUNCH_PHASES, int(true_res_every))
         stats = stats if stats is not None else self.new_stats()
         self._check(self.lib.fewha_solve(self._h, self._vec(s, self.n_slopes, self.slope_dtype, "s"),
                                          self._vec(c, self.n, self.dtype, "c"), C.byref(state.c_struct),
@@ -380,7 +406,8 @@ class Fewha:
 
     TRACE_TAGS = {1: "R1 wfs(rhs)", 2: "R2 gather(rhs)", 3: "R3 fdwt(rhs)", 4: "P^T r0", 5: "init",
                   10: "UA1 update+idwt", 16: "A2 idwt fine", 12: "B wfs", 13: "C gather",
-                  14: "D1 fdwt fine", 15: "D2E fdwt+axpy"}
+                  14: "D1 fdwt fine", 15: "D2E fdwt+axpy", 20: "TU idwt(c)", 21: "TA2 idwt fine",
+                  22: "TB wfs", 23: "TC gather", 24: "TD1 fdwt fine", 25: "TE b-Mc"}
 
     def set_trace(self, buf):
         """Enables the phase trace into a CUDA uint64/int64 tensor of shape (cap, 4), or None."""
@@ -496,7 +523,8 @@ class FewhaBatch:
     def new_stats(self):
         return self._torch.zeros(self.n * STATS_BYTES, dtype=self._torch.uint8, device=self.device)
 
-    def solve(self, slopes, cs, states, max_iter, rtol=0.0, augmented=True, recycle_all=False, stats=None):
+    def solve(self, slopes, cs, states, max_iter, rtol=0.0, augmented=True, recycle_all=False, stats=None,
+              true_res_every=0):
         """One time step of every instance; cs are updated in place."""
         n = self.n
         for f, sl, c in zip(self.fewhas, slopes, cs):
@@ -506,7 +534,7 @@ class FewhaBatch:
         cp = (C.c_void_p * n)(*[t.data_ptr() for t in cs])
         stt = (STATE * n)(*[s_.c_struct for s_ in states])
         o = OPTS(int(max_iter), float(rtol), 1 if augmented else 0, RECYCLE_ALL if recycle_all else RECYCLE_LAST,
-                 LAUNCH_PERSISTENT, 0)
+                 LAUNCH_PERSISTENT, int(true_res_every))
         stats = stats if stats is not None else self.new_stats()
         st = self.lib.fewha_batch_solve(self._b, sp, cp, stt, C.byref(o), C.c_void_p(stats.data_ptr()),
                                         _stream_ptr(self._torch))
@@ -514,7 +542,8 @@ class FewhaBatch:
             raise FewhaError(st, "fewha_batch_solve")
         return stats
 
-    def bind(self, slopes, cs, states, max_iter, rtol=0.0, augmented=True, recycle_all=False, stats=None):
+    def bind(self, slopes, cs, states, max_iter, rtol=0.0, augmented=True, recycle_all=False, stats=None,
+             true_res_every=0):
         """Fixes the buffers of launch(): every launch solves one time step of every
         instance from the current contents of `slopes` into `cs` (fewha_batch_bind)."""
         n = self.n
@@ -525,7 +554,7 @@ class FewhaBatch:
         cp = (C.c_void_p * n)(*[t.data_ptr() for t in cs])
         stt = (STATE * n)(*[s_.c_struct for s_ in states])
         o = OPTS(int(max_iter), float(rtol), 1 if augmented else 0, RECYCLE_ALL if recycle_all else RECYCLE_LAST,
-                 LAUNCH_PERSISTENT, 0)
+                 LAUNCH_PERSISTENT, int(true_res_every))
         self._bound = (slopes, cs, states, stats if stats is not None else self.new_stats())
         st = self.lib.fewha_batch_bind(self._b, sp, cp, stt, C.byref(o), C.c_void_p(self._bound[3].data_ptr()))
         if st != 0:
