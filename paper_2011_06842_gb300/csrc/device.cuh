@@ -344,6 +344,30 @@ __device__ inline void reduce_ranges(const double *part, int ncta, SlotRange r0,
     __syncthreads();
 }
 
+// Sum over CTAs of `count` consecutive slots with the loads of every slot in
+// one round: g lanes per slot (the largest power of two <= 32 with
+// g * count <= blockDim.x), each summing every g-th partial, then a shuffle
+// tree over the g lanes (fixed order).  For counts beyond the warps of a CTA.
+__device__ inline void reduce_wide(const double *part, int ncta, int slot0, int count, double *out)
+{
+    int g = 32;
+    while (g > 1 && g * count > (int)blockDim.x) g >>= 1;
+    const int s = threadIdx.x / g, j = threadIdx.x - s * g;
+    double acc = 0.0;
+    if (s < count) {
+        const double *p = part + (size_t)(slot0 + s) * kMaxCtas;
+        double v[8];
+#pragma unroll
+        for (int i = 0; i < 8; i++) v[i] = (j + g * i < ncta) ? __ldcg(p + j + g * i) : 0.0;
+        acc = ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7]));
+#pragma unroll 4
+        for (int c = j + 8 * g; c < ncta; c += g) acc += __ldcg(p + c);
+    }
+    for (int o = g >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (s < count && j == 0) out[s] = acc;
+    __syncthreads();
+}
+
 // Warp-parallel Cholesky factorisation (right-looking) of the symmetrised
 // k x k matrix G (row-major): L (row-major, k x k, lower) and dinv_j = 1/L_jj.
 // Run by one full warp; returns false if not positive definite.

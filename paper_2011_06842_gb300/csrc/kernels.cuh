@@ -239,20 +239,21 @@ __global__ void __launch_bounds__(kThreads, 1) k_rhs_gather(const __grid_constan
     if (b.kv > 0 && A.vrank() == A.ncta - 1) phase_factor<T, S>(A, b, sc);
 }
 
+// R3: the finest analysis level of u (split form), then b, r0 and P^T r0
 template <typename T, typename S>
-__global__ void __launch_bounds__(kThreads, 1) k_rhs_fdwt(const __grid_constant__ Args<T, S> Ap)
+__global__ void __launch_bounds__(kThreads, 1) k_rhs_D1(const __grid_constant__ Args<T, S> Ap)
 {
     FEWHA_PHASE_GUARD
     (void)sc;
-    phase_rhs_fdwt<T, S>(A, dyn_smem<T>(), sred);
+    phase_D1<T, S>(A, dyn_smem<T>());
 }
 
 template <typename T, typename S>
-__global__ void __launch_bounds__(kThreads, 1) k_ptr(const __grid_constant__ Args<T, S> Ap)
+__global__ void __launch_bounds__(kThreads, 1) k_rhs_update(const __grid_constant__ Args<T, S> Ap)
 {
     FEWHA_PHASE_GUARD
     (void)sc;
-    if (b.kv > 0) phase_ptr<T, S>(A, b, sred);
+    phase_rhs_update<T, S>(A, b, dyn_smem<T>(), sred);
 }
 
 template <typename T, typename S>
@@ -437,11 +438,13 @@ __device__ void solve_body(const Args<T, S> &A, Scal &sc, double *sred)
         band_gather<T, S>(A, sm);
         if (b.kv > 0 && rank == A.ncta - 1) phase_factor<T, S>(A, b, sc);
         if (!sync(2)) break;
-        phase_rhs_fdwt<T, S>(A, sm, sred);
+        if (split) {
+            phase_D1<T, S>(A, sm);  // the finest analysis level of u
+            if (!sync(6)) break;
+        }
+        phase_rhs_update<T, S>(A, b, sm, sred);  // b, r0 and P^T r0
         if (!sync(3)) break;
         if (b.kv > 0) {
-            phase_ptr<T, S>(A, b, sred);
-            if (!sync(4)) break;
             phase_init<T, S>(A, b, sc, sred);
             if (!sync(5)) break;
         }
@@ -910,9 +913,9 @@ struct Impl : ImplBase {
         CK(setattr((const void *)k_fdwt<T, S, false>));
         CK(setattr((const void *)k_fdwt<T, S, true>));
         CK(setattr((const void *)k_rhs_wfs<T, S>));
-        CK(setattr((const void *)k_rhs_fdwt<T, S>));
+        CK(setattr((const void *)k_rhs_D1<T, S>));
+        CK(setattr((const void *)k_rhs_update<T, S>));
         CK(setattr((const void *)k_rhs_gather<T, S>));
-        CK(setattr((const void *)k_ptr<T, S>));
         CK(setattr((const void *)k_init<T, S>));
         CK(setattr((const void *)k_UA1<T, S>));
         CK(setattr((const void *)k_A2<T, S>));
@@ -1415,8 +1418,8 @@ struct Impl : ImplBase {
         }
         k_rhs_wfs<T, S><<<ncta, kThreads, smem, s>>>(A);
         k_rhs_gather<T, S><<<ncta, kThreads, smem, s>>>(A);
-        k_rhs_fdwt<T, S><<<ncta, kThreads, smem, s>>>(A);
-        k_ptr<T, S><<<ncta, kThreads, smem, s>>>(A);
+        k_rhs_D1<T, S><<<ncta, kThreads, smem, s>>>(A);
+        k_rhs_update<T, S><<<ncta, kThreads, smem, s>>>(A);
         k_init<T, S><<<ncta, kThreads, smem, s>>>(A);
         for (int k = 0; k < A.max_iter; k++) {
             k_UA1<T, S><<<ncta, kThreads, smem, s>>>(A, k);

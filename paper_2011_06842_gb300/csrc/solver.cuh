@@ -156,7 +156,7 @@ template <typename T, typename S>
 __device__ __forceinline__ void phase_factor(const Args<T, S> &A, const Basis &b, Scal &sc)
 {
     const int kv = b.kv;
-    reduce_ranges(A.part, A.ncta, {kSlotGram, kv * kv, sc.gram});
+    reduce_wide(A.part, A.ncta, kSlotGram, kv * kv, sc.gram);
     if (threadIdx.x < 32) {
         const bool ok = warp_cholesky(kv, sc.gram, sc.L, sc.dinv);
         if (threadIdx.x == 0) {
@@ -169,76 +169,31 @@ __device__ __forceinline__ void phase_factor(const Args<T, S> &A, const Basis &b
     __syncthreads();
 }
 
-// ---------------------------------------------------------------------------
-// R3: right-hand side b = W^{-T} u / delta (u = P^T Gamma^T C s from the
-// preceding phases) and the warm-restart residual of Algorithm 3,
-// r0 = (b - b_prev) + r_prev;  b_prev <- b.
-// ---------------------------------------------------------------------------
-template <typename T, typename S>
-__device__ __forceinline__ void phase_rhs_fdwt(const Args<T, S> &A, T *sm, double *sred)
-{
-    typedef typename AccT<T>::type Acc;
-    constexpr int W = VW<T>::W;
-    Acc acc[2] = {0, 0};
-    layer_fdwt<T, S>(A, sm, [&](long e, const T (&b)[W]) {
-        T bp[W], rp[W], r0[W];
-        vld(A.b_prev + e, bp);
-        vld_cg(A.r + e, rp);
-#pragma unroll
-        for (int i = 0; i < W; i++) {
-            r0[i] = (b[i] - bp[i]) + rp[i];
-            acc[0] += (Acc)b[i] * (Acc)b[i];
-            acc[1] += (Acc)r0[i] * (Acc)r0[i];
-        }
-        vst(A.b_prev + e, b);
-        vst(A.r + e, r0);
-    });
-    const int slots[2] = {kSlotR2, kSlotR2 + 1};
-    block_partials<2>(acc, A.part, slots, sred, A.vrank());
-}
-
-// INIT1: P^T r0 (Algorithm 2 initial projection), per CTA slice, one element
-// per thread.
-template <typename T, typename S>
-__device__ __forceinline__ void phase_ptr(const Args<T, S> &A, const Basis &b, double *sred)
-{
-    typedef typename AccT<T>::type Acc;
-    constexpr int W = VW<T>::W;
-    __shared__ const T *sp[kK], *sq[kK];
-    basis_table(A, b, sp, sq);
-    long lo, hi;
-    cta_range_vec(A.geo.n, W, A.vrank(), A.ncta, lo, hi);
-    const int kv = b.kv;
-    Acc acc[kK];
-#pragma unroll
-    for (int j = 0; j < kK; j++) acc[j] = 0;
-    for (long e = lo + threadIdx.x; e < hi; e += blockDim.x) {
-        const T rv = ldcg(A.r + e);
-        T pj[kK];
-#pragma unroll
-        for (int j = 0; j < kK; j++) pj[j] = j < kv ? __ldg(sp[j] + e) : T(0);
-#pragma unroll
-        for (int j = 0; j < kK; j++) acc[j] += (Acc)pj[j] * (Acc)rv;
-    }
-    int slots[kK];
-    for (int j = 0; j < kK; j++) slots[j] = kSlotGram + kK * kK + j;
-    block_partials<kK>(acc, A.part, slots, sred, A.vrank());
-}
-
 // INIT2: c += P sigma, r -= Q sigma with sigma = G^{-1} P^T r0; then the
 // partial sums (q_j, z), (r, z), (r, r) with z = J^{-1} r.
 template <typename T, typename S>
 __device__ __forceinline__ void phase_init(const Args<T, S> &A, const Basis &b, Scal &sc, double *sred)
 {
     const int kv = b.kv;
+    __shared__ const T *sp[kK], *sq[kK];
+    basis_table(A, b, sp, sq);
+    // the Cholesky factor (written during R2) is loaded while P^T r0 is reduced
+    const int nf = kv * kv;
+    double fv = 0.0;
+    if (threadIdx.x < nf)
+        fv = ldcgd(A.rec->L + threadIdx.x);
+    else if (threadIdx.x < nf + kv)
+        fv = ldcgd(A.rec->dinv + threadIdx.x - nf);
     reduce_ranges(A.part, A.ncta, {kSlotGram + kK * kK, kv, sc.red});
-    load_factor(A, kv, sc);
+    if (threadIdx.x < nf)
+        sc.L[threadIdx.x] = fv;
+    else if (threadIdx.x < nf + kv)
+        sc.dinv[threadIdx.x - nf] = fv;
+    __syncthreads();
     if (threadIdx.x < 32) warp_chol_solve(kv, sc.L, sc.dinv, sc.red, sc.tau);
     __syncthreads();
     typedef typename AccT<T>::type Acc;
     constexpr int W = VW<T>::W;
-    __shared__ const T *sp[kK], *sq[kK];
-    basis_table(A, b, sp, sq);
     long lo, hi;
     cta_range_vec(A.geo.n, W, A.vrank(), A.ncta, lo, hi);
     Acc acc[kK + 2];
@@ -789,6 +744,87 @@ __device__ __forceinline__ void phase_D1(const Args<T, S> &A, T *sm)
 }
 
 
+// ---------------------------------------------------------------------------
+// The last part of W^{-T} u / delta and an element update over it.  Split form
+// (after D1): each layer CTA runs the coarser analysis levels of its layer's
+// approximation block (from A.ll) in shared memory and calls upd(e, wq) for
+// the block's W-vectors with wq taken from there; every other CTA calls it
+// for the detail coefficients in its element range with wq from A.wq (D1's
+// output).  Whole form: each layer's CTA transforms the whole of u's layer in
+// shared memory and calls upd for every W-vector of the layer.
+// ---------------------------------------------------------------------------
+template <typename T, typename S, class Upd>
+__device__ __forceinline__ void analysis_update(const Args<T, S> &A, T *buf, Upd update_w)
+{
+    constexpr int W = VW<T>::W;
+    auto update = [&](long e) {
+        T wq[W];
+        vld_cg(A.wq + e, wq);
+        update_w(e, wq);
+    };
+    const Geo<T> &G = A.geo;
+    if (!split_levels(A)) {
+        // whole layer: W^{-T} u / delta in shared memory, then the update of the
+        // layer with wq read from there
+        for (int l = A.vrank(); l < G.L; l += A.ncta) {
+            const int n = G.lay_n[l], lgn = G.lay_lg[l], nv = n * n / W;
+            const long off = G.lay_off[l];
+#pragma unroll 2
+            for (int v = threadIdx.x; v < nv; v += blockDim.x) {
+                T x[W];
+                vld_cg(A.u + off + (long)v * W, x);
+                const int s0 = spad(v * W, lgn);
+#pragma unroll
+                for (int i = 0; i < W; i++) buf[s0 + i] = x[i];
+            }
+            __syncthreads();
+            fdwt2<T>(buf, G.pingpong ? buf + n * (n + 1) : buf, lgn, G.lay_J[l], G);
+            const T sc = G.inv_delta[l];
+            for (int v = threadIdx.x; v < nv; v += blockDim.x) {
+                T wq[W];
+                const int s0 = spad(v * W, lgn);
+#pragma unroll
+                for (int i = 0; i < W; i++) wq[i] = buf[s0 + i] * sc;
+                update_w(off + (long)v * W, wq);
+            }
+            __syncthreads();
+        }
+    }
+    // split: the layer's CTA runs the coarser analysis levels of the
+    // approximation block (from D1_k), then the update on that block with
+    // W^{-T} u / delta taken from shared memory; the other CTAs update the
+    // detail coefficients (their wq from D1_k)
+    if (split_levels(A)) {
+        if (A.vrank() < G.L) {
+            const int l = A.vrank(), n = G.lay_n[l], h = n >> 1, lgh = G.lay_lg[l] - 1, nv = h * h / W;
+            const T *ll = A.ll + G.ll_off[l];
+#pragma unroll 4
+            for (int v = threadIdx.x; v < nv; v += blockDim.x) {
+                T x[W];
+                vld_cg(ll + (long)v * W, x);
+                const int s0 = spad(v * W, lgh);
+#pragma unroll
+                for (int i = 0; i < W; i++) buf[s0 + i] = x[i];
+            }
+            __syncthreads();
+            fdwt2<T>(buf, G.pingpong ? buf + h * (h + 1) : buf, lgh, G.lay_J[l] - 1, G);
+            const T sc = G.inv_delta[l];
+            for_block_vectors(G, l, [&](long e, int be) {
+                T wq[W];
+                const int s0 = spad(be, lgh);
+#pragma unroll
+                for (int i = 0; i < W; i++) wq[i] = buf[s0 + i] * sc;
+                update_w(e, wq);
+            });
+            __syncthreads();
+        } else {
+            long lo, hi;
+            cta_range_vec(G.n, W, A.vrank() - G.L, A.ncta - G.L, lo, hi);
+            for_detail_vectors(G, lo, hi, update);
+        }
+    }
+}
+
 // D2E_k: the coarser analysis levels of each layer's approximation block (the
 // layer's CTA; W^{-T} u / delta is then complete), and the update
 // q_k = wq + alpha D p_k (stored in the basis slot), c += alpha p,
@@ -869,72 +905,7 @@ __device__ __forceinline__ void phase_D2E_impl(const Args<T, S> &A, const Basis 
             }
         }
     };
-    auto update = [&](long e) {
-        T wq[W];
-        vld_cg(A.wq + e, wq);
-        update_w(e, wq);
-    };
-    const Geo<T> &G = A.geo;
-    if (!split_levels(A)) {
-        // whole layer: W^{-T} u / delta in shared memory, then the update of the
-        // layer with wq read from there
-        for (int l = A.vrank(); l < G.L; l += A.ncta) {
-            const int n = G.lay_n[l], lgn = G.lay_lg[l], nv = n * n / W;
-            const long off = G.lay_off[l];
-#pragma unroll 2
-            for (int v = threadIdx.x; v < nv; v += blockDim.x) {
-                T x[W];
-                vld_cg(A.u + off + (long)v * W, x);
-                const int s0 = spad(v * W, lgn);
-#pragma unroll
-                for (int i = 0; i < W; i++) buf[s0 + i] = x[i];
-            }
-            __syncthreads();
-            fdwt2<T>(buf, G.pingpong ? buf + n * (n + 1) : buf, lgn, G.lay_J[l], G);
-            const T sc = G.inv_delta[l];
-            for (int v = threadIdx.x; v < nv; v += blockDim.x) {
-                T wq[W];
-                const int s0 = spad(v * W, lgn);
-#pragma unroll
-                for (int i = 0; i < W; i++) wq[i] = buf[s0 + i] * sc;
-                update_w(off + (long)v * W, wq);
-            }
-            __syncthreads();
-        }
-    }
-    // split: the layer's CTA runs the coarser analysis levels of the
-    // approximation block (from D1_k), then the update on that block with
-    // W^{-T} u / delta taken from shared memory; the other CTAs update the
-    // detail coefficients (their wq from D1_k)
-    if (split_levels(A)) {
-        if (A.vrank() < G.L) {
-            const int l = A.vrank(), n = G.lay_n[l], h = n >> 1, lgh = G.lay_lg[l] - 1, nv = h * h / W;
-            const T *ll = A.ll + G.ll_off[l];
-#pragma unroll 4
-            for (int v = threadIdx.x; v < nv; v += blockDim.x) {
-                T x[W];
-                vld_cg(ll + (long)v * W, x);
-                const int s0 = spad(v * W, lgh);
-#pragma unroll
-                for (int i = 0; i < W; i++) buf[s0 + i] = x[i];
-            }
-            __syncthreads();
-            fdwt2<T>(buf, G.pingpong ? buf + h * (h + 1) : buf, lgh, G.lay_J[l] - 1, G);
-            const T sc = G.inv_delta[l];
-            for_block_vectors(G, l, [&](long e, int be) {
-                T wq[W];
-                const int s0 = spad(be, lgh);
-#pragma unroll
-                for (int i = 0; i < W; i++) wq[i] = buf[s0 + i] * sc;
-                update_w(e, wq);
-            });
-            __syncthreads();
-        } else {
-            long lo, hi;
-            cta_range_vec(G.n, W, A.vrank() - G.L, A.ncta - G.L, lo, hi);
-            for_detail_vectors(G, lo, hi, update);
-        }
-    }
+    analysis_update(A, buf, update_w);
     const int e0 = kSlotE + (k & 1) * kSlotEStride;
     int slots[NA];
     for (int i = 0; i < NA; i++) slots[i] = e0 + i;
@@ -949,6 +920,112 @@ __device__ void phase_D2E(const Args<T, S> &A, const Basis &b, int k, T *buf, do
         phase_D2E_impl<T, S, true>(A, b, k, buf, sred, alpha_sc);
     else
         phase_D2E_impl<T, S, false>(A, b, k, buf, sred, alpha_sc);
+}
+
+// ---------------------------------------------------------------------------
+// R3 (after D1 of u in the split form; on u in the whole form): the
+// right-hand side b = W^{-T} u / delta and the warm-restart residual of
+// Algorithm 3, r0 = (b - b_prev) + r_prev, b_prev <- b, with the partial
+// sums of ||b||^2 and ||r0||^2 and, when a recycled basis is present, of
+// P^T r0 (the first step of Algorithm 2's initial projection) in the same
+// pass over the elements.
+// ---------------------------------------------------------------------------
+// The W-vectors whose update analysis_update gives to this CTA, in the same
+// order: its layer's block (split form, layer CTAs), its detail range (split
+// form, other CTAs), or its whole layers (whole form).
+template <typename T, typename S, class F>
+__device__ __forceinline__ void for_updated_vectors(const Args<T, S> &A, F body)
+{
+    constexpr int W = VW<T>::W;
+    const Geo<T> &G = A.geo;
+    if (!split_levels(A)) {
+        for (int l = A.vrank(); l < G.L; l += A.ncta)
+            for (int v = threadIdx.x; v < G.lay_n[l] * G.lay_n[l] / W; v += blockDim.x) body(G.lay_off[l] + (long)v * W);
+    } else if (A.vrank() < G.L) {
+        for_block_vectors(G, A.vrank(), [&](long e, int) { body(e); });
+    } else {
+        long lo, hi;
+        cta_range_vec(G.n, W, A.vrank() - G.L, A.ncta - G.L, lo, hi);
+        for_detail_vectors(G, lo, hi, body);
+    }
+}
+
+// P^T r0 partial sums of R3 for up to KV recycled directions, together with
+// the ||b||^2 and ||r0||^2 partials already in acc.
+template <typename T, typename S, int KV>
+__device__ __noinline__ void rhs_ptr_pass(const Args<T, S> &A, const Basis &b,
+                                             const typename AccT<T>::type (&acc)[2], double *sred)
+{
+    typedef typename AccT<T>::type Acc;
+    constexpr int W = VW<T>::W;
+    const int kv = b.kv;
+    __shared__ const T *sp[kK], *sq[kK];
+    basis_table(A, b, sp, sq);
+    Acc pr[2 + KV];
+    pr[0] = acc[0];
+    pr[1] = acc[1];
+#pragma unroll
+    for (int j = 0; j < KV; j++) pr[2 + j] = 0;
+    for_updated_vectors(A, [&](long e) {
+        T r0[W];
+        vld_cg(A.r + e, r0);
+        constexpr int CJ = 2;  // directions loaded at once
+#pragma unroll
+        for (int j0 = 0; j0 < KV; j0 += CJ) {
+            if (j0 < kv) {
+                T pj[CJ][W];
+#pragma unroll
+                for (int t = 0; t < CJ; t++)
+                    if (j0 + t < kv) vld_nc(sp[j0 + t] + e, pj[t]);
+#pragma unroll
+                for (int t = 0; t < CJ; t++)
+                    if (j0 + t < kv) {
+#pragma unroll
+                        for (int i = 0; i < W; i++) pr[2 + j0 + t] += (Acc)pj[t][i] * (Acc)r0[i];
+                    }
+            }
+        }
+    });
+    int slots[2 + KV];
+    slots[0] = kSlotR2;
+    slots[1] = kSlotR2 + 1;
+#pragma unroll
+    for (int j = 0; j < KV; j++) slots[2 + j] = kSlotGram + kK * kK + j;
+    block_partials<2 + KV>(pr, A.part, slots, sred, A.vrank());
+}
+
+template <typename T, typename S>
+__device__ __forceinline__ void phase_rhs_update(const Args<T, S> &A, const Basis &b, T *buf, double *sred)
+{
+    typedef typename AccT<T>::type Acc;
+    constexpr int W = VW<T>::W;
+    const int kv = b.kv;
+    Acc acc[2] = {0, 0};
+    analysis_update(A, buf, [&](long e, const T (&bv)[W]) {
+        T bp[W], rp[W], r0[W];
+        vld(A.b_prev + e, bp);
+        vld_cg(A.r + e, rp);
+#pragma unroll
+        for (int i = 0; i < W; i++) {
+            r0[i] = (bv[i] - bp[i]) + rp[i];
+            acc[0] += (Acc)bv[i] * (Acc)bv[i];
+            acc[1] += (Acc)r0[i] * (Acc)r0[i];
+        }
+        vst(A.b_prev + e, bv);
+        vst(A.r + e, r0);
+    });
+    if (kv == 0) {
+        const int slots[2] = {kSlotR2, kSlotR2 + 1};
+        block_partials<2>(acc, A.part, slots, sred, A.vrank());
+        return;
+    }
+    // P^T r0 over the same elements (each thread rereads the r0 it wrote),
+    // in a second pass so that its accumulators are not live across the
+    // layer transforms; accumulators sized for the basis in use
+    if (kv <= 8)
+        rhs_ptr_pass<T, S, 8>(A, b, acc, sred);
+    else
+        rhs_ptr_pass<T, S, kK>(A, b, acc, sred);
 }
 
 // ---------------------------------------------------------------------------

@@ -404,7 +404,8 @@ class Fewha:
         """Time limit of the solver's device-side waits (ns)."""
         self._check(self.lib.fewha_set_timeout(self._h, int(ns)), "fewha_set_timeout")
 
-    TRACE_TAGS = {1: "R1 wfs(rhs)", 2: "R2 gather(rhs)", 3: "R3 fdwt(rhs)", 4: "P^T r0", 5: "init",
+    TRACE_TAGS = {1: "R1 wfs(rhs)", 2: "R2 gather(rhs)", 6: "R3a fdwt fine(rhs)", 3: "R3b b,r0,P^T r0",
+                  5: "init",
                   10: "UA1 update+idwt", 16: "A2 idwt fine", 12: "B wfs", 13: "C gather",
                   14: "D1 fdwt fine", 15: "D2E fdwt+axpy", 20: "TU idwt(c)", 21: "TA2 idwt fine",
                   22: "TB wfs", 23: "TC gather", 24: "TD1 fdwt fine", 25: "TE b-Mc"}
