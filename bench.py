@@ -46,7 +46,8 @@ def parse():
     p.add_argument("--no-flush", action="store_true")
     p.add_argument("--no-compare", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
-    p.add_argument("--cpu-frames", type=int, default=3)
+    p.add_argument("--cpu-frames", type=int, default=5)
+    p.add_argument("--no-cpu-all", action="store_true", help="skip the all-host-cores oracle baseline")
     p.add_argument("--tile", type=int, default=0)
     p.add_argument("--grid", type=int, default=0)
     p.add_argument("--no-batched", action="store_true", help="skip the 64-instance batched measurement")
@@ -64,11 +65,38 @@ def parse():
 
 def workload_name(geom, args):
     return ("%s: D=%.0f m, %d GS (%s), %dx%d SH, %d layers (%s), n=%d, Daubechies-%d, k=%d, "
-            "%s PCG to rel. residual %g, %s"
+            "%s PCG to rel. residual %g, SNR %g"
             % (geom.name, geom.D, len(geom.gs), "LGS H=90 km" if geom.gs[0].H > 0 else "NGS",
                geom.n_sub, geom.n_sub, len(geom.layers),
                "+".join("%d^2" % l.n for l in geom.layers), geom.n_unknowns, geom.wavelet_N,
-               args.k, "plain" if args.plain else "augmented", args.rtol, args.precision))
+               args.k, "plain" if args.plain else "augmented", args.rtol, geom.snr))
+
+
+def bench_config(geom, args, flush=True):
+    """The `config` object of the JSON line, the same for both arms."""
+    return {"workload": workload_name(geom, args), "n_unknowns": geom.n_unknowns, "n_slopes": geom.n_slopes,
+            "rtol": args.rtol, "max_iter": args.max_iter, "k_recycle": args.k, "snr": geom.snr,
+            "frames": args.warmup + args.steps,
+            "l2": "flushed (256 MB written) before every timed frame" if flush else "not flushed",
+            "parallelism": "replicas" if int(os.environ.get("WORLD_SIZE", "1")) > 1 else "single GPU"}
+
+
+def cpu_model():
+    """CPU model name of this host (lscpu or /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
 
 
 def source_hash():
@@ -178,7 +206,7 @@ def torch_float64():
     return torch.float64
 
 
-def time_solves(f, frames, dtype, args, nwarm, nsteps, aug, flush_buf, stats_buf, rtol):
+def time_solves(f, frames, dtype, args, nwarm, nsteps, aug, flush_buf, stats_buf, rtol, true_res_every=0):
     """Per-frame CUDA-event timing; returns (times_ms, stats list)."""
     import torch
     n = f.n
@@ -189,14 +217,15 @@ def time_solves(f, frames, dtype, args, nwarm, nsteps, aug, flush_buf, stats_buf
     sl = frames.to(dtype)
     for t in range(nwarm):
         f.solve(sl[t], c, st, args.max_iter, rtol=rtol, augmented=aug,
-                persistent=args.launch == "persistent", stats=stats_buf[t % len(stats_buf)])
+                persistent=args.launch == "persistent", stats=stats_buf[t % len(stats_buf)],
+                true_res_every=true_res_every)
     torch.cuda.synchronize()
     for t in range(nsteps):
         if flush_buf is not None:
             flush_buf.zero_()
         starts[t].record()
         f.solve(sl[nwarm + t], c, st, args.max_iter, rtol=rtol, augmented=aug,
-                persistent=args.launch == "persistent", stats=stats_buf[t])
+                persistent=args.launch == "persistent", stats=stats_buf[t], true_res_every=true_res_every)
         ends[t].record()
     torch.cuda.synchronize()
     times = [starts[t].elapsed_time(ends[t]) for t in range(nsteps)]
@@ -209,7 +238,7 @@ def run_ours(args):
     import torch
 
     ws, rank, local = dist_setup(args)
-    from paper_2011_06842_gb300 import Fewha, build, workload
+    from paper_2011_06842_gb300 import Fewha, build, read_bandwidth, workload
     build.build()
     from synth import configs
     geom = configs.get(args.config)
@@ -245,44 +274,56 @@ def run_ours(args):
     # roofline of the dominant kernel (the persistent solver kernel; one launch per frame)
     word = 8 if args.precision == "f64" else 4
     mean_it = float(np.mean(iters))
-    algo_bytes = workload.solve_bytes(geom, mean_it, min(args.k, max(1, int(round(mean_it)))) if aug else 0,
-                                      word)
+    kv = min(args.k, max(1, int(round(mean_it)))) if aug else 0
+    algo_bytes = workload.reference_solve_bytes(geom, mean_it, args.k, word, augmented=aug)
+    impl_bytes = workload.solve_bytes(geom, mean_it, kv, word)
     achieved = algo_bytes / (us_frame * 1e-6) / 1e9
     peak, peak_kind = measured_peaks()
-    traffic = None
+    l2_peak = read_bandwidth(48 << 20)
+    traffic, l2_traffic = None, None
     tp = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tp):
         tj = json.load(open(tp))
         key = "%s/%s/%s" % (args.config, args.precision, "aug" if aug else "plain")
-        if tj.get("source_hash") == source_hash() and key in tj.get("per_launch", {}):
-            traffic = tj["per_launch"][key]
+        if tj.get("source_hash") == source_hash():
+            traffic = tj.get("per_launch", {}).get(key)
+            l2_traffic = tj.get("l2_per_launch", {}).get(key)
 
     out = {"metric": METRIC, "value": fps, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": us_frame / 1e3, "us_per_frame": us_frame,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": args.precision, "data": "synthetic: seeded von Karman frozen-flow screens "
            "(r0=%.3f m, L0=%.0f m, wind 5-20 m/s) seen by SH sensors, SNR %g" % (geom.r0, geom.L0, geom.snr),
-           "config": {"workload": workload_name(geom, args), "n_unknowns": geom.n_unknowns,
-                      "n_slopes": geom.n_slopes, "rtol": args.rtol, "max_iter": args.max_iter,
-                      "k_recycle": args.k, "launch": args.launch, "frames": nframes,
-                      "l2": "flushed (256 MB written) before every timed frame" if flush is not None
-                      else "not flushed", "parallelism": "replicas" if ws > 1 else "single GPU"},
+           "config": bench_config(geom, args, flush is not None),
+           "launch": dict(f.launch_info(), mode=args.launch),
            "iterations": {"mean": mean_it, "min": min(iters), "max": max(iters)},
            "rel_res": {"mean": float(np.mean(relres)), "max": float(np.max(relres))},
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                         "frac": achieved / peak, "traffic": traffic,
                         "kernel": "k_solve_persistent" if args.launch == "persistent" else "all phases",
-                        "algorithmic_bytes_per_launch": algo_bytes, "peak_source": peak_kind},
+                        "algorithmic_bytes_per_launch": algo_bytes,
+                        "algorithmic_count": "per iteration 14 n solver-vector words + the operator "
+                        "intermediates (nodal layers, forward wavefronts, slopes, adjoint wavefronts, adjoint "
+                        "layers) written once and read once; per time step + 1.5 operator-equivalents "
+                        "(right-hand side, initial projection) + 9 n k basis reads (augmented)",
+                        "impl_bytes_per_launch": impl_bytes,
+                        "impl_count": "what this kernel must move: the slopes stay in registers inside the "
+                        "fused WFS phase and z is never stored",
+                        "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs, copy)" % peak_kind,
+                        "l2": {"achieved": achieved, "peak": l2_peak, "unit": "GB/s", "frac": achieved / l2_peak,
+                               "peak_source": "measured: fewha_read_probe, 48 MB L2-resident buffer read 20 times in one launch",
+                               "traffic": l2_traffic}},
            "gpu_launches": args.steps * (1 if args.launch == "persistent" else 6 + 6 * args.max_iter)}
     if clocks:
         out["clocks"] = clocks
 
     if rank == 0:
-        out["e2e"] = run_e2e(f, geom, frames, sdt, args, aug)
+        out["e2e"] = run_e2e(f, geom, frames, sdt, args, aug, flush)
         out["algorithm3"] = run_algorithm3(f, frames, sdt, args, aug, flush)
         out["mcao_fit"] = run_mcao(f, geom, frames, sdt, args, aug, flush)
         if not args.no_compare:
-            out["compare"] = run_compare(geom, w, frames, args, stats_buf, flush)
+            out["compare"] = run_compare(geom, w, frames, args, stats_buf, flush,
+                                         (args.precision, aug, us_frame, mean_it))
         if not args.no_cpu and ws == 1:
             out["cpu_baseline"] = run_cpu_baseline(geom, w, frames, iters, args, aug)
         if not args.no_batched and args.precision == "f32":
@@ -293,24 +334,15 @@ def run_ours(args):
     return out if rank == 0 else None
 
 
-def launch_shape(cand):
-    """(rounds, CTAs of the launch) of a tuned batch candidate (ctas, rounds)."""
-    if not isinstance(cand, tuple):
-        return None
-    ctas, rounds = cand
-    per = {}
-    for n, r in zip(ctas, rounds):
-        per[r] = per.get(r, 0) + n
-    return [len(per), max(per.values())]
-
-
 def run_batched(args, flush):
     """64 independent instances of uneven size (24 x tiny, 24 x medium, 16 x ELT
     geometry, each with its own seeded frozen-flow sequence), FP32, augmented
-    PCG to the same relative residual, in ONE cooperative launch per step with
-    an autotuned split of the CTAs between instances (one round, or two or
-    three rounds: the ELT instances first on many CTAs each, then the small
-    instances on the same CTAs, separated by a barrier over the launch)."""
+    PCG to the same relative residual, in ONE cooperative launch per step.
+    The launch shape (CTA split, rounds, WFS tile and P^T band height per
+    geometry class) is chosen by the library's autotuner (autotune_batch);
+    the timed steps replay a CUDA graph of the bound launch (fewha_batch_bind
+    + fewha_batch_launch), each step's slopes copied into the bound buffers
+    and L2 flushed before it, outside its events."""
     import numpy as np
     import torch
     from paper_2011_06842_gb300 import Fewha, FewhaBatch, autotune_batch, workload
@@ -327,62 +359,64 @@ def run_batched(args, flush):
     fewhas = [x["f"] for x in inst]
     frame = [0]
 
-    def step(b, t=None):
-        t = frame[0] if t is None else t
+    def step(b):
+        t = frame[0]
         b.solve([x["s"][t] for x in inst], [x["c"] for x in inst], [x["st"] for x in inst],
                 args.max_iter, rtol=args.rtol, augmented=not args.plain)
         frame[0] = (t + 1) % 4  # the autotuner reuses the first frames
 
-    # candidates: one round (the library's work-proportional split); two
-    # rounds (the 16 ELT instances on 8-9 CTAs each, then the small ones); three
-    # rounds (8 ELT instances at a time on 18-19 CTAs each, enough for the
-    # split transforms, then the small ones)
-    two = [0 if k == "elt" else 1 for k in kinds]
-    elt_ids = [i for i, k in enumerate(kinds) if k == "elt"]
-    three = [(0 if elt_ids.index(i) < 8 else 1) if k == "elt" else 2 for i, k in enumerate(kinds)]
-
-    def split(elt, med, tiny):
-        return [elt if k == "elt" else med if k == "medium" else tiny for k in kinds]
-
-    cands = [None, (split(9, 4, 1), two), (split(9, 5, 1), two), (split(8, 5, 1), two),
-             (split(19, 4, 1), three), (split(18, 5, 1), three)]
-    best, timings = autotune_batch(fewhas, step, candidates=cands, reps=2)
+    best, timings = autotune_batch(fewhas, step, reps=2)
     for x in inst:  # fresh states after tuning
         x["st"] = x["f"].new_state(args.k)
         x["c"].zero_()
-    batch = FewhaBatch(fewhas, *best)
-    stats = [batch.new_stats() for _ in range(K)]
-    for t in range(W):
-        batch.solve([x["s"][4 + t] for x in inst], [x["c"] for x in inst], [x["st"] for x in inst],
-                    args.max_iter, rtol=args.rtol, augmented=not args.plain)
+    batch = FewhaBatch(fewhas, best["ctas"], best["rounds"], best["tiles"])
+    bound_s = [torch.empty_like(x["s"][0]) for x in inst]
+    stats = batch.bind(bound_s, [x["c"] for x in inst], [x["st"] for x in inst], args.max_iter, rtol=args.rtol,
+                       augmented=not args.plain)
+
+    def load(t):
+        for x, b in zip(inst, bound_s):
+            b.copy_(x["s"][t])
+
+    for t in range(W):  # warm-up through the bound launch
+        load(4 + t)
+        batch.launch()
+    graph = batch.capture_graph()
     torch.cuda.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    its, ok = [], True
     for t in range(K):
+        load(4 + W + t)
         if flush is not None:
             flush.zero_()
         ev[t][0].record()
-        batch.solve([x["s"][4 + W + t] for x in inst], [x["c"] for x in inst], [x["st"] for x in inst],
-                    args.max_iter, rtol=args.rtol, augmented=not args.plain, stats=stats[t])
+        graph.replay()
         ev[t][1].record()
+        rows = batch.read_stats(stats)  # synchronises, outside the events
+        ok = ok and all(r["status"] == 0 for r in rows)
+        its.append([r["iterations"] for r in rows])
     torch.cuda.synchronize()
     ms = sum(a.elapsed_time(b) for a, b in ev)
-    st = [batch.read_stats(x) for x in stats]
-    bad = [r for row in st for r in row if r["status"] != 0]
-    its = np.array([[r["iterations"] for r in row] for row in st])
-    algo = sum(workload.solve_bytes(x["geom"], float(its[:, i].mean()), args.k, 4) for i, x in enumerate(inst))
+    its = np.array(its)
+    algo = sum(workload.reference_solve_bytes(x["geom"], float(its[:, i].mean()), args.k, 4)
+               for i, x in enumerate(inst))
     us_step = ms / K * 1e3
     peak, _ = measured_peaks()
+    by_kind = {}
+    for i, k in enumerate(kinds):
+        by_kind.setdefault(k, {"ctas": best["ctas"][i], "round": best["rounds"][i] if best["rounds"] else 0,
+                               "wfs_tile": list(best["tiles"][i]), "pt_band_rows": list(best["bands"][i])})
     out = {"instances": len(inst), "mix": "24 x tiny (8 m, 16x16, 4 NGS, 2 x 32^2) + 24 x medium (16 m, 40x40, "
            "4 LGS, 5 x 64^2) + 16 x ELT (39 m, 84x84, 6 LGS, 9 layers)", "steps": K, "warmup": W,
-           "us_per_step": us_step, "instance_frames_per_s": len(inst) * K / (ms / 1e3),
+           "timed": "CUDA-graph replay of the bound batched launch", "us_per_step": us_step,
+           "instance_frames_per_s": len(inst) * K / (ms / 1e3),
            "elt_instance_frames_per_s": 16 * K / (ms / 1e3),
            "elt_equivalent_frames_per_s": sum(x["f"].n for x in inst) / inst[-1]["f"].n * K / (ms / 1e3),
-           "iterations_mean": float(its.mean()),
-           "ctas": batch.ctas(), "rounds": batch.rounds,
-           "autotune_ms_per_step": [[launch_shape(c), t] for c, t in timings],
-           "status_ok": not bad, "roofline": {"bound": "hbm", "achieved": algo / (us_step * 1e-6) / 1e9,
-                                             "peak": peak, "unit": "GB/s",
-                                             "frac": algo / (us_step * 1e-6) / 1e9 / peak},
+           "iterations_mean": float(its.mean()), "chosen": by_kind, "autotune_best_ms": best["ms"],
+           "autotune_candidates": len(timings),
+           "status_ok": ok, "roofline": {"bound": "hbm", "achieved": algo / (us_step * 1e-6) / 1e9,
+                                         "peak": peak, "unit": "GB/s",
+                                         "frac": algo / (us_step * 1e-6) / 1e9 / peak},
            "gpu_launches_per_step": 2}
     batch.close()
     for x in inst:
@@ -390,35 +424,41 @@ def run_batched(args, flush):
     return out
 
 
-def run_e2e(f, geom, frames, sdt, args, aug):
+def run_e2e(f, geom, frames, sdt, args, aug, flush):
     """Same metric through the public API with host buffers: per frame the
-    slopes are copied from pinned host memory and the solution c is read back."""
+    slopes are copied from pinned host memory and the solution c is read back
+    into pinned host memory, both inside the frame's timed window; L2 is
+    flushed before every frame (outside the window), as for `value`."""
     import torch
     K = args.steps
     host = frames[args.warmup:args.warmup + K].to(sdt).cpu().pin_memory()
+    warm = frames[:args.warmup].to(sdt).cpu().pin_memory()
     out_host = torch.empty((K, f.n), dtype=f.dtype).pin_memory()
     dev_s = torch.empty(f.n_slopes, dtype=sdt, device="cuda")
     c = torch.zeros(f.n, dtype=f.dtype, device="cuda")
     st = f.new_state(args.k)
     stats = f.new_stats()
-    for t in range(min(args.warmup, K)):
-        dev_s.copy_(host[t], non_blocking=True)
+    for t in range(args.warmup):
+        dev_s.copy_(warm[t], non_blocking=True)
         f.solve(dev_s, c, st, args.max_iter, rtol=args.rtol, augmented=aug,
                 persistent=args.launch == "persistent", stats=stats)
     torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
     for t in range(K):
+        if flush is not None:
+            flush.zero_()
+        ev[t][0].record()
         dev_s.copy_(host[t], non_blocking=True)
         f.solve(dev_s, c, st, args.max_iter, rtol=args.rtol, augmented=aug,
                 persistent=args.launch == "persistent", stats=stats)
         out_host[t].copy_(c, non_blocking=True)
-    e1.record()
+        ev[t][1].record()
     torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
+    ms = sum(a.elapsed_time(b) for a, b in ev)
     esz = torch.tensor([], dtype=sdt).element_size()
     return {"value": K / (ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": f.n_slopes * esz,
-            "d2h_bytes_per_step": f.n * c.element_size(), "us_per_frame": ms / K * 1e3}
+            "d2h_bytes_per_step": f.n * c.element_size(), "us_per_frame": ms / K * 1e3,
+            "l2": "flushed before every frame (outside the timed window), as for value"}
 
 
 def run_algorithm3(f, frames, sdt, args, aug, flush):
@@ -519,32 +559,80 @@ def run_mcao(f, geom, frames, sdt, args, aug, flush):
             "gpu_launches_per_fit": 2}
 
 
-def run_compare(geom, w, frames, args, stats_buf, flush):
-    """Plain PCG, the FP64 forms and the mixed-precision (BF16 storage) form on
-    the same frames and residual target."""
+def run_compare(geom, w, frames, args, stats_buf, flush, main):
+    """Plain PCG against augmented PCG on the same frames and residual target,
+    at the workload's SNR and at SNR 100 (where recycling saves iterations),
+    plus the FP64 forms, the mixed-precision (BF16 storage) form and the
+    residual replacement every 5 iterations.  `main` is the timed line's own
+    (precision, augmented, us per frame, mean iterations)."""
+    import copy
     import numpy as np
     import torch
     from paper_2011_06842_gb300 import Fewha
     K = min(args.steps, 60)
-    res = {}
-    for prec, aug in (("f32", False), ("f64", False), ("f64", True), ("f32", True), ("bf16s", True)):
-        if prec == args.precision and aug == (not args.plain):
-            continue
-        f = Fewha(geom, w, prec, tile=args.tile, grid=args.grid)
-        sdt = {"f64": torch.float64, "f32": torch.float32, "bf16s": torch.bfloat16}[prec]
-        times, stats = time_solves(f, frames, sdt, args, args.warmup, K, aug, flush, stats_buf, args.rtol)
+    sdts = {"f64": torch.float64, "f32": torch.float32, "bf16s": torch.bfloat16}
+
+    def one(g, wts, fr, prec, aug, tre=0):
+        f = Fewha(g, wts, prec, tile=args.tile, grid=args.grid)
+        a = copy.copy(args)
+        times, stats = time_solves(f, fr, sdts[prec], a, args.warmup, K, aug, flush, stats_buf, args.rtol,
+                                   true_res_every=tre)
         f.close()
-        it = [s["iterations"] for s in stats]
-        res["%s_%s" % ("aug" if aug else "plain", prec)] = {
-            "frames_per_s": K / (sum(times) / 1e3), "us_per_frame": sum(times) / K * 1e3,
-            "iterations_mean": float(np.mean(it)), "frames": K,
-            "status_ok": all(s["status"] == 0 for s in stats)}
+        it = [x["iterations"] for x in stats]
+        return {"us_per_frame": sum(times) / K * 1e3, "frames_per_s": K / (sum(times) / 1e3),
+                "iterations_mean": float(np.mean(it)), "frames": K,
+                "status_ok": all(x["status"] == 0 for x in stats)}
+
+    res = {}
+    snr0 = "snr%g" % geom.snr
+    res[snr0] = {}
+    for prec, aug, tre in (("f32", False, 0), ("f32", True, 0), ("f32", True, 5), ("f64", False, 0),
+                           ("f64", True, 0), ("bf16s", True, 0)):
+        key = "%s_%s%s" % ("aug" if aug else "plain", prec, "_true_res5" if tre else "")
+        if prec == main[0] and aug == main[1] and tre == 0:
+            res[snr0][key] = {"us_per_frame": main[2], "iterations_mean": main[3], "frames": args.steps,
+                              "note": "the timed line itself"}
+            continue
+        res[snr0][key] = one(geom, w, frames, prec, aug, tre)
+    g100 = copy.deepcopy(geom)
+    g100.snr = 100.0
+    fr100, w100 = make_frames(g100, args.warmup + K, seed=200, device="cuda")
+    res["snr100"] = {"plain_f32": one(g100, w100, fr100, "f32", False),
+                     "aug_f32": one(g100, w100, fr100, "f32", True)}
+    for snr, r in res.items():
+        if "plain_f32" in r and "aug_f32" in r:
+            r["aug_minus_plain_us"] = r["aug_f32"]["us_per_frame"] - r["plain_f32"]["us_per_frame"]
     return res
 
 
+def _oracle_worker(job):
+    """One host core: the FP64 oracle over the frames of one sequence
+    (independent of the other workers); returns (frames timed, seconds)."""
+    import time as _t
+    geom_name, snr, k, w, invJ, s, warm, iters, rtol, max_iter, aug = job
+    sys.path.insert(0, ROOT)
+    from oracle import Oracle
+    from synth import configs
+    geom = configs.get(geom_name)
+    geom.snr = snr
+    o = Oracle(geom, w, with_precond=False)
+    o.set_invJ(invJ)
+    st = o.new_state(k)
+    for t in range(warm):
+        o.solve(s[t], st, max_iter=max_iter, rtol=rtol, augmented=aug)
+    t0 = _t.perf_counter()
+    for t, it in enumerate(iters):
+        o.solve(s[warm + t], st, max_iter=it, rtol=0.0, augmented=aug)
+    return len(iters), _t.perf_counter() - t0
+
+
 def run_cpu_baseline(geom, w, frames, gpu_iters, args, aug):
-    """The FP64 oracle, single-threaded, on the first frames of the same sequence
-    with the same per-frame iteration counts as the GPU run."""
+    """The FP64 oracle as it stands on the same frames with the same per-frame
+    iteration counts as the GPU frames: single-threaded, and on all host
+    cores (one independent copy of the sequence per core, spawned processes:
+    whole-machine frames/s = frames of all workers / the slowest worker's
+    time)."""
+    import multiprocessing as mp
     import numpy as np
     from oracle import Oracle
     nf = max(1, min(args.cpu_frames, args.steps))
@@ -557,15 +645,28 @@ def run_cpu_baseline(geom, w, frames, gpu_iters, args, aug):
     for t in range(nf):
         o.solve(s[args.warmup + t], st, max_iter=gpu_iters[t], rtol=0.0, augmented=aug)
     dt = time.perf_counter() - t0
-    return {"value": nf / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "%d ELT frames after %d warm-up frames, FP64, same iteration counts as the GPU "
-                      "frames (%s)" % (nf, args.warmup, ",".join(str(i) for i in gpu_iters[:nf]))}
+    cores = os.cpu_count() or 1
+    job = (args.config, geom.snr, args.k, np.asarray(w), o.invJ(), s, args.warmup, list(gpu_iters[:nf]),
+           args.rtol, args.max_iter, aug)
+    all_cores = None
+    if cores > 1 and not args.no_cpu_all:
+        with mp.get_context("spawn").Pool(cores) as pool:
+            t1 = time.perf_counter()
+            parts = pool.map(_oracle_worker, [job] * cores)
+            wall = time.perf_counter() - t1
+        all_cores = {"value": sum(p[0] for p in parts) / max(p[1] for p in parts), "unit": UNIT,
+                     "cores": cores, "workers": cores, "pool_wall_s": wall}
+    model = cpu_model()
+    return {"value": nf / dt, "unit": UNIT, "cores": 1, "kind": "oracle", "cpu_model": model, "nproc": cores,
+            "sample": "%d ELT frames after %d warm-up frames, FP64, single-threaded, same iteration counts as "
+                      "the GPU frames (%s)" % (nf, args.warmup, ",".join(str(i) for i in gpu_iters[:nf])),
+            "all_cores": all_cores}
 
 
 def run_reference(args):
-    """Reference arm: the FP64 CPU oracle on the host cores (rank 0 only)."""
+    """Reference arm: the FP64 CPU oracle as it stands, single-threaded on a
+    host core (rank 0 only), one full frame of the same workload per step."""
     import numpy as np
-    import torch
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return None
@@ -575,6 +676,7 @@ def run_reference(args):
     geom = configs.get(args.config)
     if args.snr:
         geom.snr = args.snr
+    geom.k_recycle = args.k
     sim = FrozenFlowSensors(geom, seed=100)
     s, w = sim.sequence_chunked(args.warmup + args.steps, seed=101, dtype=torch_float64())
     s = s.numpy()
@@ -593,11 +695,13 @@ def run_reference(args):
     return {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic (same seeded frozen-flow workload)",
-            "config": {"workload": workload_name(geom, args) + " [FP64 CPU oracle]", "rtol": args.rtol},
+            "data": "synthetic: seeded von Karman frozen-flow screens (r0=%.3f m, L0=%.0f m, wind 5-20 m/s) "
+                    "seen by SH sensors, SNR %g" % (geom.r0, geom.L0, geom.snr),
+            "config": bench_config(geom, args, not args.no_flush),
             "iterations": {"mean": float(np.mean(its))},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": "%d full frames, one per step, single-threaded" % args.steps},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "cpu_model": cpu_model(),
+                             "sample": "%d full frames (FP64 oracle, its own stopping test), one per step, "
+                                       "single-threaded" % args.steps},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 

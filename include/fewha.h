@@ -187,8 +187,20 @@ typedef struct {
     int split_levels, staged_tables;
     int wfs_tile_y, wfs_tile_x;
     int pt_bands, pt_rows_chunk;
+    int pt_rows_large, pt_rows_small;  /* P^T band height on the largest / the smaller layers */
 } fewha_launch_info;
 int fewha_get_launch_info(const void *handle, fewha_launch_info *out);
+
+/* Height of the P_g^T gather's work items (bands of layer rows): rows_large
+ * on the layers of the largest grid, rows_small on the smaller ones (default
+ * 8 and 4); each is capped so that a band has at most 1024 layer nodes.
+ * Re-plans the band tables and the shared memory they need; FEWHA_ERR_GEOMETRY
+ * (and the earlier plan kept) when the staged rows do not fit.  Waits for the
+ * device to be idle (blocking); batches created before the call are refused
+ * by fewha_batch_solve / fewha_batch_bind when their shared memory no longer
+ * suffices.  A tuning knob (fewha autotuner); results do not depend on it
+ * beyond rounding order.  The paper has no counterpart. */
+int fewha_set_pt_bands(void *handle, int rows_large, int rows_small);
 
 /* Copies the diagonal of alpha*D (Sec. 3) or of J^{-1} (Sec. 4) to host memory (n doubles). */
 int fewha_get_prior(const void *handle, double *alpha_d_host);
@@ -262,7 +274,15 @@ int fewha_batch_create(void *const *handles, int n, const int *ctas, void **batc
  * instances can take many CTAs in one round and many small ones the next.
  * With ctas == NULL the CTAs of each round are split in proportion to work. */
 int fewha_batch_create_rounds(void *const *handles, int n, const int *ctas, const int *rounds, void **batch_out);
+/* Same, with the WFS tile of each instance fixed: tiles[2i], tiles[2i+1] =
+ * tile rows and columns in pupil nodes (4..64 each, within the shared
+ * memory of a CTA; FEWHA_ERR_ARG otherwise), or 0, 0 for the choice of
+ * fewha_batch_create for the instance's CTA count.  tiles may be NULL. */
+int fewha_batch_create_ex(void *const *handles, int n, const int *ctas, const int *rounds, const int *tiles,
+                          void **batch_out);
+/* CTAs and WFS tiles (2 ints per instance) of a batch. */
 int fewha_batch_ctas(const void *batch, int *ctas_out);
+int fewha_batch_tiles(const void *batch, int *tiles_out);
 int fewha_batch_solve(void *batch, const void *const *slopes, void *const *c, const fewha_state *states,
                       const fewha_solve_opts *opts, fewha_stats *stats_dev, cudaStream_t stream);
 void fewha_batch_destroy(void *batch);
@@ -420,6 +440,16 @@ void fewha_mcao_destroy(void *mcao);
  * x, y: device vectors of length n, 16-byte aligned, not overlapping. */
 #define FEWHA_NOALLOC_SCRATCH_BYTES (8u << 20)
 int fewha_apply_op_noalloc(void *handle, const void *x, void *y, cudaStream_t stream);
+
+/* Memory-bandwidth probe (measurement aid; the paper has no counterpart):
+ * one launch that reads the `bytes` of device buffer `buf` `reps` times over
+ * with 16-byte loads from 4 CTAs of 512 threads per SM, bypassing L1.  Timed
+ * by the caller (CUDA events on `stream`); a buffer that fits the
+ * L2 cache gives the L2 read bandwidth after the first pass, a larger one the
+ * DRAM read bandwidth.  bytes: a positive multiple of 16; buf 16-byte
+ * aligned; sink: device array of at least 4 x SMs floats (per-CTA sums, so
+ * that no load is dropped).  Asynchronous. */
+int fewha_read_probe(const void *buf, long bytes, int reps, float *sink, cudaStream_t stream);
 
 /* Text of a status code. */
 const char *fewha_strerror(int status);

@@ -8,4 +8,4 @@ libfewha.so in-tree; ``workload`` holds the paper's FLOP model and the
 algorithmic byte counts used for the roofline.
 """
 from .fewha import (Fewha, FewhaBatch, FewhaError, FewhaState, McaoFit, autotune_batch, exported_symbols,  # noqa: F401
-                    load_library, make_geometry)
+                    load_library, make_geometry, read_bandwidth)

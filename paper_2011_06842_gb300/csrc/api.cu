@@ -198,6 +198,14 @@ int fewha_get_launch_info(const void *handle, fewha_launch_info *out)
     return FEWHA_OK;
 }
 
+int fewha_set_pt_bands(void *handle, int rows_large, int rows_small)
+{
+    if (!handle || rows_large < 1 || rows_small < 1) return FEWHA_ERR_ARG;
+    Handle *h = static_cast<Handle *>(handle);
+    if (cudaSetDevice(h->device) != cudaSuccess) return FEWHA_ERR_CUDA;
+    return h->w()->set_bands(rows_large, rows_small);
+}
+
 int fewha_get_prior(const void *handle, double *out)
 {
     if (!handle || !out) return FEWHA_ERR_ARG;
@@ -332,6 +340,12 @@ int fewha_batch_create(void *const *handles, int n, const int *ctas, void **batc
 
 int fewha_batch_create_rounds(void *const *handles, int n, const int *ctas, const int *rounds, void **batch_out)
 {
+    return fewha_batch_create_ex(handles, n, ctas, rounds, nullptr, batch_out);
+}
+
+int fewha_batch_create_ex(void *const *handles, int n, const int *ctas, const int *rounds, const int *tiles,
+                          void **batch_out)
+{
     if (!handles || n < 1 || !batch_out) return FEWHA_ERR_ARG;
     *batch_out = nullptr;
     std::unique_ptr<Batch> b(new (std::nothrow) Batch());
@@ -394,7 +408,15 @@ int fewha_batch_create_rounds(void *const *handles, int n, const int *ctas, cons
     for (int i = 0; i < n; i++) {
         b->cta0[i] = used[round[i]];
         used[round[i]] += b->ncta[i];
-        if ((st = b->impl[i]->tiles_for(b->ncta[i], &b->ty[i], &b->tx[i]))) return st;
+        if (tiles && (tiles[2 * i] || tiles[2 * i + 1])) {
+            b->ty[i] = tiles[2 * i];
+            b->tx[i] = tiles[2 * i + 1];
+            if (b->ty[i] < 4 || b->ty[i] > 64 || b->tx[i] < 4 || b->tx[i] > 64 ||
+                b->impl[i]->smem_for(b->ty[i], b->tx[i]) > 200 * 1024)
+                return FEWHA_ERR_ARG;
+        } else if ((st = b->impl[i]->tiles_for(b->ncta[i], &b->ty[i], &b->tx[i]))) {
+            return st;
+        }
         b->smem = std::max(b->smem, b->impl[i]->smem_for(b->ty[i], b->tx[i]));
     }
     b->total = *std::max_element(used.begin(), used.end());
@@ -427,6 +449,17 @@ int fewha_batch_ctas(const void *batch, int *ctas_out)
     return FEWHA_OK;
 }
 
+int fewha_batch_tiles(const void *batch, int *tiles_out)
+{
+    if (!batch || !tiles_out) return FEWHA_ERR_ARG;
+    const Batch *b = static_cast<const Batch *>(batch);
+    for (int i = 0; i < b->n; i++) {
+        tiles_out[2 * i] = b->ty[i];
+        tiles_out[2 * i + 1] = b->tx[i];
+    }
+    return FEWHA_OK;
+}
+
 int fewha_batch_solve(void *batch, const void *const *slopes, void *const *c, const fewha_state *states,
                       const fewha_solve_opts *opts, fewha_stats *stats_dev, cudaStream_t stream)
 {
@@ -444,6 +477,7 @@ int fewha_batch_solve(void *batch, const void *const *slopes, void *const *c, co
         if (!slopes[i] || !c[i] || !st->b_prev || !st->r_prev || !st->basis_P || !st->basis_Q || !st->basis_pq ||
             !st->meta || st->k_cap < 1 || st->k_cap > FEWHA_MAX_K)
             return FEWHA_ERR_ARG;
+        if (b->impl[i]->smem_for(b->ty[i], b->tx[i]) > b->smem) return FEWHA_ERR_ARG;  // re-planned since
         if (!aligned16(c[i]) || !aligned16(st->b_prev) || !aligned16(st->r_prev) || !aligned16(st->basis_P) ||
             !aligned16(st->basis_Q))
             return FEWHA_ERR_ARG;
@@ -472,6 +506,7 @@ int fewha_batch_bind(void *batch, const void *const *slopes, void *const *c, con
         if (!slopes[i] || !c[i] || !st->b_prev || !st->r_prev || !st->basis_P || !st->basis_Q || !st->basis_pq ||
             !st->meta || st->k_cap < 1 || st->k_cap > FEWHA_MAX_K)
             return FEWHA_ERR_ARG;
+        if (b->impl[i]->smem_for(b->ty[i], b->tx[i]) > b->smem) return FEWHA_ERR_ARG;  // re-planned since
         if (!aligned16(c[i]) || !aligned16(st->b_prev) || !aligned16(st->r_prev) || !aligned16(st->basis_P) ||
             !aligned16(st->basis_Q))
             return FEWHA_ERR_ARG;
@@ -492,6 +527,8 @@ int fewha_batch_launch(void *batch, cudaStream_t stream)
     if (!batch) return FEWHA_ERR_ARG;
     Batch *b = static_cast<Batch *>(batch);
     if (!b->bound) return FEWHA_ERR_ARG;
+    for (int i = 0; i < b->n; i++)
+        if (b->impl[i]->smem_for(b->ty[i], b->tx[i]) > b->smem) return FEWHA_ERR_ARG;  // re-planned since
     return b->impl[0]->launch_batched(b->d_bound, b->d_map, b->n, b->total, b->smem, b->nrounds, b->d_brec,
                                       b->bound_true_res, stream);
 }

@@ -598,6 +598,8 @@ struct ImplBase {
     // memory (no allocation); FEWHA_ERR_SCRATCH if `bytes` is too small.
     virtual int apply_in_scratch(const void *x, void *y, void *scratch, size_t bytes, cudaStream_t s) = 0;
     virtual void launch_info(fewha_launch_info *out) const = 0;
+    // P^T band heights (layer rows) on the largest and on the smaller layers
+    virtual int set_bands(int rows_large, int rows_small) = 0;
 };
 
 template <typename T, typename S>
@@ -613,6 +615,10 @@ struct Impl : ImplBase {
     size_t multi_stride = 0;
 
     size_t sm_fixed = 0;  // dynamic shared memory of every phase but the WFS tiles
+    size_t sm_base = 0;   // of the layer and WFS phases alone (before the P^T bands)
+    size_t sm_layer_ = 0; // of the layer phases alone
+    std::vector<void *> band_owned;  // device tables of the P^T bands (replaced by plan_bands)
+    int band_rows_large = 0, band_rows_small = 0;
 
     explicit Impl(const Plan &p) : P(p) {}
 
@@ -656,6 +662,7 @@ struct Impl : ImplBase {
     ~Impl() override
     {
         for (void *q : owned) cudaFree(q);
+        for (void *q : band_owned) cudaFree(q);
     }
 
     template <typename U>
@@ -668,11 +675,167 @@ struct Impl : ImplBase {
         return st;
     }
     template <typename U>
+    int upb(const std::vector<U> &v, const U **d)  // a P^T band table (replaced by plan_bands)
+    {
+        U *dd;
+        int st = upload(v, &dd);
+        if (dd) band_owned.push_back(dd);
+        *d = dd;
+        return st;
+    }
+    template <typename U>
     int alloc(size_t count, U **d)
     {
         if (cudaMalloc(d, count * sizeof(U)) != cudaSuccess) return FEWHA_ERR_NOMEM;
         owned.push_back(*d);
         CK(cudaMemset(*d, 0, count * sizeof(U)));
+        return FEWHA_OK;
+    }
+
+    // P^T work items and their tables: bands of rows_large layer rows on the
+    // largest layers and rows_small on the smaller ones (at most kBandOutputs
+    // outputs each); with the staging groups, tap lists and the shared memory
+    // they need.  Replaces the tables of an earlier call.
+    int plan_bands(int rows_large, int rows_small)
+    {
+        if (rows_large < 1 || rows_small < 1) return FEWHA_ERR_ARG;
+        Geo<T> &G = base.geo;
+        int st;
+        int nmax = 0;
+        for (int l = 0; l < P.L; l++) nmax = std::max(nmax, P.geom.layers[l].n);
+        for (void *q : band_owned) cudaFree(q);
+        band_owned.clear();
+        // bands of BR rows with BR * n_l <= kBandOutputs outputs; by default 8
+        // rows on the largest layers and 4 on the smaller ones (their coarser
+        // grid touches about twice as many pupil rows per layer row, so a
+        // half-height band balances the staged work)
+        std::vector<int> bl, br0, brs;
+        int n_largest = 0;
+        for (int l = 0; l < P.L; l++) n_largest = std::max(n_largest, P.geom.layers[l].n);
+        for (int l = 0; l < P.L; l++) {
+            const int n = P.geom.layers[l].n;
+            int BR = std::max(1, std::min(n, std::min(kBandOutputs / n, n < n_largest ? rows_small : rows_large)));
+            for (int a0 = 0; a0 < n; a0 += BR) {
+                bl.push_back(l);
+                br0.push_back(a0);
+                brs.push_back(std::min(BR, n - a0));
+            }
+        }
+        G.nbands = (int)bl.size();
+        std::vector<int> bilo((size_t)P.G * G.nbands), bihi((size_t)P.G * G.nbands);
+        int max_rows = 1, max_rows_sum = 1;
+        std::vector<int> rows_sum(G.nbands, 0);
+        for (int g = 0; g < P.G; g++)
+            for (int w = 0; w < G.nbands; w++) {
+                int lo = P.m, hi = 0;
+                size_t by = ((size_t)g * P.L + bl[w]) * 2 + 1;
+                for (int a = br0[w]; a < br0[w] + brs[w]; a++) {
+                    int alo = P.alo[by * FEWHA_MAX_GRID + a], ahi = P.ahi[by * FEWHA_MAX_GRID + a];
+                    if (alo < ahi) {
+                        lo = std::min(lo, alo);
+                        hi = std::max(hi, ahi);
+                    }
+                }
+                if (lo >= hi) lo = hi = 0;
+                bilo[(size_t)g * G.nbands + w] = lo;
+                bihi[(size_t)g * G.nbands + w] = hi;
+                max_rows = std::max(max_rows, hi - lo);
+                rows_sum[w] += hi - lo;
+                max_rows_sum = std::max(max_rows_sum, rows_sum[w]);
+            }
+        if ((st = upb(bl, &G.band_layer)) || (st = upb(br0, &G.band_row0)) || (st = upb(brs, &G.band_rows)) ||
+            (st = upb(bilo, &G.band_ilo)) || (st = upb(bihi, &G.band_ihi)))
+            return st;
+        // band_gather stages rows_chunk psi rows and their x-contraction
+        // (all guide stars of a band at once when they fit, else in groups)
+        const size_t row_bytes = (size_t)(P.m + nmax) * sizeof(T);
+        const size_t smem_cap = 200 * 1024;  // 227 KB per CTA minus the static shared memory
+        size_t smem = sm_base;
+        size_t want = (size_t)max_rows_sum * row_bytes;
+        if (want > smem) smem = std::min(want, smem_cap);
+        G.rows_chunk = (int)std::min<size_t>(max_rows_sum, smem / row_bytes);
+        if (smem > smem_cap || G.rows_chunk < max_rows) return FEWHA_ERR_GEOMETRY;
+        {
+            // guide stars of each band in groups of consecutive guide stars whose
+            // pupil rows fit rows_chunk staged rows
+            std::vector<int> gend((size_t)P.G * G.nbands), gc((size_t)P.G * G.nbands);
+            for (int w = 0; w < G.nbands; w++)
+                for (int g0 = 0, g1; g0 < P.G; g0 = g1) {
+                    int rows_tot = 0;
+                    for (g1 = g0; g1 < P.G; g1++) {
+                        const size_t i = (size_t)g1 * G.nbands + w;
+                        if (rows_tot + bihi[i] - bilo[i] > G.rows_chunk) break;
+                        rows_tot += bihi[i] - bilo[i];
+                    }
+                    if (g1 == g0) return FEWHA_ERR_GEOMETRY;  // rows_chunk >= max_rows
+                    for (int g = g0, c = 0; g < g1; g++) {
+                        const size_t i = (size_t)g * G.nbands + w;
+                        gend[i] = g1;
+                        gc[i] = c;
+                        c += (bihi[i] - bilo[i]) * P.m;
+                    }
+                }
+            if ((st = upb(gend, &G.band_gend)) || (st = upb(gc, &G.band_gc))) return st;
+            // y-contraction lists: for band row r of band w and the group that
+            // starts at g0, the staged row (gc/m + pupil row - ilo) and weight of
+            // each tap, guide star after guide star
+            int ybr = 1, ymax = 1;
+            for (int w = 0; w < G.nbands; w++) ybr = std::max(ybr, brs[w]);
+            auto ytaps = [&](int w, int g, int r, std::vector<std::pair<int, double>> *out) {
+                const size_t t = ((size_t)g * P.L + bl[w]) * 2 + 1;
+                const int a = br0[w] + r, lo = P.alo[t * FEWHA_MAX_GRID + a], hi = P.ahi[t * FEWHA_MAX_GRID + a];
+                const size_t i = (size_t)g * G.nbands + w;
+                int cnt = 0;
+                for (int j = lo; j < hi; j++, cnt++) {
+                    if (!out) continue;
+                    const double w0 = P.fw[t * P.m + j];
+                    out->push_back({gc[i] / P.m + (j - bilo[i]), P.fk[t * P.m + j] == a ? 1.0 - w0 : w0});
+                }
+                return cnt;
+            };
+            for (int w = 0; w < G.nbands; w++)
+                for (int g0 = 0; g0 < P.G; g0 = gend[(size_t)g0 * G.nbands + w])
+                    for (int r = 0; r < brs[w]; r++) {
+                        int c = 0;
+                        for (int g = g0; g < gend[(size_t)g0 * G.nbands + w]; g++) c += ytaps(w, g, r, nullptr);
+                        ymax = std::max(ymax, c);
+                    }
+            std::vector<int> ycnt((size_t)G.nbands * P.G * ybr, 0), yrow(ycnt.size() * ymax, 0);
+            std::vector<T> yw(ycnt.size() * ymax, T(0));
+            for (int w = 0; w < G.nbands; w++)
+                for (int g0 = 0; g0 < P.G; g0 = gend[(size_t)g0 * G.nbands + w])
+                    for (int r = 0; r < brs[w]; r++) {
+                        std::vector<std::pair<int, double>> taps;
+                        for (int g = g0; g < gend[(size_t)g0 * G.nbands + w]; g++) ytaps(w, g, r, &taps);
+                        const size_t e = ((size_t)w * P.G + g0) * ybr + r;
+                        ycnt[e] = (int)taps.size();
+                        for (size_t t = 0; t < taps.size(); t++) {
+                            yrow[e * ymax + t] = taps[t].first;
+                            yw[e * ymax + t] = (T)taps[t].second;
+                        }
+                    }
+            G.ybr = ybr;
+            G.ymax = ymax;
+            if ((st = upb(ycnt, &G.band_ycnt)) || (st = upb(yrow, &G.band_yrow)) || (st = upb(yw, &G.band_yw)))
+                return st;
+        }
+        size_t sm_fixed = std::max(sm_layer_, std::min(want, smem_cap));
+        // P^T x weight tables of one band (all guide stars) staged beside the
+        // psi rows when kTabPT entries per thread and the shared memory suffice
+        const size_t tab_entries = (size_t)P.G * nmax;
+        const size_t tab_bytes = tab_entries * (kAdjW * sizeof(T) + 2 * sizeof(int));
+        const size_t gather_bytes = (size_t)G.rows_chunk * row_bytes + tab_bytes;
+        G.stage_tab = 0;
+        if (tab_entries <= (size_t)kTabPT * kThreads && gather_bytes <= smem_cap) {
+            G.stage_tab = 1;
+            smem = std::max(smem, gather_bytes);
+            sm_fixed = std::max(sm_fixed, gather_bytes);
+        }
+        this->smem = smem;
+        this->sm_fixed = sm_fixed;
+        base.smem_bytes = smem;
+        band_rows_large = rows_large;
+        band_rows_small = rows_small;
         return FEWHA_OK;
     }
 
@@ -718,46 +881,11 @@ struct Impl : ImplBase {
         if ((st = up(fw, &G.fw)) || (st = up(weight_table(), &G.wmask)) || (st = up(ad, &G.alpha_d)) ||
             (st = up(one, &G.invJ)))
             return st;
-        // P^T work items: bands of rows with band_rows * n_l <= kBandOutputs outputs;
-        // 8 rows, and 4 rows on layers smaller than the largest (their coarser
-        // grid touches about twice as many pupil rows per layer row, so a
-        // half-height band balances the staged work)
-        std::vector<int> bl, br0, brs;
-        int n_largest = 0;
-        for (int l = 0; l < P.L; l++) n_largest = std::max(n_largest, P.geom.layers[l].n);
         for (int l = 0; l < P.L; l++) {
-            int n = P.geom.layers[l].n, lg = 0;
-            while ((1 << lg) < n) lg++;
+            int lg = 0;
+            while ((1 << lg) < P.geom.layers[l].n) lg++;
             G.lay_lg[l] = lg;
-            int BR = std::max(1, std::min(n, std::min(kBandOutputs / n, n < n_largest ? 4 : 8)));
-            for (int a0 = 0; a0 < n; a0 += BR) {
-                bl.push_back(l);
-                br0.push_back(a0);
-                brs.push_back(std::min(BR, n - a0));
-            }
         }
-        G.nbands = (int)bl.size();
-        std::vector<int> bilo((size_t)P.G * G.nbands), bihi((size_t)P.G * G.nbands);
-        int max_rows = 1, max_rows_sum = 1;
-        std::vector<int> rows_sum(G.nbands, 0);
-        for (int g = 0; g < P.G; g++)
-            for (int w = 0; w < G.nbands; w++) {
-                int lo = P.m, hi = 0;
-                size_t by = ((size_t)g * P.L + bl[w]) * 2 + 1;
-                for (int a = br0[w]; a < br0[w] + brs[w]; a++) {
-                    int alo = P.alo[by * FEWHA_MAX_GRID + a], ahi = P.ahi[by * FEWHA_MAX_GRID + a];
-                    if (alo < ahi) {
-                        lo = std::min(lo, alo);
-                        hi = std::max(hi, ahi);
-                    }
-                }
-                if (lo >= hi) lo = hi = 0;
-                bilo[(size_t)g * G.nbands + w] = lo;
-                bihi[(size_t)g * G.nbands + w] = hi;
-                max_rows = std::max(max_rows, hi - lo);
-                rows_sum[w] += hi - lo;
-                max_rows_sum = std::max(max_rows_sum, rows_sum[w]);
-            }
         // compact P_g^T weights: per layer node, its pupil-node range and weights
         {
             size_t nt = (size_t)P.G * P.L * 2 * FEWHA_MAX_GRID;
@@ -781,9 +909,6 @@ struct Impl : ImplBase {
                 if ((st = up(P.fit_k, &fit_k)) || (st = up(fw2, &fit_w))) return st;
             }
         }
-        if ((st = up(bl, &G.band_layer)) || (st = up(br0, &G.band_row0)) || (st = up(brs, &G.band_rows)) ||
-            (st = up(bilo, &G.band_ilo)) || (st = up(bihi, &G.band_ihi)))
-            return st;
         if ((st = alloc((size_t)P.n, &base.nodal)) || (st = alloc((size_t)P.n, &base.u)) ||
             (st = alloc((size_t)P.n, &base.wq)) ||
             (st = alloc((size_t)P.G * P.m * P.m, &base.psi)) || (st = alloc((size_t)P.n / 4 + 1, &base.ll)) ||
@@ -816,95 +941,15 @@ struct Impl : ImplBase {
         }
         sm_layer = std::max(sm_layer, sm_fine);
         smem = std::max(sm_layer, sm_wfs);
-        // band_gather stages rows_chunk psi rows and their x-contraction
-        // (all guide stars of a band at once when they fit, else in groups)
-        const size_t row_bytes = (size_t)(P.m + nmax) * sizeof(T);
-        const size_t smem_cap = 200 * 1024;  // 227 KB per CTA minus the static shared memory
-        size_t want = (size_t)max_rows_sum * row_bytes;
-        if (want > smem) smem = std::min(want, smem_cap);
-        G.rows_chunk = (int)std::min<size_t>(max_rows_sum, smem / row_bytes);
-        if (smem > smem_cap || G.rows_chunk < max_rows) return FEWHA_ERR_GEOMETRY;
-        {
-            // guide stars of each band in groups of consecutive guide stars whose
-            // pupil rows fit rows_chunk staged rows
-            std::vector<int> gend((size_t)P.G * G.nbands), gc((size_t)P.G * G.nbands);
-            for (int w = 0; w < G.nbands; w++)
-                for (int g0 = 0, g1; g0 < P.G; g0 = g1) {
-                    int rows_tot = 0;
-                    for (g1 = g0; g1 < P.G; g1++) {
-                        const size_t i = (size_t)g1 * G.nbands + w;
-                        if (rows_tot + bihi[i] - bilo[i] > G.rows_chunk) break;
-                        rows_tot += bihi[i] - bilo[i];
-                    }
-                    if (g1 == g0) return FEWHA_ERR_GEOMETRY;  // rows_chunk >= max_rows
-                    for (int g = g0, c = 0; g < g1; g++) {
-                        const size_t i = (size_t)g * G.nbands + w;
-                        gend[i] = g1;
-                        gc[i] = c;
-                        c += (bihi[i] - bilo[i]) * P.m;
-                    }
-                }
-            if ((st = up(gend, &G.band_gend)) || (st = up(gc, &G.band_gc))) return st;
-            // y-contraction lists: for band row r of band w and the group that
-            // starts at g0, the staged row (gc/m + pupil row - ilo) and weight of
-            // each tap, guide star after guide star
-            int ybr = 1, ymax = 1;
-            for (int w = 0; w < G.nbands; w++) ybr = std::max(ybr, brs[w]);
-            auto ytaps = [&](int w, int g, int r, std::vector<std::pair<int, double>> *out) {
-                const size_t t = ((size_t)g * P.L + bl[w]) * 2 + 1;
-                const int a = br0[w] + r, lo = P.alo[t * FEWHA_MAX_GRID + a], hi = P.ahi[t * FEWHA_MAX_GRID + a];
-                const size_t i = (size_t)g * G.nbands + w;
-                int cnt = 0;
-                for (int j = lo; j < hi; j++, cnt++) {
-                    if (!out) continue;
-                    const double w0 = P.fw[t * P.m + j];
-                    out->push_back({gc[i] / P.m + (j - bilo[i]), P.fk[t * P.m + j] == a ? 1.0 - w0 : w0});
-                }
-                return cnt;
-            };
-            for (int w = 0; w < G.nbands; w++)
-                for (int g0 = 0; g0 < P.G; g0 = gend[(size_t)g0 * G.nbands + w])
-                    for (int r = 0; r < brs[w]; r++) {
-                        int c = 0;
-                        for (int g = g0; g < gend[(size_t)g0 * G.nbands + w]; g++) c += ytaps(w, g, r, nullptr);
-                        ymax = std::max(ymax, c);
-                    }
-            std::vector<int> ycnt((size_t)G.nbands * P.G * ybr, 0), yrow(ycnt.size() * ymax, 0);
-            std::vector<T> yw(ycnt.size() * ymax, T(0));
-            for (int w = 0; w < G.nbands; w++)
-                for (int g0 = 0; g0 < P.G; g0 = gend[(size_t)g0 * G.nbands + w])
-                    for (int r = 0; r < brs[w]; r++) {
-                        std::vector<std::pair<int, double>> taps;
-                        for (int g = g0; g < gend[(size_t)g0 * G.nbands + w]; g++) ytaps(w, g, r, &taps);
-                        const size_t e = ((size_t)w * P.G + g0) * ybr + r;
-                        ycnt[e] = (int)taps.size();
-                        for (size_t t = 0; t < taps.size(); t++) {
-                            yrow[e * ymax + t] = taps[t].first;
-                            yw[e * ymax + t] = (T)taps[t].second;
-                        }
-                    }
-            G.ybr = ybr;
-            G.ymax = ymax;
-            if ((st = up(ycnt, &G.band_ycnt)) || (st = up(yrow, &G.band_yrow)) || (st = up(yw, &G.band_yw)))
-                return st;
-        }
-        sm_fixed = std::max(sm_layer, std::min(want, smem_cap));
-        // P^T x weight tables of one band (all guide stars) staged beside the
-        // psi rows when kTabPT entries per thread and the shared memory suffice
-        const size_t tab_entries = (size_t)P.G * nmax;
-        const size_t tab_bytes = tab_entries * (kAdjW * sizeof(T) + 2 * sizeof(int));
-        const size_t gather_bytes = (size_t)G.rows_chunk * row_bytes + tab_bytes;
-        G.stage_tab = 0;
-        if (tab_entries <= (size_t)kTabPT * kThreads && gather_bytes <= smem_cap) {
-            G.stage_tab = 1;
-            smem = std::max(smem, gather_bytes);
-            sm_fixed = std::max(sm_fixed, gather_bytes);
-        }
+        sm_base = smem;
+        sm_layer_ = sm_layer;
+        if ((st = plan_bands(8, 4))) return st;
         int dev, nsm;
         CK(cudaGetDevice(&dev));
         CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+        // the attribute allows the cap, so that plan_bands may change smem later
         auto setattr = [&](const void *f) {
-            return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         };
         CK(setattr((const void *)k_apply_idwt<T, S>));
         CK(setattr((const void *)k_wfs<T, S, false>));
@@ -959,6 +1004,19 @@ struct Impl : ImplBase {
         return FEWHA_OK;
     }
 
+    int set_bands(int rows_large, int rows_small) override
+    {
+        if (rows_large < 1 || rows_small < 1) return FEWHA_ERR_ARG;
+        CK(cudaDeviceSynchronize());  // the tables may be in use
+        const int ol = band_rows_large, os = band_rows_small;
+        int st = plan_bands(rows_large, rows_small);
+        if (st != FEWHA_OK) {
+            plan_bands(ol, os);  // keep the earlier plan
+            return st;
+        }
+        return FEWHA_OK;
+    }
+
     void launch_info(fewha_launch_info *out) const override
     {
         out->ctas = ncta;
@@ -970,6 +1028,8 @@ struct Impl : ImplBase {
         out->wfs_tile_x = base.geo.tile_x;
         out->pt_bands = base.geo.nbands;
         out->pt_rows_chunk = base.geo.rows_chunk;
+        out->pt_rows_large = band_rows_large;
+        out->pt_rows_small = band_rows_small;
     }
 
     int get_invJ(double *host) const override

@@ -61,7 +61,8 @@ class OPTS(C.Structure):
 class LAUNCH_INFO(C.Structure):
     _fields_ = [("ctas", C.c_int), ("threads", C.c_int), ("smem_bytes", C.c_long),
                 ("split_levels", C.c_int), ("staged_tables", C.c_int), ("wfs_tile_y", C.c_int),
-                ("wfs_tile_x", C.c_int), ("pt_bands", C.c_int), ("pt_rows_chunk", C.c_int)]
+                ("wfs_tile_x", C.c_int), ("pt_bands", C.c_int), ("pt_rows_chunk", C.c_int),
+                ("pt_rows_large", C.c_int), ("pt_rows_small", C.c_int)]
 
 
 class STATS(C.Structure):
@@ -93,6 +94,10 @@ def load_library(path=LIB_PATH):
     lib.fewha_n_slopes.restype = C.c_long
     lib.fewha_layer_spacing.argtypes = [vp, C.c_int]
     lib.fewha_layer_spacing.restype = C.c_double
+    lib.fewha_read_probe.argtypes = [vp, C.c_long, C.c_int, vp, vp]
+    lib.fewha_read_probe.restype = C.c_int
+    lib.fewha_set_pt_bands.argtypes = [vp, C.c_int, C.c_int]
+    lib.fewha_set_pt_bands.restype = C.c_int
     lib.fewha_set_noise.argtypes = [vp, dp, C.c_int]
     lib.fewha_set_noise.restype = C.c_int
     lib.fewha_get_launch_info.argtypes = [vp, C.POINTER(LAUNCH_INFO)]
@@ -115,6 +120,11 @@ def load_library(path=LIB_PATH):
     lib.fewha_batch_create_rounds.restype = C.c_int
     lib.fewha_batch_ctas.argtypes = [vp, C.POINTER(C.c_int)]
     lib.fewha_batch_ctas.restype = C.c_int
+    lib.fewha_batch_tiles.argtypes = [vp, C.POINTER(C.c_int)]
+    lib.fewha_batch_tiles.restype = C.c_int
+    lib.fewha_batch_create_ex.argtypes = [C.POINTER(vp), C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                          C.POINTER(C.c_int), C.POINTER(vp)]
+    lib.fewha_batch_create_ex.restype = C.c_int
     lib.fewha_batch_solve.argtypes = [vp, C.POINTER(vp), C.POINTER(vp), C.POINTER(STATE), C.POINTER(OPTS), vp, vp]
     lib.fewha_batch_solve.restype = C.c_int
     lib.fewha_batch_bind.argtypes = [vp, C.POINTER(vp), C.POINTER(vp), C.POINTER(STATE), C.POINTER(OPTS), vp]
@@ -180,7 +190,8 @@ def exported_symbols():
             "fewha_conv3x3_wgrad_workspace", "fewha_conv3x3_bwd_weight", "fewha_relu_bwd",
             "fewha_mse_grad", "fewha_adam_step", "fewha_scale", "fewha_learned_targets",
             "fewha_deflate_warm_start", "fewha_mcao_create", "fewha_mcao_n_actuators", "fewha_mcao_fit",
-            "fewha_mcao_destroy", "fewha_get_launch_info", "fewha_set_noise"]
+            "fewha_mcao_destroy", "fewha_get_launch_info", "fewha_set_noise", "fewha_read_probe", "fewha_set_pt_bands",
+            "fewha_batch_create_ex", "fewha_batch_tiles"]
 
 
 def make_geometry(geom, noise_w, precision="f64", tile=0, grid=0) -> GEOMETRY:
@@ -279,6 +290,10 @@ class Fewha:
             raise ValueError("one weight per guide star")
         self._check(self.lib.fewha_set_noise(self._h, w.ctypes.data_as(C.POINTER(C.c_double)),
                                               1 if refresh_precond else 0), "fewha_set_noise")
+
+    def set_pt_bands(self, rows_large, rows_small):
+        """P^T gather band heights (layer rows) on the largest / smaller layers."""
+        self._check(self.lib.fewha_set_pt_bands(self._h, int(rows_large), int(rows_small)), "fewha_set_pt_bands")
 
     def launch_info(self):
         """Launch shape chosen at creation (fewha_get_launch_info) as a dict."""
@@ -498,7 +513,7 @@ class FewhaBatch:
     """Many instances (Fewha handles of one precision) solved by one
     cooperative launch, each by its own group of CTAs (fewha_batch_*)."""
 
-    def __init__(self, fewhas, ctas=None, rounds=None):
+    def __init__(self, fewhas, ctas=None, rounds=None, tiles=None):
         import torch
         self._torch = torch
         self.fewhas = list(fewhas)
@@ -507,11 +522,12 @@ class FewhaBatch:
         hs = (C.c_void_p * n)(*[f._h.value for f in self.fewhas])
         cs = (C.c_int * n)(*ctas) if ctas is not None else None
         rs = (C.c_int * n)(*rounds) if rounds is not None else None
+        ts = (C.c_int * (2 * n))(*[v for t in tiles for v in (t or (0, 0))]) if tiles is not None else None
         self.rounds = list(rounds) if rounds is not None else [0] * n
         b = C.c_void_p()
-        st = self.lib.fewha_batch_create_rounds(hs, n, cs, rs, C.byref(b))
+        st = self.lib.fewha_batch_create_ex(hs, n, cs, rs, ts, C.byref(b))
         if st != 0:
-            raise FewhaError(st, "fewha_batch_create_rounds")
+            raise FewhaError(st, "fewha_batch_create_ex")
         self._b = b
         self.n = n
         self.device = self.fewhas[0].device
@@ -520,6 +536,11 @@ class FewhaBatch:
         out = (C.c_int * self.n)()
         self.lib.fewha_batch_ctas(self._b, out)
         return list(out)
+
+    def tiles(self):
+        out = (C.c_int * (2 * self.n))()
+        self.lib.fewha_batch_tiles(self._b, out)
+        return [(out[2 * i], out[2 * i + 1]) for i in range(self.n)]
 
     def new_stats(self):
         return self._torch.zeros(self.n * STATS_BYTES, dtype=self._torch.uint8, device=self.device)
@@ -601,41 +622,152 @@ class FewhaBatch:
             pass
 
 
-def autotune_batch(fewhas, step, candidates=None, reps=3):
-    """Chooses the CTA groups (and rounds) of a batch by timing: `step(batch)`
-    runs one batched time step; each candidate (None = the library's work-
-    proportional default, a list of CTAs per instance, or a pair (ctas,
-    rounds)) is timed over `reps` steps with CUDA events.  Returns the fastest
-    as a pair (ctas, rounds) and all timings (ms per step)."""
+def _split(cap, work):
+    """CTAs for instances of the given work filling `cap` CTAs in proportion
+    to work, at least one each (cap >= number of instances)."""
+    tot = float(sum(work))
+    c = [max(1, int(cap * w / tot)) for w in work]
+    while sum(c) > cap:
+        c[max(range(len(c)), key=lambda i: c[i])] -= 1
+    while sum(c) < cap:
+        c[max(range(len(c)), key=lambda i: work[i] / c[i])] += 1
+    return c
+
+
+def _time_batch(batch, step, reps):
+    """ms per batched time step of `step(batch)` over reps steps (after one)."""
+    import torch
+    step(batch)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        step(batch)
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def autotune_batch(fewhas, step, candidates=None, reps=3, tiles=((8, 8), (16, 16), (16, 24), (24, 24),
+                                                                   (32, 32)),
+                   bands=((8, 4), (4, 4), (8, 8), (4, 2), (2, 2)), log=None):
+    """Chooses the launch shape of a batch by timing `step(batch)` (one
+    batched time step).  Instances with the same geometry (unknowns, guide
+    stars, subapertures) form a class and share their settings.  Stages:
+      1. CTA split and rounds: the library's work-proportional split in one
+         round; two rounds with the largest class first on the whole GPU
+         (CTAs per instance = SMs / instances of that class) and the others
+         after it, split in proportion to their work; variants of those
+         splits (scaled by 3/4 and 5/4 within the SM count).  `candidates`
+         (a list of (ctas, rounds) pairs) replaces the generated ones.
+      2. WFS tile shape per class (`tiles`), in turn, keeping a change only
+         when the step gets faster.
+      3. P^T band heights per class (`bands`: rows on the largest and on the
+         smaller layers of the geometry), the same way (set on the handles).
+    The CTA cap is the device's SM count (one CTA of 512 threads per SM).
+    Returns ({"ctas", "rounds", "tiles", "bands", "ms"}, timings): the best
+    setting (the handles keep its band heights) and every timed candidate."""
     import torch
     n = len(fewhas)
-    if candidates is None:
-        sizes = [f.n for f in fewhas]
-        tot = sum(sizes)
-        cap = 148
-        candidates = [None,
-                      [max(1, int(cap * s / tot)) for s in sizes],
-                      [max(1, cap // n)] * n]
+    cap = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    say = log or (lambda *a: None)
+    key = [(f.n, f.n_slopes) for f in fewhas]
+    classes = sorted(set(key), key=lambda k: -k[0])
+    members = {k: [i for i in range(n) if key[i] == k] for k in classes}
     timings = []
-    best, best_ms = None, float("inf")
-    for cand in candidates:
-        ctas, rounds = cand if isinstance(cand, tuple) else (cand, None)
+
+    def run(ctas, rounds, tl):
         try:
-            b = FewhaBatch(fewhas, ctas, rounds)
+            b = FewhaBatch(fewhas, ctas, rounds, tl)
         except FewhaError:
-            timings.append((cand, None))
-            continue
-        step(b)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(reps):
-            step(b)
-        e1.record()
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / reps
-        timings.append(((b.ctas(), b.rounds), ms))
-        if ms < best_ms:
-            best, best_ms = (b.ctas(), b.rounds), ms
+            timings.append(((ctas, rounds, tl), None))
+            return None, None
+        ms = _time_batch(b, step, reps)
+        got = (b.ctas(), list(b.rounds), b.tiles())
         b.close()
-    return best, timings
+        timings.append((got, ms))
+        say("autotune %s -> %.3f ms" % (got[0][:1] + got[0][-1:], ms))
+        return ms, got
+
+    # stage 1: CTA split and rounds
+    if candidates is None:
+        work = [f.n for f in fewhas]
+        big = members[classes[0]]
+        rest = [i for i in range(n) if i not in big]
+        candidates = [(None, None)]
+        if rest:
+            # the largest class first on all SMs (in one or two rounds), the
+            # others after it
+            for parts in (1, 2):
+                per = (len(big) + parts - 1) // parts
+                c = [0] * n
+                r = [0] * n
+                for j, i in enumerate(big):
+                    c[i] = max(1, cap // per)
+                    r[i] = j // per
+                for i, ci in zip(rest, _split(cap, [work[i] for i in rest])):
+                    c[i] = ci
+                    r[i] = parts
+                candidates.append((c, r))
+        else:
+            candidates.append((_split(cap, [f.n for f in fewhas]), None))
+    best_ms, best = float("inf"), None
+    for ctas, rounds in candidates:
+        ms, got = run(ctas, rounds, None)
+        if ms is not None and ms < best_ms:
+            best_ms, best = ms, got
+    if best is None:
+        raise FewhaError(-1, "autotune_batch: no candidate launch fits")
+    ctas, rounds, tl = best
+    # stage 2: WFS tiles per class
+    for k in classes:
+        for t in tiles:
+            if all(tl[i] == t for i in members[k]):
+                continue
+            trial = [t if i in members[k] else tl[i] for i in range(n)]
+            ms, got = run(ctas, rounds, trial)
+            if ms is not None and ms < best_ms:
+                best_ms, tl = ms, got[2]
+    # stage 3: P^T band heights per class
+    band = {}
+    for k in classes:
+        f0 = fewhas[members[k][0]]
+        li = f0.launch_info()
+        cur = (li["pt_rows_large"], li["pt_rows_small"])
+        for bl in bands:
+            if bl == cur:
+                continue
+            try:
+                for i in members[k]:
+                    fewhas[i].set_pt_bands(*bl)
+            except FewhaError:
+                continue
+            ms, got = run(ctas, rounds, tl)
+            if ms is not None and ms < best_ms:
+                best_ms, cur = ms, bl
+        for i in members[k]:
+            fewhas[i].set_pt_bands(*cur)
+        band[k] = cur
+    return ({"ctas": ctas, "rounds": rounds, "tiles": tl, "bands": [band[key[i]] for i in range(n)],
+             "ms": best_ms}, timings)
+
+def read_bandwidth(nbytes, reps=20):
+    """Read bandwidth [GB/s] of the library's streaming probe over a device
+    buffer of nbytes (fewha_read_probe: one launch reading it reps times),
+    timed with CUDA events after one untimed pass: an L2-resident buffer
+    measures the L2, a large one DRAM."""
+    import torch
+    lib = load_library()
+    buf = torch.ones(nbytes // 4, dtype=torch.float32, device="cuda")
+    sink = torch.empty(4 * torch.cuda.get_device_properties(0).multi_processor_count, dtype=torch.float32,
+                       device="cuda")
+    stream = _stream_ptr(torch)
+    st = lib.fewha_read_probe(C.c_void_p(buf.data_ptr()), buf.numel() * 4, 1, C.c_void_p(sink.data_ptr()), stream)
+    if st != 0:
+        raise FewhaError(st, "fewha_read_probe")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    lib.fewha_read_probe(C.c_void_p(buf.data_ptr()), buf.numel() * 4, reps, C.c_void_p(sink.data_ptr()), stream)
+    e1.record()
+    torch.cuda.synchronize()
+    return buf.numel() * 4 * reps / (e0.elapsed_time(e1) * 1e-3) / 1e9

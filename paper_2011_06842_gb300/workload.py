@@ -73,3 +73,36 @@ def solve_bytes(geom, iters, kv, word=4):
     rhs = 2 * geom.n_sub ** 2 * G + 2 * G * m2 + 4 * n
     init = (5 * kv + 6) * n if kv > 0 else 0
     return word * (rhs + init) + iters * bytes_per_iter(geom, word, augmented=kv > 0)
+
+
+def op_intermediate_words(geom):
+    """Operator intermediates of one application of M, each written once and
+    read once: nodal layers (n), forward wavefronts (G (n_s+1)^2), slopes
+    (G 2 n_s^2), adjoint wavefronts (G (n_s+1)^2), adjoint layers (n)."""
+    n = sum(l.n * l.n for l in geom.layers)
+    G = len(geom.gs)
+    m2 = (geom.n_sub + 1) ** 2
+    return 2 * (2 * n + 2 * G * m2 + 2 * G * geom.n_sub ** 2)
+
+
+def reference_bytes_per_iter(geom, word=4):
+    """The per-iteration count of the scope table's measurement row: solver
+    vectors ~14 n words (read p, J^{-1}, p_m, q_m, c, r, q, z; write q, c, r,
+    z, p, the basis copy) plus the operator intermediates
+    (op_intermediate_words), written once and read once, whether or not an
+    implementation keeps them in registers or shared memory (the fused WFS
+    phase never stores the slopes)."""
+    n = sum(l.n * l.n for l in geom.layers)
+    return word * (14 * n + op_intermediate_words(geom))
+
+
+def reference_solve_bytes(geom, iters, k, word=4, augmented=True):
+    """Bytes of one time step under the same count: iters iterations, the
+    right-hand side and initial projection (~1.5 operator-equivalents for
+    augmented PCG, the right-hand side alone, 0.5, for plain PCG) and the
+    9 n k projection reads of the recycled basis (augmented only; the FLOP
+    table's 9 n_lay^2 L augmented term)."""
+    n = sum(l.n * l.n for l in geom.layers)
+    op = op_intermediate_words(geom)
+    extra = (1.5 * op + 9 * n * k) if augmented else 0.5 * op
+    return iters * reference_bytes_per_iter(geom, word) + word * extra

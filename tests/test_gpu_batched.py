@@ -113,3 +113,69 @@ def test_batched_graph_replay_matches_oracle(lib):
             assert rg["status"] == 0 and rg["iterations"] == ro["iterations"]
             assert rel(c.cpu().numpy(), st_o["c"]) < 1e-5
     batch.close()
+
+
+def test_pt_bands_replan_keeps_the_operator(lib):
+    """fewha_set_pt_bands re-plans the P^T gather's work items: the operator
+    (ELT geometry, FP64) equals the oracle for every band height tried, and a
+    band that does not fit is refused with the earlier plan kept."""
+    geom = configs.get("elt")
+    s, w = FrozenFlowSensors(geom, seed=71).sequence(1, seed=72)
+    o = Oracle(geom, w)
+    f = lib.Fewha(geom, w, "f64")
+    x = np.random.default_rng(3).standard_normal(f.n)
+    y0 = o.apply_op(x)
+    planned = 0
+    for bl in ((4, 2), (2, 2), (8, 8), (1, 16), (8, 4)):
+        before = f.launch_info()
+        try:
+            f.set_pt_bands(*bl)
+            planned += 1
+            li = f.launch_info()
+            assert (li["pt_rows_large"], li["pt_rows_small"]) == bl
+        except lib.FewhaError as e:  # staged rows beyond the shared memory: the plan stays
+            assert e.status == -2
+            assert f.launch_info() == before
+        y = f.apply_op(torch.tensor(x, device="cuda")).cpu().numpy()
+        assert rel(y, y0) < 1e-10, bl
+    assert planned >= 3
+    f.close()
+
+
+def test_batched_explicit_tiles_and_autotuner(lib):
+    """Explicit WFS tiles per instance (fewha_batch_create_ex) and the
+    autotuner's chosen launch (CTA split, rounds, tiles, band heights) give
+    the oracle's time steps (FP64, 1e-10)."""
+    names = ["tiny", "mixed", "micro", "tiny"]
+    inst = []
+    for i, name in enumerate(names):
+        geom = configs.get(name)
+        s, w = FrozenFlowSensors(geom, seed=110 + i).sequence(8, seed=120 + i)
+        o = Oracle(geom, w)
+        f = lib.Fewha(geom, w, "f64")
+        inst.append([o, o.new_state(4), f, f.new_state(4), torch.zeros(f.n, dtype=torch.float64, device="cuda"),
+                     s.cuda(), s.numpy()])
+    fewhas = [x[2] for x in inst]
+    b = lib.FewhaBatch(fewhas, [5, 7, 1, 3], None, [(8, 8), (16, 8), (4, 4), (24, 16)])
+    assert b.tiles() == [(8, 8), (16, 8), (4, 4), (24, 16)]
+    for t in range(2):
+        stats = b.solve([x[5][t] for x in inst], [x[4] for x in inst], [x[3] for x in inst], max_iter=4)
+        for x, rg in zip(inst, b.read_stats(stats)):
+            x[0].solve(x[6][t], x[1], max_iter=4, augmented=True)
+            assert rg["status"] == 0 and rel(x[4].cpu().numpy(), x[1]["c"]) < 1e-10
+    b.close()
+    frame = [2]
+
+    def step(batch):  # the tuning steps run on scratch states
+        batch.solve([x[5][frame[0]] for x in inst], [torch.zeros_like(x[4]) for x in inst],
+                    [x[2].new_state(4) for x in inst], max_iter=4)
+
+    best, timings = lib.autotune_batch(fewhas, step, reps=1)
+    assert len(timings) >= 3 and best["ms"] > 0
+    b = lib.FewhaBatch(fewhas, best["ctas"], best["rounds"], best["tiles"])
+    for t in range(2, 4):
+        stats = b.solve([x[5][t] for x in inst], [x[4] for x in inst], [x[3] for x in inst], max_iter=4)
+        for x, rg in zip(inst, b.read_stats(stats)):
+            x[0].solve(x[6][t], x[1], max_iter=4, augmented=True)
+            assert rg["status"] == 0 and rel(x[4].cpu().numpy(), x[1]["c"]) < 1e-10
+    b.close()
