@@ -44,6 +44,8 @@ typedef struct {
     double r0, alpha;
     int n_taps;
     const double *taps;
+    /* subapertures across the sensor of each guide star (NULL or 0: n_sub) */
+    const int *gs_ns;
 } orc_params;
 
 typedef struct {
@@ -53,8 +55,12 @@ typedef struct {
     double *lay_h, *lay_cn2, *lay_delta, *taps;
     int *lay_n, *lay_J;
     /* derived geometry */
-    double ds;         /* subaperture size D/n_s */
-    unsigned char *mask; /* n_s*n_s valid subapertures */
+    double ds;         /* subaperture size D/n_s of the main (mirror) grid */
+    int *gns;          /* per guide star: subapertures across its sensor */
+    double *gds;       /* per guide star: its subaperture size D/n_g */
+    long *slope_off;   /* per guide star: offset of its slopes (2 n_g^2 each), n_gs + 1 */
+    long *mask_off;    /* per guide star: offset of its mask (n_g^2 each), n_gs + 1 */
+    unsigned char *mask; /* valid subapertures, sensor after sensor */
     double *lay_d;     /* layer grid spacing */
     long *lay_off;     /* offset of layer l in the coefficient vector */
     long n;            /* total unknowns */
@@ -66,8 +72,10 @@ typedef struct {
 /* Geometry (Sec. 2, Sec. 3, Fig. grids)                                     */
 /* ------------------------------------------------------------------------ */
 
-/* Pupil node (i, j): x = -D/2 + j*ds (first axis), y = -D/2 + i*ds. */
+/* Pupil node (i, j): x = -D/2 + j*ds (first axis), y = -D/2 + i*ds; ds of
+ * the main grid (the mirror's actuators) or of guide star g's sensor. */
 static double pupil_coord(const orc_ctx *c, int idx) { return -0.5 * c->p.D + idx * c->ds; }
+static double pupil_coord_g(const orc_ctx *c, int g, int idx) { return -0.5 * c->p.D + idx * c->gds[g]; }
 
 /* Cone compression factor of guide star g at height h: 1 for an NGS,
  * 1 - h/H for an LGS at height H (Sec. 2, P^LGS). */
@@ -220,13 +228,13 @@ static int layer_position(const orc_ctx *c, int g, int l, double x, double y,
     return ORC_OK;
 }
 
-/* P_g: layers (nodal) -> wavefront on the (n_s+1)^2 pupil nodes. */
+/* P_g: layers (nodal) -> wavefront on the (n_g+1)^2 pupil nodes of g's sensor. */
 void orc_prop_fwd(const orc_ctx *c, int g, const double *nodal, double *wf)
 {
-    int m = c->p.n_sub + 1;
+    int m = c->gns[g] + 1;
     for (int i = 0; i < m; i++) {
         for (int j = 0; j < m; j++) {
-            double x = pupil_coord(c, j), y = pupil_coord(c, i), v = 0.0;
+            double x = pupil_coord_g(c, g, j), y = pupil_coord_g(c, g, i), v = 0.0;
             for (int l = 0; l < c->p.n_layers; l++) {
                 int kx, ky, n = c->lay_n[l];
                 double wx, wy;
@@ -243,10 +251,10 @@ void orc_prop_fwd(const orc_ctx *c, int g, const double *nodal, double *wf)
 /* P_g^T: scatter form of the exact transpose (accumulates into nodal). */
 void orc_prop_adj(const orc_ctx *c, int g, const double *wf, double *nodal)
 {
-    int m = c->p.n_sub + 1;
+    int m = c->gns[g] + 1;
     for (int i = 0; i < m; i++) {
         for (int j = 0; j < m; j++) {
-            double x = pupil_coord(c, j), y = pupil_coord(c, i), v = wf[i * m + j];
+            double x = pupil_coord_g(c, g, j), y = pupil_coord_g(c, g, i), v = wf[i * m + j];
             for (int l = 0; l < c->p.n_layers; l++) {
                 int kx, ky, n = c->lay_n[l];
                 double wx, wy;
@@ -302,47 +310,48 @@ void orc_gamma_adj(int ns, const double *s, double *wf)
 /* ------------------------------------------------------------------------ */
 
 long orc_n_unknowns(const orc_ctx *c) { return c->n; }
-long orc_n_slopes(const orc_ctx *c) { return 2L * c->p.n_sub * c->p.n_sub * c->p.n_gs; }
+long orc_n_slopes(const orc_ctx *c) { return c->slope_off[c->p.n_gs]; }
+long orc_slope_offset(const orc_ctx *c, int g) { return c->slope_off[g]; }
+int orc_sensor_ns(const orc_ctx *c, int g) { return c->gns[g]; }
 double orc_layer_spacing(const orc_ctx *c, int l) { return c->lay_d[l]; }
 const unsigned char *orc_mask(const orc_ctx *c) { return c->mask; }
 
 /* s = A phi (all guide stars, all subapertures, no weighting). */
 void orc_apply_A(const orc_ctx *c, const double *nodal, double *s)
 {
-    int ns = c->p.n_sub, m = ns + 1;
-    double *wf = malloc(sizeof(double) * m * m);
     for (int g = 0; g < c->p.n_gs; g++) {
+        int ns = c->gns[g], m = ns + 1;
+        double *wf = malloc(sizeof(double) * m * m);
         orc_prop_fwd(c, g, nodal, wf);
-        orc_gamma_fwd(ns, wf, s + 2L * ns * ns * g);
+        orc_gamma_fwd(ns, wf, s + c->slope_off[g]);
+        free(wf);
     }
-    free(wf);
 }
 
 /* phi = A^T s (overwrites phi). */
 void orc_apply_AT(const orc_ctx *c, const double *s, double *nodal)
 {
-    int ns = c->p.n_sub, m = ns + 1;
-    double *wf = malloc(sizeof(double) * m * m);
     memset(nodal, 0, sizeof(double) * c->n);
     for (int g = 0; g < c->p.n_gs; g++) {
-        memset(wf, 0, sizeof(double) * m * m);
-        orc_gamma_adj(ns, s + 2L * ns * ns * g, wf);
+        int ns = c->gns[g], m = ns + 1;
+        double *wf = calloc((size_t)m * m, sizeof(double));
+        orc_gamma_adj(ns, s + c->slope_off[g], wf);
         orc_prop_adj(c, g, wf, nodal);
+        free(wf);
     }
-    free(wf);
 }
 
 /* C_eta^{-1}: diagonal, 1/sigma_g^2 on valid subapertures and 0 elsewhere
  * (reading of the noise covariance; the paper gives no form). */
 void orc_apply_Cinv(const orc_ctx *c, double *s)
 {
-    int ns = c->p.n_sub;
     for (int g = 0; g < c->p.n_gs; g++) {
+        int ns = c->gns[g];
         double w = c->p.gs_w[g];
         for (int a = 0; a < 2; a++)
             for (int i = 0; i < ns * ns; i++) {
-                long k = 2L * ns * ns * g + (long)a * ns * ns + i;
-                s[k] = c->mask[i] ? w * s[k] : 0.0;
+                long k = c->slope_off[g] + (long)a * ns * ns + i;
+                s[k] = c->mask[c->mask_off[g] + i] ? w * s[k] : 0.0;
             }
     }
 }
@@ -419,16 +428,21 @@ int orc_fit(const orc_ctx *c, const double *coef, double *a)
 }
 
 /* Pseudo-open-loop measurements (closed loop): s_out = s + Gamma a for every
- * guide star, a the mirror shape applied two steps earlier. */
-void orc_pol_slopes(const orc_ctx *c, const double *s, const double *a, double *s_out)
+ * guide star, a the mirror shape applied two steps earlier.  The mirror's
+ * actuators sit on the main pupil grid, so every sensor must have the main
+ * n_sub (ORC_ERR_GEOMETRY otherwise). */
+int orc_pol_slopes(const orc_ctx *c, const double *s, const double *a, double *s_out)
 {
     int ns = c->p.n_sub;
+    for (int g = 0; g < c->p.n_gs; g++)
+        if (c->gns[g] != ns) return ORC_ERR_GEOMETRY;
     long per = 2L * ns * ns;
     double *ga = malloc(sizeof(double) * per);
     orc_gamma_fwd(ns, a, ga);
     for (int g = 0; g < c->p.n_gs; g++)
         for (long e = 0; e < per; e++) s_out[g * per + e] = s[g * per + e] + ga[e];
     free(ga);
+    return ORC_OK;
 }
 
 /* Gain control: closed loop a_next = a_i + gain (a~ - a_{i-1}); open loop
@@ -500,13 +514,14 @@ double orc_data_diag(const orc_ctx *c, long i)
     W_inv(c, e, v);
     orc_apply_A(c, v, s);
     double acc = 0.0;
-    int ns = c->p.n_sub;
-    for (int g = 0; g < c->p.n_gs; g++)
+    for (int g = 0; g < c->p.n_gs; g++) {
+        int ns = c->gns[g];
         for (int a = 0; a < 2; a++)
             for (int k = 0; k < ns * ns; k++) {
-                double val = s[2L * ns * ns * g + (long)a * ns * ns + k];
-                if (c->mask[k]) acc += c->p.gs_w[g] * val * val;
+                double val = s[c->slope_off[g] + (long)a * ns * ns + k];
+                if (c->mask[c->mask_off[g] + k]) acc += c->p.gs_w[g] * val * val;
             }
+    }
     free(e);
     free(v);
     free(s);
@@ -597,16 +612,36 @@ int orc_create(const orc_params *p, int with_precond, orc_ctx **out)
     c->p.lay_n = c->lay_n;
     c->p.lay_J = c->lay_J;
 
-    int ns = p->n_sub;
-    c->ds = p->D / ns;
-    c->mask = malloc(ns * ns);
+    c->ds = p->D / p->n_sub;
+    /* sensors: guide star g has an n_g x n_g Shack-Hartmann sensor over the
+     * pupil; a subaperture is lit iff its centre radius is within
+     * [obstruction D/2, D/2], except that the single subaperture of a 1x1
+     * sensor sees the whole pupil and is always lit (reading) */
+    int G = p->n_gs;
+    c->gns = malloc(sizeof(int) * G);
+    c->gds = malloc(sizeof(double) * G);
+    c->slope_off = malloc(sizeof(long) * (G + 1));
+    c->mask_off = malloc(sizeof(long) * (G + 1));
+    c->slope_off[0] = c->mask_off[0] = 0;
+    for (int g = 0; g < G; g++) {
+        int ns = (p->gs_ns && p->gs_ns[g] > 0) ? p->gs_ns[g] : p->n_sub;
+        c->gns[g] = ns;
+        c->gds[g] = p->D / ns;
+        c->slope_off[g + 1] = c->slope_off[g] + 2L * ns * ns;
+        c->mask_off[g + 1] = c->mask_off[g] + (long)ns * ns;
+    }
+    c->p.gs_ns = NULL;
+    c->mask = malloc(c->mask_off[G] > 0 ? c->mask_off[G] : 1);
     double rin = 0.5 * p->obstruction * p->D, rout = 0.5 * p->D;
-    for (int i = 0; i < ns; i++)
-        for (int j = 0; j < ns; j++) {
-            double cx = -0.5 * p->D + (j + 0.5) * c->ds, cy = -0.5 * p->D + (i + 0.5) * c->ds;
-            double r = sqrt(cx * cx + cy * cy);
-            c->mask[i * ns + j] = (r >= rin && r <= rout) ? 1 : 0;
-        }
+    for (int g = 0; g < G; g++) {
+        int ns = c->gns[g];
+        for (int i = 0; i < ns; i++)
+            for (int j = 0; j < ns; j++) {
+                double cx = -0.5 * p->D + (j + 0.5) * c->gds[g], cy = -0.5 * p->D + (i + 0.5) * c->gds[g];
+                double r = sqrt(cx * cx + cy * cy);
+                c->mask[c->mask_off[g] + i * ns + j] = (ns == 1 || (r >= rin && r <= rout)) ? 1 : 0;
+            }
+    }
 
     c->lay_d = malloc(sizeof(double) * p->n_layers);
     c->lay_off = malloc(sizeof(long) * (p->n_layers + 1));
@@ -647,6 +682,7 @@ void orc_destroy(orc_ctx *c)
     free(c->gs_tx); free(c->gs_ty); free(c->gs_H); free(c->gs_w);
     free(c->lay_h); free(c->lay_cn2); free(c->lay_delta); free(c->taps);
     free(c->lay_n); free(c->lay_J); free(c->mask); free(c->lay_d); free(c->lay_off);
+    free(c->gns); free(c->gds); free(c->slope_off); free(c->mask_off);
     free(c->prior); free(c->invJ);
     free(c);
 }

@@ -46,7 +46,7 @@ class _Params(C.Structure):
                 ("n_gs", C.c_int), ("gs_tx", _dp), ("gs_ty", _dp), ("gs_H", _dp), ("gs_w", _dp),
                 ("n_layers", C.c_int), ("lay_h", _dp), ("lay_cn2", _dp), ("lay_delta", _dp),
                 ("lay_n", _ip), ("lay_J", _ip), ("r0", C.c_double), ("alpha", C.c_double),
-                ("n_taps", C.c_int), ("taps", _dp)]
+                ("n_taps", C.c_int), ("taps", _dp), ("gs_ns", _ip)]
 
 
 class _Opts(C.Structure):
@@ -104,6 +104,11 @@ def _load():
             lib.orc_fit.argtypes = [vp, _dp, _dp]
             lib.orc_fit.restype = C.c_int
             lib.orc_pol_slopes.argtypes = [vp, _dp, _dp, _dp]
+            lib.orc_pol_slopes.restype = C.c_int
+            lib.orc_slope_offset.argtypes = [vp, C.c_int]
+            lib.orc_slope_offset.restype = C.c_long
+            lib.orc_sensor_ns.argtypes = [vp, C.c_int]
+            lib.orc_sensor_ns.restype = C.c_int
             lib.orc_control.argtypes = [C.c_long, C.c_int, C.c_double, _dp, _dp, _dp, _dp]
             _lib = lib
     return _lib
@@ -201,10 +206,11 @@ class Oracle:
         ld = arr([l.delta for l in lays])
         ln = arr([l.n for l in lays], np.int32)
         lJ = arr([l.J for l in lays], np.int32)
+        gns = arr([getattr(g, "n_sub", 0) or geom.n_sub for g in gs], np.int32)
         ip = lambda a: a.ctypes.data_as(_ip)  # noqa: E731
         self._p = _Params(geom.D, geom.obstruction, geom.n_sub, len(gs), _ptr(tx), _ptr(ty),
                           _ptr(H), _ptr(w), len(lays), _ptr(lh), _ptr(lc), _ptr(ld), ip(ln), ip(lJ),
-                          geom.r0, geom.alpha, len(self.taps), _ptr(self.taps))
+                          geom.r0, geom.alpha, len(self.taps), _ptr(self.taps), ip(gns))
         h = C.c_void_p()
         st = lib.orc_create(C.byref(self._p), 1 if with_precond else 0, C.byref(h))
         if st != 0:
@@ -214,6 +220,8 @@ class Oracle:
         self.n = lib.orc_n_unknowns(h)
         self.n_slopes = lib.orc_n_slopes(h)
         self.n_sub = geom.n_sub
+        self.sensor_ns = [lib.orc_sensor_ns(h, g) for g in range(len(gs))]
+        self.slope_off = [lib.orc_slope_offset(h, g) for g in range(len(gs))] + [self.n_slopes]
         self.layer_n = [l.n for l in lays]
         self.layer_off = np.concatenate([[0], np.cumsum([l.n * l.n for l in lays])]).astype(int)
 
@@ -226,9 +234,11 @@ class Oracle:
     def layer_spacing(self, l):
         return self._lib.orc_layer_spacing(self._h, l)
 
-    def mask(self):
-        m = self._lib.orc_mask(self._h)
-        return np.ctypeslib.as_array(m, shape=(self.n_sub * self.n_sub,)).copy().astype(bool)
+    def mask(self, g=0):
+        """Lit subapertures of guide star g's sensor (n_g^2 booleans)."""
+        off = sum(n * n for n in self.sensor_ns[:g])
+        m = np.ctypeslib.as_array(self._lib.orc_mask(self._h), shape=(off + self.sensor_ns[g] ** 2,))
+        return m[off:].copy().astype(bool)
 
     def prior(self):
         return np.ctypeslib.as_array(self._lib.orc_prior(self._h), shape=(self.n,)).copy()
@@ -271,7 +281,8 @@ class Oracle:
         """s + Gamma a for every guide star (pseudo-open-loop measurements)."""
         s, a = _f64(s), _f64(a)
         out = np.zeros_like(s)
-        self._lib.orc_pol_slopes(self._h, _ptr(s), _ptr(a), _ptr(out))
+        if self._lib.orc_pol_slopes(self._h, _ptr(s), _ptr(a), _ptr(out)) != 0:
+            raise ValueError("pseudo-open-loop slopes need every sensor on the mirror's grid")
         return out
 
     def control(self, closed, gain, a_im1, a_i, a_fit):
@@ -298,7 +309,7 @@ class Oracle:
 
     def prop_fwd(self, g, nodal):
         nodal = _f64(nodal)
-        wf = np.empty((self.n_sub + 1) ** 2)
+        wf = np.empty((self.sensor_ns[g] + 1) ** 2)
         self._lib.orc_prop_fwd(self._h, g, _ptr(nodal), _ptr(wf))
         return wf
 

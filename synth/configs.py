@@ -19,6 +19,7 @@ class GuideStar:
     theta_x: float  # direction [rad]
     theta_y: float
     H: float = 0.0  # LGS height [m]; 0 = natural guide star (no cone effect)
+    n_sub: int = 0  # subapertures across its sensor; 0 = the geometry's n_sub
 
 
 @dataclass
@@ -50,9 +51,13 @@ class Geometry:
     def n_unknowns(self):
         return sum(l.n * l.n for l in self.layers)
 
+    def sensor_ns(self, g):
+        """Subapertures across the sensor of guide star g."""
+        return self.gs[g].n_sub or self.n_sub
+
     @property
     def n_slopes(self):
-        return 2 * self.n_sub * self.n_sub * len(self.gs)
+        return sum(2 * self.sensor_ns(g) ** 2 for g in range(len(self.gs)))
 
 
 def _ring(n, radius_rad, H, phase=0.0):
@@ -104,6 +109,36 @@ def ltao() -> Geometry:
                     layers=layers, r0=0.129, L0=25.0, k_recycle=8, wind=_winds(9, 1005))
 
 
+def mcao() -> Geometry:
+    """The paper's MCAO asterism (Sec. 5.1 and its system-settings table):
+    6 LGS at 90 km with 84x84 sensors and 3 NGS with low-order sensors, one
+    2x2 and two 1x1; the text puts the NGS on a 2 arcmin and the LGS on an
+    8/3 arcmin diameter circle (the table swaps the two; the text is
+    followed).  39 m pupil with 28 % obstruction; the 9-layer profile of the
+    ELT workload."""
+    hs = [2000.0 * i for i in range(9)]
+    w = [math.exp(-h / 4000.0) for h in hs]
+    tot = sum(w)
+    layers = [Layer(h, wi / tot, 128 if h <= 8000.0 else 64, 5) for h, wi in zip(hs, w)]
+    ngs = _ring(3, 60 * ARCSEC, 0.0, phase=math.pi / 2)
+    for g, ns in zip(ngs, (2, 1, 1)):
+        g.n_sub = ns
+    return Geometry("mcao", D=39.0, obstruction=0.28, n_sub=84,
+                    gs=ngs + _ring(6, 80 * ARCSEC, 90000.0), layers=layers,
+                    r0=0.129, L0=25.0, k_recycle=8, wind=_winds(9, 1006))
+
+
+def sizes() -> Geometry:
+    """Small asterism with sensors of different sizes: LGS with 16x16 and
+    12x12 sensors, NGS with 2x2 and 1x1 sensors, 3 layers (exercises the
+    per-sensor paths of the operator at test size)."""
+    gs = [GuideStar(20 * ARCSEC, 0.0, 90000.0), GuideStar(-10 * ARCSEC, 17 * ARCSEC, 90000.0, 12),
+          GuideStar(-10 * ARCSEC, -17 * ARCSEC, 0.0, 2), GuideStar(30 * ARCSEC, 30 * ARCSEC, 0.0, 1)]
+    return Geometry("sizes", D=8.0, obstruction=0.2, n_sub=16, gs=gs,
+                    layers=[Layer(0.0, 0.5, 32, 3), Layer(4000.0, 0.3, 32, 3), Layer(9000.0, 0.2, 16, 2)],
+                    r0=0.15, wind=_winds(3, 1007))
+
+
 def medium() -> Geometry:
     """16 m, 40x40 SH, 4 LGS at 90 km on a 45'' ring, 5 layers on 64x64 grids
     (0-12 km), Daubechies-3 with 4 levels (the mid-size batched instance)."""
@@ -137,7 +172,8 @@ def mixed_ngs_lgs() -> Geometry:
                     r0=0.14, wind=_winds(3, 1004))
 
 
-CONFIGS = {"tiny": tiny, "elt": elt, "ltao": ltao, "medium": medium, "micro": micro, "mixed": mixed_ngs_lgs}
+CONFIGS = {"tiny": tiny, "elt": elt, "ltao": ltao, "mcao": mcao, "sizes": sizes, "medium": medium, "micro": micro,
+           "mixed": mixed_ngs_lgs}
 
 
 def get(name: str) -> Geometry:

@@ -19,9 +19,13 @@ import numpy as np
 import torch
 
 
-def pupil_mask(geom) -> np.ndarray:
-    """Illuminated subapertures: centre radius within [obstruction*D/2, D/2]."""
-    ns, D = geom.n_sub, geom.D
+def pupil_mask(geom, ns=None) -> np.ndarray:
+    """Illuminated subapertures of an ns x ns sensor (default: the geometry's
+    n_sub): centre radius within [obstruction*D/2, D/2]; the single
+    subaperture of a 1x1 sensor sees the whole pupil and is always lit."""
+    ns, D = ns or geom.n_sub, geom.D
+    if ns == 1:
+        return np.ones(1, dtype=bool)
     c = -D / 2 + (np.arange(ns) + 0.5) * D / ns
     r = np.hypot(c[None, :], c[:, None])
     return ((r >= geom.obstruction * D / 2) & (r <= D / 2)).reshape(-1)
@@ -66,17 +70,22 @@ class FrozenFlowSensors:
         self.screens = torch.tensor(np.stack(screens), dtype=torch.float64, device=self.device)
         winds = geom.wind if geom.wind else [(10.0, 0.0)] * len(geom.layers)
         self.wind = [(s * math.cos(d), s * math.sin(d)) for s, d in winds]
-        # edge sample points on the pupil
+        # edge sample points of every sensor size: per size, the vertical
+        # edges (x = nodes[j], y = rows[i, e], shape (ns, ns+1, 3)) and the
+        # horizontal edges (y = nodes[i], x = rows[j, e], shape (ns+1, ns, 3))
         t = torch.tensor([1.0 / 6, 0.5, 5.0 / 6], dtype=torch.float64, device=self.device)
-        nodes = -D / 2 + torch.arange(ns + 1, dtype=torch.float64, device=self.device) * self.ds
-        rows = -D / 2 + (torch.arange(ns, dtype=torch.float64, device=self.device)[:, None] + t) * self.ds
-        # vertical edges: x = nodes[j], y = rows[i, e]   -> (ns, ns+1, 3)
-        self.vx = nodes[None, :, None].expand(ns, ns + 1, 3)
-        self.vy = rows[:, None, :].expand(ns, ns + 1, 3)
-        # horizontal edges: y = nodes[i], x = rows[j, e] -> (ns+1, ns, 3)
-        self.hx = rows[None, :, :].expand(ns + 1, ns, 3)
-        self.hy = nodes[:, None, None].expand(ns + 1, ns, 3)
-        self.mask = pupil_mask(geom)
+        self.edges, self.masks = {}, {}
+        for g in range(len(geom.gs)):
+            nsg = geom.sensor_ns(g)
+            if nsg in self.edges:
+                continue
+            dsg = D / nsg
+            nodes = -D / 2 + torch.arange(nsg + 1, dtype=torch.float64, device=self.device) * dsg
+            rows = -D / 2 + (torch.arange(nsg, dtype=torch.float64, device=self.device)[:, None] + t) * dsg
+            self.edges[nsg] = (nodes[None, :, None].expand(nsg, nsg + 1, 3), rows[:, None, :].expand(nsg, nsg + 1, 3),
+                               rows[None, :, :].expand(nsg + 1, nsg, 3), nodes[:, None, None].expand(nsg + 1, nsg, 3))
+            self.masks[nsg] = pupil_mask(geom, nsg)
+        self.mask = self.masks[geom.sensor_ns(0)]
 
     def _sample(self, l, px, py):
         M, st = self.M, self.step
@@ -113,9 +122,10 @@ class FrozenFlowSensors:
     def clean_slopes(self, frame) -> torch.Tensor:
         """Noise-free slopes of all sensors, [x block | y block] per guide star."""
         out = []
-        for g in self.geom.gs:
-            V = self._phase(g, frame, self.vx, self.vy).mean(-1)  # (ns, ns+1)
-            Hh = self._phase(g, frame, self.hx, self.hy).mean(-1)  # (ns+1, ns)
+        for k, g in enumerate(self.geom.gs):
+            vx, vy, hx, hy = self.edges[self.geom.sensor_ns(k)]
+            V = self._phase(g, frame, vx, vy).mean(-1)  # (ns, ns+1)
+            Hh = self._phase(g, frame, hx, hy).mean(-1)  # (ns+1, ns)
             sx = V[:, 1:] - V[:, :-1]
             sy = Hh[1:, :] - Hh[:-1, :]
             out += [sx.reshape(-1), sy.reshape(-1)]
@@ -124,9 +134,10 @@ class FrozenFlowSensors:
     def clean_slopes_many(self, frames) -> torch.Tensor:
         """clean_slopes for a 1-D tensor of frame indices: (len(frames), n_slopes)."""
         out = []
-        for g in self.geom.gs:
-            V = self._phase(g, frames, self.vx, self.vy).mean(-1)
-            Hh = self._phase(g, frames, self.hx, self.hy).mean(-1)
+        for k, g in enumerate(self.geom.gs):
+            vx, vy, hx, hy = self.edges[self.geom.sensor_ns(k)]
+            V = self._phase(g, frames, vx, vy).mean(-1)
+            Hh = self._phase(g, frames, hx, hy).mean(-1)
             sx = V[:, :, 1:] - V[:, :, :-1]
             sy = Hh[:, 1:, :] - Hh[:, :-1, :]
             out += [sx.reshape(len(frames), -1), sy.reshape(len(frames), -1)]
@@ -135,21 +146,27 @@ class FrozenFlowSensors:
     def noise_sigma(self) -> np.ndarray:
         """sigma_g = rms of the noise-free slopes of g on lit subapertures / SNR."""
         s0 = self.clean_slopes(0).cpu().numpy()
-        ns2 = self.geom.n_sub ** 2
-        sig = []
+        sig, off = [], 0
         for g in range(len(self.geom.gs)):
-            blk = s0[2 * ns2 * g: 2 * ns2 * (g + 1)]
-            v = np.concatenate([blk[:ns2][self.mask], blk[ns2:][self.mask]])
+            nsg = self.geom.sensor_ns(g)
+            ns2, mk = nsg * nsg, self.masks[nsg]
+            blk = s0[off: off + 2 * ns2]
+            off += 2 * ns2
+            v = np.concatenate([blk[:ns2][mk], blk[ns2:][mk]])
             sig.append(math.sqrt(float(np.mean(v * v))) / self.geom.snr)
         return np.array(sig)
+
+    def _sigma_vector(self, sig):
+        """sigma_g repeated over the 2 n_g^2 slopes of every guide star."""
+        reps = [2 * self.geom.sensor_ns(g) ** 2 for g in range(len(self.geom.gs))]
+        return torch.tensor(np.repeat(sig, reps), dtype=torch.float64, device=self.device)
 
     def sequence(self, n_frames, seed=1, noise=True, dtype=torch.float64, first_frame=0):
         """Returns (slopes [n_frames, n_slopes] on self.device, noise weights 1/sigma^2)."""
         sig = self.noise_sigma()
         gen = torch.Generator(device=self.device)
         gen.manual_seed(seed)
-        ns2 = self.geom.n_sub ** 2
-        sig_vec = torch.tensor(np.repeat(sig, 2 * ns2), dtype=torch.float64, device=self.device)
+        sig_vec = self._sigma_vector(sig)
         frames = torch.empty((n_frames, self.geom.n_slopes), dtype=dtype, device=self.device)
         for t in range(n_frames):
             s = self.clean_slopes(first_frame + t)
@@ -166,8 +183,7 @@ class FrozenFlowSensors:
         sig = self.noise_sigma()
         gen = torch.Generator(device=self.device)
         gen.manual_seed(seed)
-        ns2 = self.geom.n_sub ** 2
-        sig_vec = torch.tensor(np.repeat(sig, 2 * ns2), dtype=torch.float64, device=self.device)
+        sig_vec = self._sigma_vector(sig)
         frames = torch.empty((n_frames, self.geom.n_slopes), dtype=dtype, device=self.device)
         for t0 in range(0, n_frames, chunk):
             f = torch.arange(first_frame + t0, first_frame + min(n_frames, t0 + chunk), device=self.device)

@@ -63,7 +63,7 @@ def test_layer_grid_reading(name):
         assert abs(R / d - (lay.n / 2 - 2)) < 1e-9
 
 
-@pytest.mark.parametrize("name", ["micro", "tiny", "mixed"])
+@pytest.mark.parametrize("name", ["micro", "tiny", "mixed", "sizes"])
 def test_propagation_reproduces_bilinear_functions(name):
     geom = configs.get(name)
     o = _oracle(geom)
@@ -75,10 +75,11 @@ def test_propagation_reproduces_bilinear_functions(name):
         ux, uy = u[None, :], u[:, None]
         a, b, c, e = coeffs[l]
         nodal[o.layer_off[l]:o.layer_off[l + 1]] = (a + b * ux + c * uy + e * ux * uy).ravel()
-    m = geom.n_sub + 1
-    x = -geom.D / 2 + np.arange(m) * geom.D / geom.n_sub
-    X, Y = x[None, :], x[:, None]
     for gi, g in enumerate(geom.gs):
+        ns = geom.sensor_ns(gi)
+        m = ns + 1
+        x = -geom.D / 2 + np.arange(m) * geom.D / ns
+        X, Y = x[None, :], x[:, None]
         expect = np.zeros((m, m))
         for l, lay in enumerate(geom.layers):
             s = (1 - lay.h / g.H) if g.H > 0 else 1.0
@@ -89,12 +90,12 @@ def test_propagation_reproduces_bilinear_functions(name):
         assert np.max(np.abs(got - expect)) < 1e-11 * max(1.0, np.max(np.abs(expect)))
 
 
-@pytest.mark.parametrize("name", ["micro", "mixed"])
+@pytest.mark.parametrize("name", ["micro", "mixed", "sizes"])
 def test_propagation_adjoint(name):
     geom = configs.get(name)
     o = _oracle(geom)
-    m = geom.n_sub + 1
     for g in range(len(geom.gs)):
+        m = geom.sensor_ns(g) + 1
         x = RNG.standard_normal(o.n)
         y = RNG.standard_normal(m * m)
         lhs = o.prop_fwd(g, x) @ y
@@ -102,7 +103,7 @@ def test_propagation_adjoint(name):
         assert abs(lhs - rhs) < 1e-12 * (abs(lhs) + 1)
 
 
-@pytest.mark.parametrize("name", ["micro", "tiny", "mixed"])
+@pytest.mark.parametrize("name", ["micro", "tiny", "mixed", "sizes"])
 def test_tomography_adjoint_and_M_symmetric(name):
     geom = configs.get(name)
     o = _oracle(geom)
@@ -115,20 +116,49 @@ def test_tomography_adjoint_and_M_symmetric(name):
     assert o.apply_op(x) @ x > 0
 
 
-def test_noise_weight_mask():
-    geom = configs.mixed_ngs_lgs()
-    w = np.array([1.0, 2.0, 3.0, 4.0, 5.0])
+@pytest.mark.parametrize("name", ["mixed", "sizes"])
+def test_noise_weight_mask(name):
+    geom = configs.get(name)
+    w = np.arange(1.0, len(geom.gs) + 1.0)
     o = _oracle(geom, w)
-    mask = pupil_mask(geom)
-    assert np.array_equal(o.mask(), mask)
-    assert mask.sum() < mask.size  # the obstruction removes subapertures
     s = np.ones(o.n_slopes)
     cs = o.apply_Cinv(s)
-    ns2 = geom.n_sub ** 2
+    off = 0
     for g in range(len(geom.gs)):
+        ns = geom.sensor_ns(g)
+        mask = pupil_mask(geom, ns)
+        assert np.array_equal(o.mask(g), mask)
+        if ns > 2:
+            assert mask.sum() < mask.size  # the obstruction removes subapertures
+        if ns == 1:
+            assert mask.all()  # a 1x1 sensor sees the whole pupil
+        assert o.slope_off[g] == off
         for a in range(2):
-            blk = cs[2 * ns2 * g + a * ns2: 2 * ns2 * g + (a + 1) * ns2]
+            blk = cs[off + a * ns * ns: off + (a + 1) * ns * ns]
             assert np.all(blk[mask] == w[g]) and np.all(blk[~mask] == 0.0)
+        off += 2 * ns * ns
+    assert off == o.n_slopes == geom.n_slopes
+
+
+def test_planar_ground_layer_gives_constant_slopes_on_every_sensor_size():
+    """A plane a x + b y on the ground layer (no cone, no shift at h = 0)
+    seen by sensors of 16, 12, 2 and 1 subapertures across: every subaperture
+    of sensor g measures s^x = a D/n_g, s^y = b D/n_g (Sec. 2, Gamma)."""
+    geom = configs.get("sizes")
+    o = _oracle(geom)
+    a, b = 0.37, -1.21
+    nodal = np.zeros(o.n)
+    lay = geom.layers[0]
+    d = o.layer_spacing(0)
+    u = (np.arange(lay.n) - lay.n / 2) * d
+    nodal[:lay.n * lay.n] = (a * u[None, :] + b * u[:, None]).ravel()
+    s = o.apply_A(nodal)
+    for g in range(len(geom.gs)):
+        ns = geom.sensor_ns(g)
+        ds = geom.D / ns
+        blk = s[o.slope_off[g]:o.slope_off[g + 1]]
+        assert np.allclose(blk[:ns * ns], a * ds, rtol=0, atol=1e-12 * abs(a * ds))
+        assert np.allclose(blk[ns * ns:], b * ds, rtol=0, atol=1e-12 * abs(b * ds))
 
 
 def _explicit_matrices(o, geom, w):
@@ -146,24 +176,28 @@ def _explicit_matrices(o, geom, w):
                         for i in range(nn)], axis=1)
         a, b = o.layer_off[l], o.layer_off[l + 1]
         Winv[a:b, a:b] = blk / lay.delta
-    ns = geom.n_sub
-    m = ns + 1
-    x = -geom.D / 2 + np.arange(m) * geom.D / ns
-    G = np.zeros((2 * ns * ns, m * m))
-    for i in range(ns):
-        for j in range(ns):
-            r = i * ns + j
-            G[r, i * m + j + 1] += 0.5
-            G[r, i * m + j] -= 0.5
-            G[r, (i + 1) * m + j + 1] += 0.5
-            G[r, (i + 1) * m + j] -= 0.5
-            G[ns * ns + r, (i + 1) * m + j] += 0.5
-            G[ns * ns + r, i * m + j] -= 0.5
-            G[ns * ns + r, (i + 1) * m + j + 1] += 0.5
-            G[ns * ns + r, i * m + j + 1] -= 0.5
+    def gamma(ns):
+        m = ns + 1
+        G = np.zeros((2 * ns * ns, m * m))
+        for i in range(ns):
+            for j in range(ns):
+                r = i * ns + j
+                G[r, i * m + j + 1] += 0.5
+                G[r, i * m + j] -= 0.5
+                G[r, (i + 1) * m + j + 1] += 0.5
+                G[r, (i + 1) * m + j] -= 0.5
+                G[ns * ns + r, (i + 1) * m + j] += 0.5
+                G[ns * ns + r, i * m + j] -= 0.5
+                G[ns * ns + r, (i + 1) * m + j + 1] += 0.5
+                G[ns * ns + r, i * m + j + 1] -= 0.5
+        return G
     hat = lambda t: np.maximum(0.0, 1.0 - np.abs(t))  # noqa: E731
     blocks = []
-    for g in geom.gs:
+    for gi, g in enumerate(geom.gs):
+        ns = geom.sensor_ns(gi)
+        m = ns + 1
+        x = -geom.D / 2 + np.arange(m) * geom.D / ns
+        G = gamma(ns)
         P = np.zeros((m * m, n))
         for l, lay in enumerate(geom.layers):
             d = o.layer_spacing(l)
@@ -176,12 +210,12 @@ def _explicit_matrices(o, geom, w):
             P[:, o.layer_off[l]:o.layer_off[l + 1]] = np.kron(Wy, Wx)
         blocks.append(G @ P)
     A = np.concatenate(blocks, axis=0)
-    mask = pupil_mask(geom)
-    cdiag = np.concatenate([np.concatenate([w[g] * mask, w[g] * mask]) for g in range(len(geom.gs))])
+    masks = [pupil_mask(geom, geom.sensor_ns(g)) for g in range(len(geom.gs))]
+    cdiag = np.concatenate([np.concatenate([w[g] * masks[g], w[g] * masks[g]]) for g in range(len(geom.gs))])
     return Winv, A, cdiag
 
 
-@pytest.mark.parametrize("name", ["micro", "tiny"])
+@pytest.mark.parametrize("name", ["micro", "tiny", "sizes"])
 def test_dense_M_matches_explicit_product_and_is_spd(name):
     geom = configs.get(name)
     w = np.linspace(0.7, 1.9, len(geom.gs))
