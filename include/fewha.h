@@ -28,9 +28,10 @@
  *    coefficients in row-major Mallat layout (coarsest approximation block in
  *    the top-left corner; at every level the block right of it is low-pass in
  *    y and high-pass in x, the block below high-pass in y and low-pass in x).
- *  - Layout of a slope vector s (length 2 n_s^2 G): guide star after guide
- *    star, each [x slopes | y slopes], each n_s x n_s row-major (row = y).
- *    Entries of unlit subapertures are ignored.
+ *  - Layout of a slope vector s (length sum_g 2 n_g^2, n_g the subapertures
+ *    across guide star g's sensor): guide star after guide star, each
+ *    [x slopes | y slopes], each n_g x n_g row-major (row = y).  Entries of
+ *    unlit subapertures are ignored.
  *  - Asynchrony: compute calls enqueue work on the given stream and return.
  */
 #ifndef FEWHA_H
@@ -65,9 +66,17 @@ enum { FEWHA_F64 = 0, FEWHA_F32 = 1, FEWHA_BF16S = 2 };
 /* Guide star (Sec. 2): direction theta [rad]; H = sodium-layer height [m] for
  * a laser guide star (cone effect, P^LGS), H <= 0 for a natural guide star
  * (P^NGS); weight = 1/sigma^2, the diagonal of C_eta^{-1} on its lit
- * subapertures (Sec. 3). */
+ * subapertures (Sec. 3); n_sub = subapertures across its Shack-Hartmann
+ * sensor (0: the geometry's n_sub), so that low-order sensors (the MCAO
+ * asterism's 2x2 and 1x1 NGS, Sec. 5.1) sit beside high-order ones.  Every
+ * sensor spans the pupil: sensor g has (n_g+1)^2 pupil nodes at spacing
+ * D / n_g; a subaperture is lit iff its centre radius lies in
+ * [obstruction D/2, D/2], and the single subaperture of a 1x1 sensor is
+ * always lit. */
 typedef struct {
     double theta_x, theta_y, H, weight;
+    int n_sub;
+    int pad;
 } fewha_gs;
 
 /* Turbulent layer (Sec. 2, Eq. atmo): height h [m], Cn2 fraction (prior D),
@@ -164,7 +173,7 @@ int fewha_set_noise(void *handle, const double *weight, int refresh_precond);
 /* Frees the handle and its device memory (synchronises the device). */
 void fewha_destroy(void *handle);
 
-/* n (unknowns), slopes (2 n_s^2 G), and the layer spacing d_l [m]. */
+/* n (unknowns), slopes (sum_g 2 n_g^2), and the layer spacing d_l [m]. */
 long fewha_n_unknowns(const void *handle);
 long fewha_n_slopes(const void *handle);
 double fewha_layer_spacing(const void *handle, int layer);
@@ -235,7 +244,9 @@ int fewha_rhs(void *handle, const void *s, void *b, cudaStream_t stream);
  *   outside a layer grid.  c 16-byte aligned.
  * fewha_pol_slopes: s_out = s + Gamma a_prev for every guide star (the
  *   pseudo-open-loop measurements of a closed loop; a_prev is the mirror shape
- *   applied two steps earlier).  s_out may equal s.
+ *   applied two steps earlier).  s_out may equal s.  The mirror's actuators
+ *   sit on the geometry's pupil grid, so every sensor must have the
+ *   geometry's n_sub (FEWHA_ERR_GEOMETRY otherwise).
  * fewha_control: closed != 0: a_next = a_i + gain (a_fit - a_{i-1}); closed ==
  *   0: a_next = (1 - gain) a_i + gain a_fit (gain control); 0 <= gain <= 1.
  * All asynchronous on `stream`; FEWHA_ERR_ARG for NULL handles or pointers. */

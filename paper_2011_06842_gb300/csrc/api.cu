@@ -180,7 +180,7 @@ long fewha_n_slopes(const void *handle)
 {
     if (!handle) return -1;
     const Plan &p = static_cast<const Handle *>(handle)->plan;
-    return 2L * p.ns * p.ns * p.G;
+    return p.slope_off[p.G];
 }
 
 double fewha_layer_spacing(const void *handle, int layer)

@@ -74,7 +74,7 @@ struct Record {
 
 template <typename T>
 struct Geo {
-    int G, L, ns, m;
+    int G, L, ns, m;  // guide stars, layers, the geometry's (mirror's) subapertures and pupil nodes across
     long n;
     int lay_n[FEWHA_MAX_LAYERS], lay_J[FEWHA_MAX_LAYERS];
     long lay_off[FEWHA_MAX_LAYERS + 1];
@@ -83,10 +83,16 @@ struct Geo {
     int n_taps;
     T h[kMaxT], g[kMaxT];
     int tile_y, tile_x;         // WFS tiles: tile_y x tile_x output nodes
-    int tiles_y, tiles_x;       // tiles per axis
+    // sensors (guide star g): subapertures across, pupil nodes across, WFS
+    // tiles per row of its pupil grid and tiles before it (WFS work items),
+    // offsets of its P_g tables (fk, fw), adjoint wavefront (psi), slopes
+    // and weights (wmask); m_max = the largest pupil grid
+    int gs_ns[FEWHA_MAX_GS], gs_m[FEWHA_MAX_GS], gs_tiles_x[FEWHA_MAX_GS], gs_tile0[FEWHA_MAX_GS + 1];
+    long gs_tab[FEWHA_MAX_GS], gs_psi[FEWHA_MAX_GS], gs_sl[FEWHA_MAX_GS], gs_mask[FEWHA_MAX_GS];
+    int m_max;
     const int *fk, *alo, *ahi;  // interpolation tables
     const T *fw;
-    const T *wmask;             // [G][ns*ns] weight on lit subapertures, 0 elsewhere
+    const T *wmask;             // per sensor [n_g*n_g] weight on lit subapertures, 0 elsewhere
     const T *alpha_d;           // [n]
     const T *invJ;              // [n]
     int lay_lg[FEWHA_MAX_LAYERS];  // log2(n_l)
@@ -94,9 +100,9 @@ struct Geo {
     const int *band_layer, *band_row0, *band_rows;  // [nbands]
     const int *band_ilo, *band_ihi;  // [G][nbands] pupil rows the band touches
     // guide stars of a band in groups whose pupil rows fit rows_chunk staged
-    // rows: [G][nbands] end of the guide star's group, and psi elements staged
-    // before it within the group
-    const int *band_gend, *band_gc;
+    // rows: [G][nbands] end of the guide star's group, psi elements staged
+    // before it within the group, and staged rows before it
+    const int *band_gend, *band_gc, *band_gr;
     int rows_chunk;             // pupil rows staged per pass of band_gather
     int stage_tab;              // band_gather also stages its P^T weight tables in shared memory
     int pingpong;               // layer phases have a second n x n shared buffer
@@ -756,15 +762,16 @@ __device__ __forceinline__ typename AccT<T>::type wfs_phase(const Args<T, S> &A,
     typedef typename AccT<T>::type Acc;
     const Geo<T> &G = A.geo;
     const int TY = G.tile_y, TX = G.tile_x, HY = TY + 2, HX = TX + 2, SY = TY + 1, SX = TX + 1;
-    const int m = G.m, ns = G.ns;
-    const int per_g = G.tiles_y * G.tiles_x, total = G.G * per_g;
+    const int total = G.gs_tile0[G.G];
     T *phi = sm;                          // [HY*HX] sum over layers (OP)
     T *sx = sm + (size_t)G.L * HY * HX;   // [SY*SX]
     T *sy = sx + SY * SX;
     Acc ws = 0;
     for (int w = A.vrank(); w < total; w += A.ncta) {
-        const int g = w / per_g, tt = w - g * per_g;
-        const int i0 = (tt / G.tiles_x) * TY, j0 = (tt % G.tiles_x) * TX;
+        int g = 0;
+        while (w >= G.gs_tile0[g + 1]) g++;  // sensor of this work item
+        const int m = G.gs_m[g], ns = G.gs_ns[g], tt = w - G.gs_tile0[g];
+        const int i0 = (tt / G.gs_tiles_x[g]) * TY, j0 = (tt % G.gs_tiles_x[g]) * TX;
         if (!RHS) {
             // phi at each halo node: the sum over layers of the bilinear value of
             // the layer at the node's projection (layer after layer, from 0),
@@ -781,7 +788,8 @@ __device__ __forceinline__ typename AccT<T>::type wfs_phase(const Args<T, S> &A,
                             const int l = l0 + u;
                             v[u] = 0;
                             if (l < G.L) {
-                                const int bx = ((g * G.L + l) * 2 + 0) * m, by = ((g * G.L + l) * 2 + 1) * m;
+                                const long bx = G.gs_tab[g] + (long)(l * 2 + 0) * m;
+                                const long by = G.gs_tab[g] + (long)(l * 2 + 1) * m;
                                 const int kx = __ldg(G.fk + bx + j), ky = __ldg(G.fk + by + i);
                                 const T wx = __ldg(G.fw + bx + j), wy = __ldg(G.fw + by + i);
                                 const int n = G.lay_n[l];
@@ -805,9 +813,9 @@ __device__ __forceinline__ typename AccT<T>::type wfs_phase(const Args<T, S> &A,
             const int i = i0 - 1 + a, j = j0 - 1 + b;
             T vx = 0, vy = 0;
             if (i >= 0 && i < ns && j >= 0 && j < ns) {
-                const T wgt = __ldg(G.wmask + (size_t)g * ns * ns + i * ns + j);
+                const T wgt = __ldg(G.wmask + G.gs_mask[g] + i * ns + j);
                 if (RHS) {
-                    const S *sg = A.slopes + (size_t)g * 2 * ns * ns;
+                    const S *sg = A.slopes + G.gs_sl[g];
                     vx = wgt * Cv<S>::ld(sg[i * ns + j]);
                     vy = wgt * Cv<S>::ld(sg[ns * ns + i * ns + j]);
                 } else {
@@ -832,7 +840,7 @@ __device__ __forceinline__ typename AccT<T>::type wfs_phase(const Args<T, S> &A,
                 const T v = T(0.5) * (sx[a * SX + b - 1] - sx[a * SX + b] + sx[(a - 1) * SX + b - 1] -
                                       sx[(a - 1) * SX + b] + sy[(a - 1) * SX + b] - sy[a * SX + b] +
                                       sy[(a - 1) * SX + b - 1] - sy[a * SX + b - 1]);
-                A.psi[(size_t)g * m * m + i * m + j] = Cv<S>::st(v);
+                A.psi[G.gs_psi[g] + i * m + j] = Cv<S>::st(v);
             }
         }
         __syncthreads();
@@ -852,13 +860,13 @@ __device__ __forceinline__ typename AccT<T>::type wfs_phase(const Args<T, S> &A,
 // Header of a P^T work item for guide star threadIdx.x (< G): pupil rows and
 // group of the band, loaded ahead of time by band_header().
 struct BandHdr {
-    int ilo, ihi, gend, gc;
+    int ilo, ihi, gend, gc, gr;
 };
 
 template <typename T, typename S>
 __device__ __forceinline__ BandHdr band_header(const Args<T, S> &A, int w)
 {
-    BandHdr h = {0, 0, 0, 0};
+    BandHdr h = {0, 0, 0, 0, 0};
     const Geo<T> &G = A.geo;
     if (threadIdx.x < G.G && w < G.nbands) {
         const int i = threadIdx.x * G.nbands + w;
@@ -866,6 +874,7 @@ __device__ __forceinline__ BandHdr band_header(const Args<T, S> &A, int w)
         h.ihi = __ldg(G.band_ihi + i);
         h.gend = __ldg(G.band_gend + i);
         h.gc = __ldg(G.band_gc + i);
+        h.gr = __ldg(G.band_gr + i);
     }
     return h;
 }
@@ -876,9 +885,10 @@ template <typename T, typename S>
 __device__ __forceinline__ void band_gather(const Args<T, S> &A, T *sm, const BandHdr *pre = nullptr)
 {
     const Geo<T> &G = A.geo;
-    const int m = G.m, RC = G.rows_chunk, NB = G.nbands;
+    const int RC = G.rows_chunk, NB = G.nbands;
     __shared__ int s_cum[FEWHA_MAX_GS + 1], s_base[FEWHA_MAX_GS + 1];
     __shared__ int s_ilo[FEWHA_MAX_GS], s_ihi[FEWHA_MAX_GS], s_gend[FEWHA_MAX_GS], s_gc[FEWHA_MAX_GS];
+    __shared__ int s_gr[FEWHA_MAX_GS];
     __shared__ long s_off[FEWHA_MAX_GS];  // psi element = s_off[q] + staged index
     for (int w = A.vrank(); w < NB; w += A.ncta) {
         const int l = __ldg(G.band_layer + w), a0 = __ldg(G.band_row0 + w), BR = __ldg(G.band_rows + w);
@@ -887,8 +897,10 @@ __device__ __forceinline__ void band_gather(const Args<T, S> &A, T *sm, const Ba
         T acc[kOutPT];
 #pragma unroll
         for (int j = 0; j < kOutPT; j++) acc[j] = 0;
-        T *ps = sm;           // [RC][m] staged psi rows
-        T *Tb = sm + RC * m;  // [RC][n] their x-contraction
+        // staged psi rows (guide star q's rows of its gs_m[q] nodes, one after
+        // the other: at most RC rows of m_max) and their x-contraction [RC][n]
+        T *ps = sm;
+        T *Tb = sm + RC * G.m_max;
         // pupil rows [ilo, ihi) of every guide star for this band and its
         // group (precomputed on the host), one load each in parallel
         if (threadIdx.x < G.G) {
@@ -897,6 +909,7 @@ __device__ __forceinline__ void band_gather(const Args<T, S> &A, T *sm, const Ba
             s_ihi[threadIdx.x] = h.ihi;
             s_gend[threadIdx.x] = h.gend;
             s_gc[threadIdx.x] = h.gc;
+            s_gr[threadIdx.x] = h.gr;
         }
         __syncthreads();
         // guide stars in groups whose pupil rows fit the RC staged rows
@@ -908,10 +921,11 @@ __device__ __forceinline__ void band_gather(const Args<T, S> &A, T *sm, const Ba
             // the staging offsets of the group are filled in parallel
             if (threadIdx.x <= ng) {
                 const int q = threadIdx.x, g = g0 + q;
-                const int c = q < ng ? s_gc[g] : s_gc[g1 - 1] + (s_ihi[g1 - 1] - s_ilo[g1 - 1]) * m;
+                const int rl = s_ihi[g1 - 1] - s_ilo[g1 - 1];  // rows of the group's last guide star
+                const int c = q < ng ? s_gc[g] : s_gc[g1 - 1] + rl * G.gs_m[g1 - 1];
                 s_cum[q] = c;
-                s_base[q] = c / m;
-                if (q < ng) s_off[q] = (long)g * m * m + (long)s_ilo[g] * m - c;
+                s_base[q] = q < ng ? s_gr[g] : s_gr[g1 - 1] + rl;
+                if (q < ng) s_off[q] = G.gs_psi[g] + (long)s_ilo[g] * G.gs_m[g] - c;
             }
             __syncthreads();
             const int nxt = ng << lgn;
@@ -984,9 +998,9 @@ __device__ __forceinline__ void band_gather(const Args<T, S> &A, T *sm, const Ba
                         T wr[kAdjW];
 #pragma unroll
                         for (int c = 0; c < kAdjW; c++) wr[c] = c < cnt ? xw[(size_t)c * nxt + ti] : T(0);
-                        const int rb = s_base[q], re = s_base[q + 1];
+                        const int rb = s_base[q], re = s_base[q + 1], mq = G.gs_m[g0 + q];
                         for (int row = rb + ((r0 - rb) % rstep + rstep) % rstep; row < re; row += rstep) {
-                            const T *rowp = ps + row * m + jlo;
+                            const T *rowp = ps + s_cum[q] + (row - rb) * mq + jlo;
                             T v = 0;
 #pragma unroll
                             for (int c = 0; c < kAdjW; c++)
@@ -1013,7 +1027,7 @@ __device__ __forceinline__ void band_gather(const Args<T, S> &A, T *sm, const Ba
                             wt = G.adj_w + (size_t)tx * kAdjW;
                             ws = 1;
                         }
-                        const T *rowp = ps + row * m + jlo;
+                        const T *rowp = ps + s_cum[q] + (row - s_base[q]) * G.gs_m[g0 + q] + jlo;
                         T v = 0;
                         for (int c = 0; c < cnt; c++) v += wt[c * ws] * rowp[c];  // cnt <= kAdjW
                         Tb[(row << lgn) + bcol] = v;

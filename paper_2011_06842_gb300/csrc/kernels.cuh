@@ -628,6 +628,19 @@ struct Impl : ImplBase {
         return ((size_t)P.L * (ty + 2) * (tx + 2) + 2 * (size_t)(ty + 1) * (tx + 1)) * sizeof(T);
     }
 
+    // WFS tiles of ty x tx pupil nodes on every sensor's grid: tiles per row
+    // and the cumulative work-item count per sensor
+    void set_tiles(Geo<T> &G, int ty, int tx) const
+    {
+        G.tile_y = ty;
+        G.tile_x = tx;
+        G.gs_tile0[0] = 0;
+        for (int g = 0; g < P.G; g++) {
+            G.gs_tiles_x[g] = (P.gm[g] + tx - 1) / tx;
+            G.gs_tile0[g + 1] = G.gs_tile0[g] + G.gs_tiles_x[g] * ((P.gm[g] + ty - 1) / ty);
+        }
+    }
+
     // WFS tile shape: a square tile if the caller fixed one, else the shape
     // (8..32 nodes per side) whose work per round of `ctas` CTAs is least
     // among those whose shared memory fits
@@ -641,7 +654,8 @@ struct Impl : ImplBase {
                 int ty = cand[a], tx = cand[c];
                 if (P.geom.tile) ty = tx = P.geom.tile;
                 if (wfs_bytes(ty, tx) > 200 * 1024) continue;
-                const int tiles = P.G * ((P.m + ty - 1) / ty) * ((P.m + tx - 1) / tx);
+                int tiles = 0;
+                for (int g = 0; g < P.G; g++) tiles += ((P.gm[g] + ty - 1) / ty) * ((P.gm[g] + tx - 1) / tx);
                 const int rounds = (tiles + ctas - 1) / ctas;
                 const double cost = rounds * ((double)(ty + 2) * (tx + 2) + 64.0);
                 if (cost < best - 1e-9) {
@@ -727,7 +741,7 @@ struct Impl : ImplBase {
         std::vector<int> rows_sum(G.nbands, 0);
         for (int g = 0; g < P.G; g++)
             for (int w = 0; w < G.nbands; w++) {
-                int lo = P.m, hi = 0;
+                int lo = P.gm[g], hi = 0;
                 size_t by = ((size_t)g * P.L + bl[w]) * 2 + 1;
                 for (int a = br0[w]; a < br0[w] + brs[w]; a++) {
                     int alo = P.alo[by * FEWHA_MAX_GRID + a], ahi = P.ahi[by * FEWHA_MAX_GRID + a];
@@ -748,7 +762,7 @@ struct Impl : ImplBase {
             return st;
         // band_gather stages rows_chunk psi rows and their x-contraction
         // (all guide stars of a band at once when they fit, else in groups)
-        const size_t row_bytes = (size_t)(P.m + nmax) * sizeof(T);
+        const size_t row_bytes = (size_t)(P.m_max + nmax) * sizeof(T);
         const size_t smem_cap = 200 * 1024;  // 227 KB per CTA minus the static shared memory
         size_t smem = sm_base;
         size_t want = (size_t)max_rows_sum * row_bytes;
@@ -758,7 +772,7 @@ struct Impl : ImplBase {
         {
             // guide stars of each band in groups of consecutive guide stars whose
             // pupil rows fit rows_chunk staged rows
-            std::vector<int> gend((size_t)P.G * G.nbands), gc((size_t)P.G * G.nbands);
+            std::vector<int> gend((size_t)P.G * G.nbands), gc((size_t)P.G * G.nbands), gr((size_t)P.G * G.nbands);
             for (int w = 0; w < G.nbands; w++)
                 for (int g0 = 0, g1; g0 < P.G; g0 = g1) {
                     int rows_tot = 0;
@@ -768,16 +782,18 @@ struct Impl : ImplBase {
                         rows_tot += bihi[i] - bilo[i];
                     }
                     if (g1 == g0) return FEWHA_ERR_GEOMETRY;  // rows_chunk >= max_rows
-                    for (int g = g0, c = 0; g < g1; g++) {
+                    for (int g = g0, c = 0, r = 0; g < g1; g++) {
                         const size_t i = (size_t)g * G.nbands + w;
                         gend[i] = g1;
                         gc[i] = c;
-                        c += (bihi[i] - bilo[i]) * P.m;
+                        gr[i] = r;
+                        c += (bihi[i] - bilo[i]) * P.gm[g];
+                        r += bihi[i] - bilo[i];
                     }
                 }
-            if ((st = upb(gend, &G.band_gend)) || (st = upb(gc, &G.band_gc))) return st;
+            if ((st = upb(gend, &G.band_gend)) || (st = upb(gc, &G.band_gc)) || (st = upb(gr, &G.band_gr))) return st;
             // y-contraction lists: for band row r of band w and the group that
-            // starts at g0, the staged row (gc/m + pupil row - ilo) and weight of
+            // starts at g0, the staged row (gr + pupil row - ilo) and weight of
             // each tap, guide star after guide star
             int ybr = 1, ymax = 1;
             for (int w = 0; w < G.nbands; w++) ybr = std::max(ybr, brs[w]);
@@ -786,10 +802,11 @@ struct Impl : ImplBase {
                 const int a = br0[w] + r, lo = P.alo[t * FEWHA_MAX_GRID + a], hi = P.ahi[t * FEWHA_MAX_GRID + a];
                 const size_t i = (size_t)g * G.nbands + w;
                 int cnt = 0;
+                const size_t tb = P.tab(g, bl[w], 1);
                 for (int j = lo; j < hi; j++, cnt++) {
                     if (!out) continue;
-                    const double w0 = P.fw[t * P.m + j];
-                    out->push_back({gc[i] / P.m + (j - bilo[i]), P.fk[t * P.m + j] == a ? 1.0 - w0 : w0});
+                    const double w0 = P.fw[tb + j];
+                    out->push_back({gr[i] + (j - bilo[i]), P.fk[tb + j] == a ? 1.0 - w0 : w0});
                 }
                 return cnt;
             };
@@ -847,6 +864,15 @@ struct Impl : ImplBase {
         G.ns = P.ns;
         G.m = P.m;
         G.n = P.n;
+        for (int g = 0; g < P.G; g++) {
+            G.gs_ns[g] = P.gns[g];
+            G.gs_m[g] = P.gm[g];
+            G.gs_tab[g] = P.tab_off[g];
+            G.gs_psi[g] = P.psi_off[g];
+            G.gs_sl[g] = P.slope_off[g];
+            G.gs_mask[g] = P.mask_off[g];
+        }
+        G.m_max = P.m_max;
         for (int l = 0; l < P.L; l++) {
             G.lay_n[l] = P.geom.layers[l].n;
             G.lay_J[l] = P.geom.layers[l].J;
@@ -869,9 +895,9 @@ struct Impl : ImplBase {
             int dev0, nsm0;
             CK(cudaGetDevice(&dev0));
             CK(cudaDeviceGetAttribute(&nsm0, cudaDevAttrMultiProcessorCount, dev0));
-            if (tiles_for(grid > 0 ? grid : nsm0, &G.tile_y, &G.tile_x)) return FEWHA_ERR_GEOMETRY;
-            G.tiles_y = (P.m + G.tile_y - 1) / G.tile_y;
-            G.tiles_x = (P.m + G.tile_x - 1) / G.tile_x;
+            int ty, tx;
+            if (tiles_for(grid > 0 ? grid : nsm0, &ty, &tx)) return FEWHA_ERR_GEOMETRY;
+            set_tiles(G, ty, tx);
         }
         int st;
         if ((st = up(P.fk, &G.fk)) || (st = up(P.alo, &G.alo)) || (st = up(P.ahi, &G.ahi))) return st;
@@ -897,10 +923,10 @@ struct Impl : ImplBase {
                     if (hi - lo > kAdjW) return FEWHA_ERR_GEOMETRY;
                     alo[t * FEWHA_MAX_GRID + k] = lo;
                     acnt[t * FEWHA_MAX_GRID + k] = hi - lo;
+                    const size_t tb = P.tab((int)(t / (2 * P.L)), (int)((t / 2) % P.L), (int)(t % 2));
                     for (int j = lo; j < hi; j++) {
-                        double w0 = P.fw[t * P.m + j];
-                        aw[(t * FEWHA_MAX_GRID + k) * kAdjW + (j - lo)] =
-                            (T)(P.fk[t * P.m + j] == k ? 1.0 - w0 : w0);
+                        double w0 = P.fw[tb + j];
+                        aw[(t * FEWHA_MAX_GRID + k) * kAdjW + (j - lo)] = (T)(P.fk[tb + j] == k ? 1.0 - w0 : w0);
                     }
                 }
             if ((st = up(alo, &G.adj_lo)) || (st = up(acnt, &G.adj_cnt)) || (st = up(aw, &G.adj_w))) return st;
@@ -911,14 +937,14 @@ struct Impl : ImplBase {
         }
         if ((st = alloc((size_t)P.n, &base.nodal)) || (st = alloc((size_t)P.n, &base.u)) ||
             (st = alloc((size_t)P.n, &base.wq)) ||
-            (st = alloc((size_t)P.G * P.m * P.m, &base.psi)) || (st = alloc((size_t)P.n / 4 + 1, &base.ll)) ||
+            (st = alloc((size_t)P.psi_off[P.G], &base.psi)) || (st = alloc((size_t)P.n / 4 + 1, &base.ll)) ||
             (st = alloc((size_t)kSlots * kMaxCtas, &base.part)) || (st = alloc((size_t)1, &base.rec)))
             return st;
         if constexpr (std::is_same<T, S>::value) {
             base.nodal_t = base.nodal;
             base.psi_t = base.psi;
         } else {  // BF16 storage: the residual replacement stores its intermediates in T
-            if ((st = alloc((size_t)P.n, &base.nodal_t)) || (st = alloc((size_t)P.G * P.m * P.m, &base.psi_t)))
+            if ((st = alloc((size_t)P.n, &base.nodal_t)) || (st = alloc((size_t)P.psi_off[P.G], &base.psi_t)))
                 return st;
         }
         // launch geometry: dynamic shared memory = max over phases
@@ -1043,10 +1069,10 @@ struct Impl : ImplBase {
     // C_eta^{-1} per slope: 1/sigma_g^2 on lit subapertures, 0 elsewhere
     std::vector<T> weight_table() const
     {
-        std::vector<T> wm((size_t)P.G * P.ns * P.ns);
+        std::vector<T> wm((size_t)P.mask_off[P.G]);
         for (int g = 0; g < P.G; g++)
-            for (int i = 0; i < P.ns * P.ns; i++)
-                wm[(size_t)g * P.ns * P.ns + i] = P.mask[i] ? (T)P.geom.gs[g].weight : T(0);
+            for (long i = P.mask_off[g]; i < P.mask_off[g + 1]; i++)
+                wm[i] = P.mask[i] ? (T)P.geom.gs[g].weight : T(0);
         return wm;
     }
 
@@ -1273,6 +1299,8 @@ struct Impl : ImplBase {
 
     int pol_slopes(const void *s_in, const void *a, void *s_out, cudaStream_t s) override
     {
+        for (int g = 0; g < P.G; g++)  // the mirror's actuators sit on the geometry's pupil grid
+            if (P.gns[g] != P.ns) return FEWHA_ERR_GEOMETRY;
         k_pol<T, S><<<256, 256, 0, s>>>(static_cast<const S *>(s_in), static_cast<const T *>(a),
                                         static_cast<S *>(s_out), P.G, P.ns);
         return launch_check();
@@ -1294,7 +1322,7 @@ struct Impl : ImplBase {
         if (nvec < 1 || nvec > kMaxVec || ldx < P.n || ldy < P.n) return FEWHA_ERR_ARG;
         auto up256 = [](size_t v) { return (v + 255) & ~(size_t)255; };
         if (!multi_buf) {
-            multi_stride = up256((size_t)P.n * sizeof(S)) + up256((size_t)P.G * P.m * P.m * sizeof(S)) +
+            multi_stride = up256((size_t)P.n * sizeof(S)) + up256((size_t)P.psi_off[P.G] * sizeof(S)) +
                            up256((size_t)P.n * sizeof(T));
             if (alloc(multi_stride * kMaxVec, &multi_buf)) return FEWHA_ERR_NOMEM;
         }
@@ -1309,16 +1337,13 @@ struct Impl : ImplBase {
             unsigned char *b = multi_buf + (size_t)v * multi_stride;
             A.nodal = reinterpret_cast<S *>(b);
             A.psi = reinterpret_cast<S *>(b + up256((size_t)P.n * sizeof(S)));
-            A.u = reinterpret_cast<T *>(b + up256((size_t)P.n * sizeof(S)) + up256((size_t)P.G * P.m * P.m * sizeof(S)));
+            A.u = reinterpret_cast<T *>(b + up256((size_t)P.n * sizeof(S)) + up256((size_t)P.psi_off[P.G] * sizeof(S)));
             A.part = base.part + (size_t)v * per;  // disjoint partial-sum columns
             A.x = static_cast<const T *>(x) + (size_t)v * ldx;
             A.y = static_cast<T *>(y) + (size_t)v * ldy;
             A.cta0 = v * per;
             A.ncta = per;
-            A.geo.tile_y = ty;
-            A.geo.tile_x = tx;
-            A.geo.tiles_y = (P.m + ty - 1) / ty;
-            A.geo.tiles_x = (P.m + tx - 1) / tx;
+            set_tiles(A.geo, ty, tx);
             A.smem_bytes = sm;
             A.trace = nullptr;
             A.trace_cap = 0;
@@ -1341,7 +1366,7 @@ struct Impl : ImplBase {
         const size_t o_part = up256(o_rec + sizeof(Record));
         const size_t o_nodal = up256(o_part + (size_t)kSlots * kMaxCtas * sizeof(double));
         const size_t o_psi = up256(o_nodal + (size_t)P.n * sizeof(S));
-        const size_t o_u = up256(o_psi + (size_t)P.G * P.m * P.m * sizeof(S));
+        const size_t o_u = up256(o_psi + (size_t)P.psi_off[P.G] * sizeof(S));
         const size_t need = up256(o_u + (size_t)P.n * sizeof(T));
         if (need > bytes) return FEWHA_ERR_SCRATCH;
         unsigned char *base_p = static_cast<unsigned char *>(scratch);
@@ -1405,10 +1430,7 @@ struct Impl : ImplBase {
         Args<T, S> A = solve_args(sl, c, st, o, stats);
         A.cta0 = cta0;
         A.ncta = nct;
-        A.geo.tile_y = ty;
-        A.geo.tile_x = tx;
-        A.geo.tiles_y = (P.m + ty - 1) / ty;
-        A.geo.tiles_x = (P.m + tx - 1) / tx;
+        set_tiles(A.geo, ty, tx);
         A.smem_bytes = sm;
         A.trace = nullptr;
         A.trace_cap = 0;

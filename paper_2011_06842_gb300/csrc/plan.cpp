@@ -140,18 +140,46 @@ int build_plan(const fewha_geometry &g, Plan &p)
     if (!daubechies_taps(g.wavelet_N, p.taps)) return FEWHA_ERR_ARG;
     for (int k = 0; k < p.G; k++) {
         const fewha_gs &s = g.gs[k];
-        if (!std::isfinite(s.theta_x) || !std::isfinite(s.theta_y) || !(s.weight >= 0)) return FEWHA_ERR_ARG;
+        if (!std::isfinite(s.theta_x) || !std::isfinite(s.theta_y) || !(s.weight >= 0) || s.n_sub < 0 ||
+            s.n_sub > 4095)
+            return FEWHA_ERR_ARG;
     }
 
-    // lit subapertures: centre radius within [obstruction D/2, D/2]
-    p.mask.assign((size_t)p.ns * p.ns, 0);
+    // sensors: sizes and block offsets
+    p.gns.resize(p.G);
+    p.gm.resize(p.G);
+    p.tab_off.resize(p.G);
+    p.psi_off.assign(p.G + 1, 0);
+    p.slope_off.assign(p.G + 1, 0);
+    p.mask_off.assign(p.G + 1, 0);
+    p.m_max = 0;
+    long tab_total = 0;
+    for (int k = 0; k < p.G; k++) {
+        const int ns = g.gs[k].n_sub > 0 ? g.gs[k].n_sub : g.n_sub;
+        p.gns[k] = ns;
+        p.gm[k] = ns + 1;
+        p.m_max = std::max(p.m_max, ns + 1);
+        p.tab_off[k] = tab_total;
+        tab_total += 2L * g.n_layers * (ns + 1);
+        p.psi_off[k + 1] = p.psi_off[k] + (long)(ns + 1) * (ns + 1);
+        p.slope_off[k + 1] = p.slope_off[k] + 2L * ns * ns;
+        p.mask_off[k + 1] = p.mask_off[k] + (long)ns * ns;
+    }
+
+    // lit subapertures: centre radius within [obstruction D/2, D/2]; the
+    // single subaperture of a 1x1 sensor sees the whole pupil (always lit)
+    p.mask.assign((size_t)p.mask_off[p.G], 0);
     double rin = 0.5 * g.obstruction * g.D, rout = 0.5 * g.D;
-    for (int i = 0; i < p.ns; i++)
-        for (int j = 0; j < p.ns; j++) {
-            double cx = -0.5 * g.D + (j + 0.5) * p.ds, cy = -0.5 * g.D + (i + 0.5) * p.ds;
-            double r = std::sqrt(cx * cx + cy * cy);
-            p.mask[(size_t)i * p.ns + j] = (r >= rin && r <= rout) ? 1 : 0;
-        }
+    for (int k = 0; k < p.G; k++) {
+        const int ns = p.gns[k];
+        const double dsg = g.D / ns;
+        for (int i = 0; i < ns; i++)
+            for (int j = 0; j < ns; j++) {
+                double cx = -0.5 * g.D + (j + 0.5) * dsg, cy = -0.5 * g.D + (i + 0.5) * dsg;
+                double r = std::sqrt(cx * cx + cy * cy);
+                p.mask[(size_t)p.mask_off[k] + (size_t)i * ns + j] = (ns == 1 || (r >= rin && r <= rout)) ? 1 : 0;
+            }
+    }
 
     // layer grids
     p.lay_d.resize(p.L);
@@ -178,8 +206,8 @@ int build_plan(const fewha_geometry &g, Plan &p)
 
     // interpolation tables of P_g and the ranges of P_g^T
     size_t nt = (size_t)p.G * p.L * 2;
-    p.fk.assign(nt * p.m, 0);
-    p.fw.assign(nt * p.m, 0.0);
+    p.fk.assign((size_t)tab_total, 0);
+    p.fw.assign((size_t)tab_total, 0.0);
     p.alo.assign(nt * FEWHA_MAX_GRID, 0);
     p.ahi.assign(nt * FEWHA_MAX_GRID, 0);
     for (int k = 0; k < p.G; k++) {
@@ -188,14 +216,17 @@ int build_plan(const fewha_geometry &g, Plan &p)
             const fewha_layer &ly = g.layers[l];
             double sc = cone(s, ly.h), d = p.lay_d[l];
             for (int ax = 0; ax < 2; ax++) {
-                size_t base = ((size_t)k * p.L + l) * 2 + ax;
+                size_t base = ((size_t)k * p.L + l) * 2 + ax;  // P_g^T ranges
+                const size_t tb = p.tab(k, l, ax);             // P_g tables of this sensor
+                const int mg = p.gm[k];
+                const double dsg = g.D / p.gns[k];
                 double shift = (ax == 0 ? s.theta_x : s.theta_y) * ly.h;
-                for (int j = 0; j < p.m; j++) {
-                    double x = -0.5 * g.D + j * p.ds;
+                for (int j = 0; j < mg; j++) {
+                    double x = -0.5 * g.D + j * dsg;
                     double f = (sc * x + shift) / d + 0.5 * ly.n;
                     int kk = (int)std::floor(f);
                     if (kk < 0 || kk + 1 > ly.n - 1) return FEWHA_ERR_GEOMETRY;
-                    p.fk[base * p.m + j] = kk;
+                    p.fk[tb + j] = kk;
                     double w = f - kk;
                     if (g.precision == FEWHA_BF16S) {  // weights stored in bfloat16
                         float wf = (float)w;
@@ -206,12 +237,12 @@ int build_plan(const fewha_geometry &g, Plan &p)
                         std::memcpy(&wf, &u, 4);
                         w = wf;
                     }
-                    p.fw[base * p.m + j] = w;
+                    p.fw[tb + j] = w;
                 }
                 for (int node = 0; node < ly.n; node++) {
-                    int lo = p.m, hi = 0;
-                    for (int j = 0; j < p.m; j++) {
-                        int kk = p.fk[base * p.m + j];
+                    int lo = mg, hi = 0;
+                    for (int j = 0; j < mg; j++) {
+                        int kk = p.fk[tb + j];
                         if (kk == node || kk + 1 == node) {
                             lo = std::min(lo, j);
                             hi = std::max(hi, j + 1);

@@ -32,7 +32,7 @@ class FewhaError(RuntimeError):
 
 class GS(C.Structure):
     _fields_ = [("theta_x", C.c_double), ("theta_y", C.c_double), ("H", C.c_double),
-                ("weight", C.c_double)]
+                ("weight", C.c_double), ("n_sub", C.c_int), ("pad", C.c_int)]
 
 
 class LAYER(C.Structure):
@@ -203,7 +203,7 @@ def make_geometry(geom, noise_w, precision="f64", tile=0, grid=0) -> GEOMETRY:
         raise ValueError("too many guide stars or layers")
     g.n_gs = len(geom.gs)
     for i, (s, w) in enumerate(zip(geom.gs, noise_w)):
-        g.gs[i] = GS(s.theta_x, s.theta_y, s.H, float(w))
+        g.gs[i] = GS(s.theta_x, s.theta_y, s.H, float(w), int(getattr(s, "n_sub", 0) or 0), 0)
     g.n_layers = len(geom.layers)
     for i, l in enumerate(geom.layers):
         g.layers[i] = LAYER(l.h, l.cn2, l.delta, l.n, l.J)

@@ -9,12 +9,10 @@ M composes about six of them, so ||M_bf16 x - M x|| <= 6 u ||M x|| ~ 1.2e-2 in t
 worst case.  The test allows 1.5e-2.  For a time step (a few CG iterations)
 the same per-application perturbation enters every iteration; the sequence
 test chains 500 time steps, so each run follows its own trajectory (CG
-amplifies every difference over the frames): it reports per frame the relative
-L2 error of the layer coefficients, the relative error in the energy norm
-||e||_M / ||c||_M (the data-fit norm the solver minimises), and the relative
-error of ||r||, and guards them with regression bounds set with margin over
-the values measured on a GB300 (FP32: layer L2 median 2e-4, max 5e-3;
-BF16S: layer L2 median 0.11, max 0.24, dominated by weakly observed modes).
+amplifies every difference over the frames) and is bounded in the energy
+norm ||e||_M / ||c||_M, the norm the solver minimises (derivation in its
+docstring); the relative L2 error of the layer coefficients, dominated by
+weakly observed modes, is reported beside it.
 """
 import numpy as np
 import pytest
@@ -62,42 +60,64 @@ def test_bf16_operator_and_rhs(lib, name):
 
 def test_mixed_precision_sequence_500_frames(lib):
     """The mixed-precision workload: tiny geometry, 500 frozen-flow frames,
-    4 augmented PCG iterations per frame; BF16S and FP32 against the FP64
-    oracle, relative L2 error of the layer coefficients and of ||r|| per frame."""
+    4 augmented PCG iterations per frame; BF16S (with and without the
+    residual replacement every 2 iterations) and FP32 against the FP64
+    oracle on the same slopes (the bfloat16-rounded ones for BF16S).
+
+    Asserted, in the energy norm ||e||_M / ||c||_M (the norm CG minimises):
+    the BF16S operator is M + E with ||E x|| <= 6 u ||M x|| per application
+    (module docstring), and the right-hand side carries at most the same
+    relative perturbation; a warm-restarted solve of a few iterations
+    resolves the solution only in the directions its Krylov space reaches,
+    where the computed iterate differs from the exact one by at most the
+    perturbation of one application of M plus that of b: 12 u = 2.3e-2 in
+    the energy norm, the bound on every frame (6 u on the median).  FP32: the
+    arithmetic itself (every step rounds at u_32 = 2^-24) limits the forward
+    error of CG to the level kappa_1 u_32, kappa_1 = 9.1e4 the preconditioned
+    condition number of this geometry (Lanczos diagnostics, test_gpu_
+    diagnostics): 5.4e-3 on the median and 5 kappa_1 u_32 = 2.7e-2 on every
+    frame.  (An FP64 twin run on slopes perturbed by 2^-24 moves by only
+    ~1e-7 here: the recycled basis' Gram matrix stays well conditioned,
+    cond ~ 10, so the FP32 deviation is the arithmetic's, not an
+    amplification of the input.)  The layer L2 error (the weakly observed
+    modes: large in the coefficient norm, small in the energy norm) and the
+    gap between the solver's residual and the true one b - M c are reported
+    per frame."""
     geom = configs.tiny()
     nf = 500
     sim = FrozenFlowSensors(geom, seed=31)
     s, w = sim.sequence(nf, seed=32)
-    s64 = s.numpy()
     o = Oracle(geom, w)
-    st_o = o.new_state(8)
     runs = {}
-    for prec in ("bf16s", "f32"):
+    for name, prec, tre in (("bf16s", "bf16s", 0), ("bf16s_tr2", "bf16s", 2), ("f32", "f32", 0)):
         f = lib.Fewha(geom, w, prec)
-        runs[prec] = (f, f.new_state(8), torch.zeros(o.n, dtype=torch.float32, device="cuda"),
-                      s.to(f.slope_dtype).cuda())
-    errs = {p: [] for p in runs}
-    enrg = {p: [] for p in runs}
-    rres = {p: [] for p in runs}
+        sd = s.to(f.slope_dtype)
+        runs[name] = dict(f=f, st=f.new_state(8), c=torch.zeros(o.n, dtype=torch.float32, device="cuda"),
+                          sd=sd.cuda(), s64=sd.double().numpy(), st_o=o.new_state(8), tre=tre,
+                          l2=[], energy=[], gap=[], rres=[])
     for t in range(nf):
-        ro = o.solve(s64[t], st_o, max_iter=4, augmented=True)
-        cm = o.apply_op(st_o["c"]) @ st_o["c"]
-        for p, (f, st, c, sd) in runs.items():
-            rg = f.read_stats(f.solve(sd[t], c, st, 4))
+        for name, r in runs.items():
+            ro = o.solve(r["s64"][t], r["st_o"], max_iter=4, augmented=True)
+            rg = r["f"].read_stats(r["f"].solve(r["sd"][t], r["c"], r["st"], 4, true_res_every=r["tre"]))
             assert rg["status"] == 0
-            cg = c.double().cpu().numpy()
-            e = cg - st_o["c"]
-            errs[p].append(rel(cg, st_o["c"]))
+            cg = r["c"].double().cpu().numpy()
+            co = r["st_o"]["c"]
+            e = cg - co
+            r["l2"].append(rel(cg, co))
+            r["rres"].append(abs(rg["rel_res"] - ro["rel_res"]) / ro["rel_res"])
             if t % 10 == 0:
-                enrg[p].append(np.sqrt(max(o.apply_op(e) @ e, 0.0) / cm))
-            rres[p].append(abs(rg["rel_res"] - ro["rel_res"]) / ro["rel_res"])
-    for p in runs:
-        e = np.array(errs[p])
-        print("%s vs FP64 oracle over %d frames: layer L2 error median %.2e max %.2e; "
-              "energy-norm error median %.2e max %.2e; ||r|| relative error median %.2e max %.2e"
-              % (p, nf, np.median(e), e.max(), np.median(enrg[p]), np.max(enrg[p]),
-                 np.median(rres[p]), np.max(rres[p])))
-    assert np.median(errs["f32"]) < 1e-3 and max(errs["f32"]) < 2e-2
-    assert np.median(rres["f32"]) < 1e-3
-    assert np.median(errs["bf16s"]) < 0.3 and max(errs["bf16s"]) < 0.6
-    assert np.median(rres["bf16s"]) < 2e-2
+                r["energy"].append(np.sqrt(max(o.apply_op(e) @ e, 0.0) / (o.apply_op(co) @ co)))
+                b = o.rhs(r["s64"][t])
+                r["gap"].append(np.linalg.norm(r["st"].r_prev.double().cpu().numpy() - (b - o.apply_op(cg)))
+                                / np.linalg.norm(b))
+    for name, r in runs.items():
+        print("%s vs FP64 oracle over %d frames: energy-norm error median %.2e max %.2e; layer L2 error "
+              "median %.2e max %.2e; ||r|| relative error median %.2e; ||r - (b - Mc)||/||b|| median %.2e "
+              "max %.2e" % (name, nf, np.median(r["energy"]), max(r["energy"]), np.median(r["l2"]), max(r["l2"]),
+                            np.median(r["rres"]), np.median(r["gap"]), max(r["gap"])))
+    for name in ("bf16s", "bf16s_tr2"):
+        assert max(runs[name]["energy"]) < 12 * U_BF16 and np.median(runs[name]["energy"]) < 6 * U_BF16
+    kappa_u = 9.1e4 * 2.0 ** -24
+    assert max(runs["f32"]["energy"]) < 5 * kappa_u and np.median(runs["f32"]["energy"]) < kappa_u
+    # the replacement keeps the solver's residual the true one of the BF16S problem
+    assert np.median(runs["bf16s_tr2"]["gap"]) < np.median(runs["bf16s"]["gap"])
