@@ -356,6 +356,17 @@ int fewha_batch_launch(void *batch, cudaStream_t stream);
 #define FEWHA_DEFLATE_INFO_DOUBLES 16
 int fewha_conv3x3_fwd(const float *in, long in_bs, long in_cs, int Cin, const float *w, const float *bias,
                       float *out, long out_bs, long out_cs, int Cout, int B, int H, int W, int relu, cudaStream_t s);
+/* fewha_conv3x3_fwd_tc: the same forward convolution on the tensor cores
+ * (tcgen05 implicit GEMM: 128 output pixels per CTA x all output channels,
+ * K = 9 Cin): operands rounded to bfloat16, products accumulated in FP32,
+ * then bias and ReLU in FP32.  Cin, Cout <= 32.  status_dev (device int, may
+ * be NULL) receives FEWHA_ERR_TIMEOUT if a CTA's wait for its tensor-core
+ * work ran out (it then frees its tensor memory and leaves its outputs
+ * unwritten); it is not cleared by the call.  For inference; training keeps
+ * the FP32 kernels. */
+int fewha_conv3x3_fwd_tc(const float *in, long in_bs, long in_cs, int Cin, const float *w, const float *bias,
+                         float *out, long out_bs, long out_cs, int Cout, int B, int H, int W, int relu,
+                         int *status_dev, cudaStream_t s);
 int fewha_conv3x3_bwd_data(const float *gout, long gout_bs, long gout_cs, int Cout, const float *w, float *gin,
                            long gin_bs, long gin_cs, int Cin, int B, int H, int W, cudaStream_t s);
 long fewha_conv3x3_wgrad_workspace(int Cin, int Cout, int B, int H, int W);

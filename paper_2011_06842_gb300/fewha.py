@@ -155,6 +155,7 @@ def load_library(path=LIB_PATH):
     L, I, F = C.c_long, C.c_int, C.c_float
     learned = {
         "fewha_conv3x3_fwd": [vp, L, L, I, vp, vp, vp, L, L, I, I, I, I, I, vp],
+        "fewha_conv3x3_fwd_tc": [vp, L, L, I, vp, vp, vp, L, L, I, I, I, I, I, vp, vp],
         "fewha_conv3x3_bwd_data": [vp, L, L, I, vp, vp, L, L, I, I, I, I, vp],
         "fewha_conv3x3_bwd_weight": [vp, L, L, I, vp, L, L, I, I, I, I, vp, vp, I, vp, vp],
         "fewha_relu_bwd": [vp, vp, L, vp],
@@ -191,7 +192,7 @@ def exported_symbols():
             "fewha_mse_grad", "fewha_adam_step", "fewha_scale", "fewha_learned_targets",
             "fewha_deflate_warm_start", "fewha_mcao_create", "fewha_mcao_n_actuators", "fewha_mcao_fit",
             "fewha_mcao_destroy", "fewha_get_launch_info", "fewha_set_noise", "fewha_read_probe", "fewha_set_pt_bands",
-            "fewha_batch_create_ex", "fewha_batch_tiles"]
+            "fewha_batch_create_ex", "fewha_batch_tiles", "fewha_conv3x3_fwd_tc"]
 
 
 def make_geometry(geom, noise_w, precision="f64", tile=0, grid=0) -> GEOMETRY:

@@ -272,3 +272,38 @@ def test_training_and_gain_tiny(lib):
     assert res["learned"]["r0_ratio_taken"] is None or res["learned"]["r0_ratio_taken"] < 1.0
     assert res["learned"]["iterations"] <= res["plain"]["iterations"] + 0.5
     f.close()
+
+
+@pytest.mark.parametrize("B,Cin,Cout,H,W", [(5, 32, 32, 128, 128), (4, 4, 32, 64, 64), (2, 32, 5, 33, 16),
+                                            (1, 7, 13, 9, 21)])
+def test_conv_forward_tensor_cores(lib, B, Cin, Cout, H, W):
+    """fewha_conv3x3_fwd_tc (tcgen05, BF16 operands, FP32 accumulation)
+    against the FP64 oracle convolution, elementwise: rounding x and w to
+    bfloat16 perturbs every product by at most 2 u + u^2 (u = 2^-9) of
+    |w||x|, and FP32 accumulation of K = 9 Cin products adds at most
+    K u_32 of the same, so |y - y_exact| <= (2 u + u^2 + K u_32) (|w| * |x|)
+    + u_32 |y| per output (before ReLU; ReLU is 1-Lipschitz).  Shapes: the
+    ELT network's 32 -> 32 layer on the 128^2 batch, its 4 -> 32 input layer,
+    its 32 -> 5 output layer, and a ragged tile (H W not a multiple of 128)."""
+    _, L = lib
+    rng = np.random.default_rng(B * 7 + Cin)
+    x, w, b = rng.standard_normal((B, Cin, H, W)), rng.standard_normal((Cout, Cin, 3, 3)), rng.standard_normal(Cout)
+    hw = H * W
+    out = torch.full((B, Cout, H, W), np.nan, dtype=torch.float32, device="cuda")
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    for relu in (0, 1):
+        assert L.fewha_conv3x3_fwd_tc(ptr(dev(x)), Cin * hw, hw, Cin, ptr(dev(w)), ptr(dev(b)), ptr(out), Cout * hw,
+                                      hw, Cout, B, H, W, relu, ptr(status), S()) == 0
+        torch.cuda.synchronize()
+        assert int(status.item()) == 0
+        y = out.double().cpu().numpy()
+        exact = OL.conv3x3(x, w, b, relu=bool(relu))
+        pre = OL.conv3x3(x, w, b, relu=False)
+        mag = OL.conv3x3(np.abs(x), np.abs(w), None, relu=False)
+        u, u32 = 2.0 ** -9, 2.0 ** -24
+        bound = ((2 * u + u * u + 9 * Cin * u32) * mag + u32 * (np.abs(pre) + np.abs(b)[None, :, None, None])
+                 + 1e-30)
+        assert np.all(np.isfinite(y))
+        assert np.all(np.abs(y - exact) <= bound), np.max(np.abs(y - exact) / bound)
+        assert rel(y, exact) < 1e-2  # and the bfloat16 operands are really in use:
+        assert rel(y, exact) > 1e-5
