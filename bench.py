@@ -745,7 +745,8 @@ def run_learned(args):
     x = torch.randn(learned.N_DIR, f.n, device="cuda")
     y = torch.empty_like(x)
     cost = {"rhs_us": ev_us(lambda: f.rhs(se[0], out=y[0])),
-            "network_forward_us": ev_us(lambda: lw.net.forward(lw.ring[4].data_ptr(), -f.n, y)),
+            "network_forward_us": ev_us(lambda: lw.net.forward(lw.ring[4].data_ptr(), -f.n, y, tensor_cores=True)),
+            "network_forward_fp32_us": ev_us(lambda: lw.net.forward(lw.ring[4].data_ptr(), -f.n, y)),
             "apply_multi5_us": ev_us(lambda: f.apply_op_multi(x, out=y)),
             "apply_single_us": ev_us(lambda: f.apply_op(x[0], out=y[1]))}
     out = {"metric": METRIC, "mode": "learned warm start", "unit": "frames/s",
@@ -754,7 +755,8 @@ def run_learned(args):
            "data": "synthetic: seeded von Karman frozen-flow screens seen by SH sensors, SNR %g" % geom.snr,
            "config": {"workload": workload_name(geom, args) + ", learned warm start",
                       "rtol": args.rtol, "max_iter": args.max_iter, "k_recycle": args.k,
-                      "network": "3x3 conv 4-32-32-5, ReLU", "train_frames": args.learned_train,
+                      "network": "3x3 conv 4-32-32-5, ReLU; inference on tcgen05 (bfloat16 operands, FP32 "
+                                 "accumulation), training on FP32 kernels", "train_frames": args.learned_train,
                       "eval_frames": args.learned_eval, "epochs": args.epochs,
                       "l2": "flushed before every frame" if flush is not None else "not flushed"},
            "slopes_generation_s": t_slopes, "study": res, "cost_breakdown": cost, "clocks": clocks}

@@ -137,6 +137,13 @@ typedef struct {
      * then see the true residual.  0 = off (the paper: Algorithms 1-3 keep
      * the recurrence residual).  0..FEWHA_MAX_ITER. */
     int true_res_every;
+    /* 1: this time step's right-hand side is already folded into the state
+     * (b_prev = b, r_prev = the warm-restart residual r0), as
+     * fewha_deflate_warm_start leaves it: the solve skips the right-hand-side
+     * phases and does not read the slopes (s may be NULL).  0: Algorithm 3's
+     * right-hand side and warm restart from s. */
+    int rhs_in_state;
+    int pad;
 } fewha_solve_opts;
 
 /* Written on the device at the end of fewha_solve. */
@@ -345,9 +352,10 @@ int fewha_batch_launch(void *batch, cudaStream_t stream);
  *   r0 = (b - b_prev) + r_prev (the warm restart of Algorithm 3),
  *   w = (D^T Q)^{-1} D^T r0 in FP64 with a Cholesky factorisation that drops
  *   directions whose pivot is below 1e-10 of their diagonal.  Taken only when
- *   ||r0 - Q w|| < ||r0||; then c += D w, r_prev <- r0 - Q w, b_prev <- b, so
- *   that the next fewha_solve starts from the corrected residual; otherwise
- *   c, b_prev and r_prev are left as they are (the plain warm start).
+ *   ||r0 - Q w|| < ||r0||; then c += D w and r_prev <- r0 - Q w; otherwise c
+ *   is left as it is and r_prev <- r0 (the plain warm start).  Either way
+ *   b_prev <- b: this time step's right-hand side is folded into the state,
+ *   and the fewha_solve that follows is called with rhs_in_state = 1.
  *   r0_work: n floats; work: FEWHA_DEFLATE_WORK_DOUBLES; info:
  *   FEWHA_DEFLATE_INFO_DOUBLES, info[0] taken (0/1), [1] ||r0 - Q w||,
  *   [2] ||r0||, [3] directions kept, [4..4+nd) w.  1 <= nd <= FEWHA_MAX_DEFLATE. */

@@ -152,7 +152,11 @@ def deflate_warm_start(b, D, Q, c, b_prev, r_prev):
     """Galerkin correction of the warm start over the rows of D (Q = M D).
 
     r0 = (b - b_prev) + r_prev; w solves sym(D^T Q) w = D^T r0; the correction
-    c + D w with residual r0 - Q w is taken if ||r0 - Q w|| < ||r0||.
+    c + D w with residual r0 - Q w is taken if ||r0 - Q w|| < ||r0||.  Either
+    way this time step's right-hand side is folded into the state: b_prev <- b
+    and r_prev <- the warm-restart residual (r0 - Q w if taken, else r0, the
+    plain warm start of Algorithm 3), so that the solve that follows need not
+    form the right-hand side again.
     Returns (taken, c_new, b_prev_new, r_prev_new, w, ||r0 - Q w||, ||r0||).
     Directions are assumed linearly independent (no pivot is dropped)."""
     b, D, Q = (np.asarray(a, dtype=np.float64) for a in (b, D, Q))
@@ -165,4 +169,4 @@ def deflate_warm_start(b, D, Q, c, b_prev, r_prev):
     n1, n0 = float(np.linalg.norm(r1)), float(np.linalg.norm(r0))
     if n1 < n0:
         return True, c + D.T @ w, b.copy(), r1, w, n1, n0
-    return False, c.copy(), b_prev.copy(), r_prev.copy(), w, n1, n0
+    return False, c.copy(), b.copy(), r0, w, n1, n0

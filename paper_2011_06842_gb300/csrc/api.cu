@@ -319,7 +319,7 @@ int fewha_rhs(void *handle, const void *s, void *b, cudaStream_t stream)
 int fewha_solve(void *handle, const void *s, void *c, const fewha_state *st, const fewha_solve_opts *o,
                 fewha_stats *stats, cudaStream_t stream)
 {
-    if (!handle || !s || !c || !st || !o) return FEWHA_ERR_ARG;
+    if (!handle || !c || !st || !o || (!s && !o->rhs_in_state)) return FEWHA_ERR_ARG;
     if (!st->b_prev || !st->r_prev || !st->basis_P || !st->basis_Q || !st->basis_pq || !st->meta)
         return FEWHA_ERR_ARG;
     if (!aligned16(c) || !aligned16(st->b_prev) || !aligned16(st->r_prev) || !aligned16(st->basis_P) ||
@@ -467,6 +467,7 @@ int fewha_batch_solve(void *batch, const void *const *slopes, void *const *c, co
     Batch *b = static_cast<Batch *>(batch);
     if (opts->max_iter < 1 || opts->max_iter > FEWHA_MAX_ITER || !(opts->rtol >= 0)) return FEWHA_ERR_ARG;
     if (opts->true_res_every < 0 || opts->true_res_every > FEWHA_MAX_ITER) return FEWHA_ERR_ARG;
+    if (opts->rhs_in_state) return FEWHA_ERR_ARG;  // batches form their right-hand sides
     if (opts->recycle_mode != FEWHA_RECYCLE_LAST && opts->recycle_mode != FEWHA_RECYCLE_ALL) return FEWHA_ERR_ARG;
     const int slot = b->next;
     b->next = (b->next + 1) % Batch::kRing;
@@ -499,6 +500,7 @@ int fewha_batch_bind(void *batch, const void *const *slopes, void *const *c, con
     Batch *b = static_cast<Batch *>(batch);
     if (opts->max_iter < 1 || opts->max_iter > FEWHA_MAX_ITER || !(opts->rtol >= 0)) return FEWHA_ERR_ARG;
     if (opts->true_res_every < 0 || opts->true_res_every > FEWHA_MAX_ITER) return FEWHA_ERR_ARG;
+    if (opts->rhs_in_state) return FEWHA_ERR_ARG;  // batches form their right-hand sides
     if (opts->recycle_mode != FEWHA_RECYCLE_LAST && opts->recycle_mode != FEWHA_RECYCLE_ALL) return FEWHA_ERR_ARG;
     std::vector<unsigned char> h(b->asz * b->n);
     for (int i = 0; i < b->n; i++) {

@@ -1,24 +1,32 @@
 // fewha_conv3x3_fwd_tc: the learned warm start's 3x3 convolution on the
-// 5th-generation tensor cores (tcgen05) of sm_103a, as an implicit GEMM
-//     out[p][co] = sum_k A[p][k] B[co][k],   k = ci * 9 + tap,
-// A the image patches (im2col) of 128 output pixels, B the weights, with
+// 5th-generation tensor cores (tcgen05) of sm_103a, as an implicit GEMM with
 // BF16 operands and FP32 accumulation in tensor memory (TMEM).  Not part of
 // the paper's method (the network is a predictor of the warm start).
 //
-// One CTA computes 128 consecutive output pixels of one image for every
-// output channel:
-//   1. warp 0 allocates 32 TMEM columns (the 128 x N FP32 accumulator);
-//   2. all threads write A (128 x Kp) and B (Np x Kp) into shared memory as
-//      BF16 in the canonical K-major layout without swizzle: 8-row x 16-byte
-//      core matrices, the core matrices of one 8-row group adjacent along K
-//      (128 bytes apart, the descriptor's leading-dimension offset), the
-//      8-row groups Kp / 8 * 128 bytes apart (its stride-dimension offset);
-//   3. one thread issues Kp / 16 tcgen05.mma (M = 128, N = Np, K = 16 each)
-//      and tcgen05.commit arrives on an mbarrier when they are done;
+// One CTA computes two output rows y0, y0 + 1 (W <= 128 pixels) of one image
+// for every output channel (two TMEM accumulators): D[x][co] = sum over taps (ky, kx) and input channels ci of
+// in[ci][y+ky-1][x+kx-1] w[co][ci][ky][kx].
+//   1. warp 0 allocates 64 TMEM columns (two 128 x N FP32 accumulators);
+//   2. all threads stage the four input rows y0-1 .. y0+2 once in shared
+//      memory as BF16, channel-minor: per (row, group of 8 channels) an array
+//      of RP pixels of 16 bytes (8 channels), pixel q holding x = q - 1 (zero
+//      for x outside the image and for padded channels); and the weights as
+//      per (tap, group of 8 input channels) the 8-row x 16-byte core matrices
+//      of the output channels; each 16-byte row is packed in registers and
+//      written with one store;
+//   3. one thread issues one tcgen05.mma (M = 128, N = Np, K = 16: two
+//      channel groups) per output row, tap and channel-group pair: the A
+//      operand of tap (ky, kx) for output row h is the staged row h + ky seen
+//      from pixel kx on, a K-major matrix
+//      without swizzle whose 8-pixel core matrices are 128 bytes apart
+//      (stride-dimension offset) and whose channel groups are RP * 16 bytes
+//      apart (leading-dimension offset), so no patch matrix is formed;
+//      tcgen05.commit arrives on an mbarrier when they are done;
 //   4. the CTA waits on the mbarrier (at most 0.5 s: on time-out it records
 //      FEWHA_ERR_TIMEOUT, waits once more with the same limit, frees its TMEM
-//      and returns); warps 0-3 read their 32 accumulator lanes each with
-//      tcgen05.ld, add the bias, apply ReLU and store; warp 0 frees the TMEM.
+//      and returns); warps 4h..4h+3 read accumulator h, 32 lanes (pixels)
+//      each, with tcgen05.ld, add the bias, apply ReLU and store; warp 0
+//      frees the TMEM.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -30,7 +38,8 @@ namespace {
 
 constexpr int kTcM = 128;       // output pixels per CTA (MMA M)
 constexpr int kTcThreads = 256;
-constexpr int kTcCols = 32;     // TMEM columns allocated (>= Np, a power of two >= 32)
+constexpr int kTcRows = 2;      // output rows per CTA (one accumulator of 32 TMEM columns each)
+constexpr int kTcCols = 32 * kTcRows;  // TMEM columns allocated (a power of two >= 32)
 constexpr unsigned long long kTcWaitNs = 500000000ull;  // a wait for the tensor cores gives up after 0.5 s
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -55,10 +64,21 @@ __device__ __forceinline__ uint32_t instr_desc(int n)
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kTcM >> 4) << 24);
 }
 
-// Byte offset of element (row, k) in the canonical layout of a rows x kp tile.
-__device__ __forceinline__ int tile_off(int row, int k, int kp)
+constexpr int kRP = 136;  // staged pixels per (row, channel group): x = -1 .. 128 plus slack (multiple of 8)
+// dynamic shared memory of the largest case (Cin 32, Cout 32): staged rows and weights
+constexpr size_t kTcSmemCap = (size_t)(kTcRows + 2) * 4 * kRP * 16 + (size_t)9 * 4 * 4 * 128;
+
+// 8 floats as 8 bfloat16 (round to nearest even) in one 16-byte word
+__device__ __forceinline__ uint4 pack8(const float (&v)[8])
 {
-    return (row >> 3) * (kp >> 3) * 128 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2;
+    uint4 u;
+    __nv_bfloat162 p0 = __floats2bfloat162_rn(v[0], v[1]), p1 = __floats2bfloat162_rn(v[2], v[3]);
+    __nv_bfloat162 p2 = __floats2bfloat162_rn(v[4], v[5]), p3 = __floats2bfloat162_rn(v[6], v[7]);
+    u.x = *reinterpret_cast<unsigned int *>(&p0);
+    u.y = *reinterpret_cast<unsigned int *>(&p1);
+    u.z = *reinterpret_cast<unsigned int *>(&p2);
+    u.w = *reinterpret_cast<unsigned int *>(&p3);
+    return u;
 }
 
 __device__ __forceinline__ unsigned long long now_ns()
@@ -114,18 +134,18 @@ template <int NP>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_conv3x3_tc(const float *__restrict__ in, long in_bs, long in_cs, int Cin, const float *__restrict__ w,
                  const float *__restrict__ bias, float *__restrict__ out, long out_bs, long out_cs, int Cout, int H,
-                 int W, int relu, int kp, int *status)
+                 int W, int relu, int ncg, int *status)
 {
+    // ncg: groups of 8 input channels (even: Cin padded to a multiple of 16)
     extern __shared__ __align__(1024) unsigned char tc_smem[];
     __shared__ __align__(8) unsigned long long mbar;
     __shared__ uint32_t tmem_base;
     const int tid = threadIdx.x, warp = tid >> 5;
-    const long hw = (long)H * W;
-    const int tiles = (int)((hw + kTcM - 1) / kTcM);
-    const int b = blockIdx.x / tiles;
-    const long p0 = (long)(blockIdx.x - b * tiles) * kTcM;
-    unsigned char *A = tc_smem;                       // kTcM x kp BF16
-    unsigned char *Bm = tc_smem + (size_t)kTcM * kp * 2;  // NP x kp BF16
+    const int ty = (H + kTcRows - 1) / kTcRows;  // row tiles per image
+    const int b = blockIdx.x / ty, y0 = (blockIdx.x - b * ty) * kTcRows;
+    constexpr int SR = kTcRows + 2;                                // staged input rows y0-1 .. y0+kTcRows
+    unsigned char *X = tc_smem;                                    // [SR][ncg][kRP] x 16 bytes
+    unsigned char *Wt = tc_smem + (size_t)SR * ncg * kRP * 16;     // [9][ncg][NP / 8] core matrices of 128 bytes
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
@@ -135,26 +155,38 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     }
     if (tid == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)) : "memory");
 
-    // B: weights w[co][ci][tap] at k = ci * 9 + tap, zero-padded to NP x kp
-    const int K = Cin * 9;
-    for (int e = tid; e < NP * kp; e += kTcThreads) {
-        const int n = e / kp, k = e - n * kp;
-        const float v = (n < Cout && k < K) ? w[(long)n * K + k] : 0.f;
-        *reinterpret_cast<__nv_bfloat16 *>(Bm + tile_off(n, k, kp)) = __float2bfloat16_rn(v);
-    }
-    // A: patches; consecutive threads take consecutive pixels of one (ci, tap)
-    for (int e = tid; e < kTcM * kp; e += kTcThreads) {
-        const int k = e / kTcM, m = e - k * kTcM;
-        const long p = p0 + m;
-        float v = 0.f;
-        if (k < K && p < hw) {
-            const int ci = k / 9, tap = k - ci * 9;
-            const int y = (int)(p / W) + tap / 3 - 1, x = (int)(p % W) + tap % 3 - 1;
-            if (y >= 0 && y < H && x >= 0 && x < W) v = in[(long)b * in_bs + (long)ci * in_cs + (long)y * W + x];
+    // Every 16-byte row of a core matrix holds 8 consecutive input channels:
+    // a thread packs them and writes them with one 16-byte store (threads
+    // with consecutive pixels / output channels write consecutive rows).
+    // Weights: row (tap t, channel group g, output channel co).
+    const int nb = NP >> 3;
+    for (int e = tid; e < 9 * ncg * NP; e += kTcThreads) {
+        const int t = e / (ncg * NP), g = (e / NP) % ncg, co = e % NP;
+        float v[8];
+#pragma unroll
+        for (int j = 0; j < 8; j++) {
+            const int ci = g * 8 + j;
+            v[j] = (co < Cout && ci < Cin) ? __ldg(w + ((long)co * Cin + ci) * 9 + t) : 0.f;
         }
-        *reinterpret_cast<__nv_bfloat16 *>(A + tile_off(m, k, kp)) = __float2bfloat16_rn(v);
+        *reinterpret_cast<uint4 *>(Wt + ((t * ncg + g) * nb + (co >> 3)) * 128 + (co & 7) * 16) = pack8(v);
     }
-    // the tiles become visible to the tensor core (async proxy)
+    // input: row (staged row r, channel group g, pixel q), q holding x = q - 1
+    // and staged row r input row y0 + r - 1 (zero outside the image: the halo
+    // pixels and rows beyond it)
+    for (int e = tid; e < SR * ncg * kRP; e += kTcThreads) {
+        const int r = e / (ncg * kRP), g = (e / kRP) % ncg, q = e % kRP;
+        const int yy = y0 + r - 1, x = q - 1;
+        const bool inside = yy >= 0 && yy < H && x >= 0 && x < W;
+        const float *px = in + (long)b * in_bs + (long)yy * W + x;
+        float v[8];
+#pragma unroll
+        for (int j = 0; j < 8; j++) {
+            const int ci = g * 8 + j;
+            v[j] = (inside && ci < Cin) ? __ldg(px + (long)ci * in_cs) : 0.f;
+        }
+        *reinterpret_cast<uint4 *>(X + ((r * ncg + g) * kRP + q) * 16) = pack8(v);
+    }
+    // the operands become visible to the tensor core (async proxy)
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -162,17 +194,26 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const uint32_t taddr = tmem_base;
 
     if (tid == 0) {
-        const uint32_t a0 = smem_u32(A), b0 = smem_u32(Bm), sbo = (uint32_t)(kp >> 3) * 128u;
-        const uint32_t idesc = instr_desc(NP);
-        for (int ks = 0; ks < kp / 16; ks++) {
-            const uint64_t ad = smem_desc(a0 + (uint32_t)ks * 256u, 128u, sbo);
-            const uint64_t bd = smem_desc(b0 + (uint32_t)ks * 256u, 128u, sbo);
-            const uint32_t acc = ks > 0 ? 1u : 0u;
-            asm volatile(
-                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(taddr),
-                "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
-                : "memory");
+        const uint32_t x0 = smem_u32(X), w0 = smem_u32(Wt), idesc = instr_desc(NP);
+        for (int h = 0; h < kTcRows; h++) {  // output row y0 + h into TMEM columns 32 h ..
+            int acc = 0;
+            for (int t = 0; t < 9; t++) {
+                const int ky = t / 3, kx = t - ky * 3;
+                for (int j = 0; j < ncg; j += 2) {
+                    // A: staged row h + ky, channel groups j, j+1, pixels kx .. kx + 127
+                    const uint64_t ad =
+                        smem_desc(x0 + (uint32_t)((((h + ky) * ncg + j) * kRP + kx) * 16), kRP * 16u, 128u);
+                    // B: tap t, channel groups j, j+1, all output channels
+                    const uint64_t bd =
+                        smem_desc(w0 + (uint32_t)((t * ncg + j) * (NP >> 3) * 128), (NP >> 3) * 128u, 128u);
+                    asm volatile(
+                        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(taddr + 32u * h),
+                        "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                        : "memory");
+                    acc = 1;
+                }
+            }
         }
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                          smem_u32(&mbar))
@@ -197,18 +238,20 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         return;
     }
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (warp < 4) {
-        // accumulator row m = 32 warp + lane lives in TMEM lane m
+    if (warp < 4 * kTcRows) {
+        // warps 4h .. 4h+3: accumulator h (output row y0 + h); its row m =
+        // 32 (warp % 4) + lane (pixel x = m) lives in TMEM lane m
+        const int h = warp >> 2, y = y0 + h;
         float v[NP];
-        tmem_load_row<NP>(taddr + ((uint32_t)(warp * 32) << 16), v);
-        const long p = p0 + warp * 32 + (tid & 31);
-        if (p < hw) {
+        tmem_load_row<NP>(taddr + 32u * h + ((uint32_t)((warp & 3) * 32) << 16), v);
+        const int x = (warp & 3) * 32 + (tid & 31);
+        if (x < W && y < H) {
 #pragma unroll
             for (int co = 0; co < NP; co++) {
                 if (co < Cout) {
                     float r = v[co] + (bias ? bias[co] : 0.f);
                     if (relu) r = r > 0.f ? r : 0.f;
-                    out[(long)b * out_bs + (long)co * out_cs + p] = r;
+                    out[(long)b * out_bs + (long)co * out_cs + (long)y * W + x] = r;
                 }
             }
         }
@@ -225,26 +268,36 @@ extern "C" int fewha_conv3x3_fwd_tc(const float *in, long in_bs, long in_cs, int
                                     const float *bias, float *out, long out_bs, long out_cs, int Cout, int B, int H,
                                     int W, int relu, int *status_dev, cudaStream_t s)
 {
-    if (!in || !w || !out || Cin < 1 || Cin > 32 || Cout < 1 || Cout > 32 || B < 1 || H < 1 || W < 1)
+    if (!in || !w || !out || Cin < 1 || Cin > 32 || Cout < 1 || Cout > 32 || B < 1 || H < 1 || W < 1 || W > kTcM)
         return FEWHA_ERR_ARG;
-    const int kp = (Cin * 9 + 15) / 16 * 16;
-    const long tiles = ((long)H * W + kTcM - 1) / kTcM;
-    if (tiles * B > 0x7FFFFFFFL) return FEWHA_ERR_ARG;
-    const size_t smem = (size_t)kTcM * kp * 2 + (size_t)(Cout <= 16 ? 16 : 32) * kp * 2;
+    const long nrt = (H + kTcRows - 1) / kTcRows;  // row tiles per image
+    if ((long)B * nrt > 0x7FFFFFFFL) return FEWHA_ERR_ARG;
+    const int ncg = (Cin + 15) / 16 * 2;  // groups of 8 input channels, an even number
+    const int np = Cout <= 16 ? 16 : 32;
+    // staged rows and weights; the MMAs read only inside them (the last A
+    // view ends at pixel 2 + 127 < kRP of row 2)
+    const size_t smem = (size_t)(kTcRows + 2) * ncg * kRP * 16 + (size_t)9 * ncg * (np / 8) * 128;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return FEWHA_ERR_CUDA;
+    // the shared-memory attribute is raised once per device and variant (a
+    // host call per launch would leave the GPU idle between short launches)
+    auto launch = [&](auto kern, size_t *done) {
+        cudaError_t e = cudaSuccess;
+        if (done[dev] < smem) {
+            e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmemCap);
+            if (e == cudaSuccess) done[dev] = kTcSmemCap;
+        }
+        if (e == cudaSuccess)
+            kern<<<(unsigned)(B * nrt), kTcThreads, smem, s>>>(in, in_bs, in_cs, Cin, w, bias, out, out_bs, out_cs, Cout,
+                                                            H, W, relu, ncg, status_dev);
+        return e;
+    };
+    static size_t set16[64], set32[64];
     cudaError_t e;
-    if (Cout <= 16) {
-        e = cudaFuncSetAttribute(k_conv3x3_tc<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e == cudaSuccess)
-            k_conv3x3_tc<16><<<(unsigned)(tiles * B), kTcThreads, smem, s>>>(in, in_bs, in_cs, Cin, w, bias, out,
-                                                                            out_bs, out_cs, Cout, H, W, relu, kp,
-                                                                            status_dev);
-    } else {
-        e = cudaFuncSetAttribute(k_conv3x3_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e == cudaSuccess)
-            k_conv3x3_tc<32><<<(unsigned)(tiles * B), kTcThreads, smem, s>>>(in, in_bs, in_cs, Cin, w, bias, out,
-                                                                            out_bs, out_cs, Cout, H, W, relu, kp,
-                                                                            status_dev);
-    }
+    if (np == 16)
+        e = launch(k_conv3x3_tc<16>, set16);
+    else
+        e = launch(k_conv3x3_tc<32>, set32);
     if (e != cudaSuccess) return FEWHA_ERR_CUDA;
     return cudaGetLastError() == cudaSuccess ? FEWHA_OK : FEWHA_ERR_CUDA;
 }

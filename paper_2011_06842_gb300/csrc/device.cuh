@@ -144,6 +144,7 @@ struct __align__(16) Args {
     int kcap;
     int max_iter, augmented, recycle_all;
     int true_res_every;  // N > 0: r <- b - M c after every N-th iteration (residual replacement)
+    int rhs_in_state;    // b_prev = b and r_prev = r0 already: no right-hand-side phases
     double rtol;
     fewha_stats *stats;
     double *part;    // kSlots * kMaxCtas
@@ -292,10 +293,15 @@ __device__ void block_partials(A (&v)[NV], double *part, const int (&slot)[NV], 
         if (lane == 0) sred[i * 32 + warp] = (double)s;
     }
     __syncthreads();
-    for (int i = warp; i < NV; i += nw) {
-        double s = lane < nw ? sred[i * 32 + lane] : 0.0;
-        s = warp_sum(s);
-        if (lane == 0) part[(size_t)slot[i] * kMaxCtas + cta] = s;
+    // compile-time indices into slot[] (a runtime index would place the
+    // caller's slot array in local memory)
+#pragma unroll
+    for (int i = 0; i < NV; i++) {
+        if (i % nw == warp) {
+            double s = lane < nw ? sred[i * 32 + lane] : 0.0;
+            s = warp_sum(s);
+            if (lane == 0) part[(size_t)slot[i] * kMaxCtas + cta] = s;
+        }
     }
     __syncthreads();
 }

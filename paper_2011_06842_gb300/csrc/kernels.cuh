@@ -225,7 +225,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_rhs_wfs(const __grid_constant__
 {
     __shared__ __align__(16) Args<T, S> A;
     args_to_smem(Ap, A);
-    wfs_phase<T, S, true>(A, dyn_smem<T>());
+    if (!A.rhs_in_state) wfs_phase<T, S, true>(A, dyn_smem<T>());
     const Basis b = basis_info(A);
     if (b.kv > 0) phase_gram<T, S>(A, b, dyn_smem<T>(), (int)(A.smem_bytes / sizeof(T)));
 }
@@ -235,7 +235,7 @@ template <typename T, typename S>
 __global__ void __launch_bounds__(kThreads, 1) k_rhs_gather(const __grid_constant__ Args<T, S> Ap)
 {
     FEWHA_PHASE_GUARD
-    band_gather<T, S>(A, dyn_smem<T>());
+    if (!A.rhs_in_state) band_gather<T, S>(A, dyn_smem<T>());
     if (b.kv > 0 && A.vrank() == A.ncta - 1) phase_factor<T, S>(A, b, sc);
 }
 
@@ -245,7 +245,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_rhs_D1(const __grid_constant__ 
 {
     FEWHA_PHASE_GUARD
     (void)sc;
-    phase_D1<T, S>(A, dyn_smem<T>());
+    if (!A.rhs_in_state) phase_D1<T, S>(A, dyn_smem<T>());
 }
 
 template <typename T, typename S>
@@ -431,14 +431,15 @@ __device__ void solve_body(const Args<T, S> &A, Scal &sc, double *sred)
     const Args<T, T> *V = nullptr;  // residual replacement's view of the arguments
     if constexpr (TR) V = TrView<T, S>::get(A);
     trace_begin(A.trace != nullptr);
+    const bool rhs = !A.rhs_in_state;  // form the right-hand side (else it is in the state)
     do {
-        wfs_phase<T, S, true>(A, sm);
+        if (rhs) wfs_phase<T, S, true>(A, sm);
         if (b.kv > 0) phase_gram<T, S>(A, b, sm, (int)(A.smem_bytes / sizeof(T)));
-        if (!sync(1)) break;
-        band_gather<T, S>(A, sm);
+        if ((rhs || b.kv > 0) && !sync(1)) break;
+        if (rhs) band_gather<T, S>(A, sm);
         if (b.kv > 0 && rank == A.ncta - 1) phase_factor<T, S>(A, b, sc);
-        if (!sync(2)) break;
-        if (split) {
+        if ((rhs || b.kv > 0) && !sync(2)) break;
+        if (split && rhs) {
             phase_D1<T, S>(A, sm);  // the finest analysis level of u
             if (!sync(6)) break;
         }
@@ -1420,6 +1421,7 @@ struct Impl : ImplBase {
         A.augmented = o->augmented ? 1 : 0;
         A.recycle_all = o->recycle_mode == FEWHA_RECYCLE_ALL ? 1 : 0;
         A.true_res_every = o->true_res_every;
+        A.rhs_in_state = o->rhs_in_state ? 1 : 0;
         A.stats = stats;
         return A;
     }

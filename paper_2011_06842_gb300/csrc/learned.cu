@@ -342,7 +342,15 @@ __global__ void k_deflate_update(const double *__restrict__ info, const float *_
                                  const float *__restrict__ b, const float *__restrict__ r0, float *__restrict__ c,
                                  float *__restrict__ b_prev, float *__restrict__ r_prev, long n)
 {
-    if (info[0] == 0.0) return;
+    // not taken: the plain warm restart r0 is folded into the state
+    const bool taken = info[0] != 0.0;
+    if (!taken) {
+        for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+            r_prev[i] = r0[i];
+            b_prev[i] = b[i];
+        }
+        return;
+    }
     float w[kMaxDir];
 #pragma unroll
     for (int j = 0; j < kMaxDir; j++) w[j] = j < nd ? wf[j] : 0.f;

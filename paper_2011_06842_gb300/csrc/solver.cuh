@@ -1001,7 +1001,19 @@ __device__ __forceinline__ void phase_rhs_update(const Args<T, S> &A, const Basi
     constexpr int W = VW<T>::W;
     const int kv = b.kv;
     Acc acc[2] = {0, 0};
-    analysis_update(A, buf, [&](long e, const T (&bv)[W]) {
+    if (A.rhs_in_state) {
+        // the state already holds b (in b_prev) and r0: partial sums only
+        for_updated_vectors(A, [&](long e) {
+            T bv[W], r0[W];
+            vld_cg(A.b_prev + e, bv);
+            vld_cg(A.r + e, r0);
+#pragma unroll
+            for (int i = 0; i < W; i++) {
+                acc[0] += (Acc)bv[i] * (Acc)bv[i];
+                acc[1] += (Acc)r0[i] * (Acc)r0[i];
+            }
+        });
+    } else analysis_update(A, buf, [&](long e, const T (&bv)[W]) {
         T bp[W], rp[W], r0[W];
         vld(A.b_prev + e, bp);
         vld_cg(A.r + e, rp);

@@ -55,7 +55,8 @@ class STATE(C.Structure):
 
 class OPTS(C.Structure):
     _fields_ = [("max_iter", C.c_int), ("rtol", C.c_double), ("augmented", C.c_int),
-                ("recycle_mode", C.c_int), ("launch_mode", C.c_int), ("true_res_every", C.c_int)]
+                ("recycle_mode", C.c_int), ("launch_mode", C.c_int), ("true_res_every", C.c_int),
+                ("rhs_in_state", C.c_int), ("pad", C.c_int)]
 
 
 class LAUNCH_INFO(C.Structure):
@@ -402,15 +403,18 @@ class Fewha:
         return self._torch.zeros(STATS_BYTES, dtype=self._torch.uint8, device=self.device)
 
     def solve(self, s, c, state, max_iter, rtol=0.0, augmented=True, recycle_all=False,
-              persistent=True, stats=None, true_res_every=0):
+              persistent=True, stats=None, true_res_every=0, rhs_in_state=False):
         """One time step; c is updated in place.  Returns the device stats buffer.
         true_res_every = N > 0 replaces the residual by b - M c after every N-th
-        iteration."""
+        iteration; rhs_in_state: the state already holds this step's
+        right-hand side (after fewha_deflate_warm_start), s is not read."""
         o = OPTS(int(max_iter), float(rtol), 1 if augmented else 0,
                  RECYCLE_ALL if recycle_all else RECYCLE_LAST,
-                 LAUNCH_PERSISTENT if persistent else LAUNCH_PHASES, int(true_res_every))
+                 LAUNCH_PERSISTENT if persistent else LAUNCH_PHASES, int(true_res_every),
+                 1 if rhs_in_state else 0)
         stats = stats if stats is not None else self.new_stats()
-        self._check(self.lib.fewha_solve(self._h, self._vec(s, self.n_slopes, self.slope_dtype, "s"),
+        sp = None if (rhs_in_state and s is None) else self._vec(s, self.n_slopes, self.slope_dtype, "s")
+        self._check(self.lib.fewha_solve(self._h, sp,
                                          self._vec(c, self.n, self.dtype, "c"), C.byref(state.c_struct),
                                          C.byref(o), C.c_void_p(stats.data_ptr()),
                                          _stream_ptr(self._torch)), "fewha_solve")

@@ -111,22 +111,32 @@ class ConvNet:
         if st != 0:
             raise FewhaError(st, what)
 
-    def forward(self, x_ptr, x_cs, y):
-        """y (5, n) = network(x), x channel k at address x_ptr + 4 * k * x_cs."""
+    def forward(self, x_ptr, x_cs, y, tensor_cores=False):
+        """y (5, n) = network(x), x channel k at address x_ptr + 4 * k * x_cs.
+        tensor_cores: the convolutions run on the tcgen05 kernel (bfloat16
+        operands, FP32 accumulation; inference), else on the FP32 kernel
+        (training: its activations feed the backward pass)."""
         lib, s = self.lib, _stream_ptr(self.torch)
         c0, c1, c2, c3 = CHANNELS
+        if tensor_cores:
+            if not hasattr(self, "tc_status"):
+                self.tc_status = self.torch.zeros(1, dtype=self.torch.int32, device=self.param.device)
+            st = C.c_void_p(self.tc_status.data_ptr())
+            conv = lambda *a: lib.fewha_conv3x3_fwd_tc(*a[:-1], st, a[-1])  # noqa: E731
+        else:
+            conv = lib.fewha_conv3x3_fwd
         for gi, (off, cnt, nl) in enumerate(self.groups):
             hw = nl * nl
             h1, h2 = self.h1[gi], self.h2[gi]
-            self._ck(lib.fewha_conv3x3_fwd(C.c_void_p(x_ptr + 4 * off), hw, x_cs, c0, self._p(self.param, "w1"),
-                                           self._p(self.param, "b1"), C.c_void_p(h1.data_ptr()), 32 * hw, hw, c1,
-                                           cnt, nl, nl, 1, s), "conv1")
-            self._ck(lib.fewha_conv3x3_fwd(C.c_void_p(h1.data_ptr()), 32 * hw, hw, c1, self._p(self.param, "w2"),
-                                           self._p(self.param, "b2"), C.c_void_p(h2.data_ptr()), 32 * hw, hw, c2,
-                                           cnt, nl, nl, 1, s), "conv2")
-            self._ck(lib.fewha_conv3x3_fwd(C.c_void_p(h2.data_ptr()), 32 * hw, hw, c2, self._p(self.param, "w3"),
-                                           self._p(self.param, "b3"), C.c_void_p(y.data_ptr() + 4 * off), hw,
-                                           y.stride(0), c3, cnt, nl, nl, 0, s), "conv3")
+            self._ck(conv(C.c_void_p(x_ptr + 4 * off), hw, x_cs, c0, self._p(self.param, "w1"),
+                          self._p(self.param, "b1"), C.c_void_p(h1.data_ptr()), 32 * hw, hw, c1, cnt, nl, nl, 1, s),
+                     "conv1")
+            self._ck(conv(C.c_void_p(h1.data_ptr()), 32 * hw, hw, c1, self._p(self.param, "w2"),
+                          self._p(self.param, "b2"), C.c_void_p(h2.data_ptr()), 32 * hw, hw, c2, cnt, nl, nl, 1, s),
+                     "conv2")
+            self._ck(conv(C.c_void_p(h2.data_ptr()), 32 * hw, hw, c2, self._p(self.param, "w3"),
+                          self._p(self.param, "b3"), C.c_void_p(y.data_ptr() + 4 * off), hw, y.stride(0), c3, cnt,
+                          nl, nl, 0, s), "conv3")
         return y
 
     def backward(self, x_ptr, x_cs, gy):
@@ -196,11 +206,12 @@ def _scale(lib, torch, x, s, y, mode):
 class LearnedWarmStart:
     """Training and online use of the network for one FP32 Fewha instance."""
 
-    def __init__(self, fewha, geom, seed=0):
+    def __init__(self, fewha, geom, seed=0, tensor_cores=True):
         import torch
         if fewha.precision != "f32":
             raise ValueError("the learned warm start runs with an FP32 Fewha instance")
         self.torch, self.f, self.lib = torch, fewha, load_library()
+        self.tensor_cores = tensor_cores  # online prediction on the tcgen05 convolution
         self.net = ConvNet(geom, seed=seed)
         n = self.n = fewha.n
         dev = fewha.device
@@ -321,7 +332,7 @@ class LearnedWarmStart:
         torch, lib, n = self.torch, self.lib, self.n
         self.f.rhs(s, out=self.b)
         j = (self.count - 1) % 4
-        self.net.forward(self.ring[j + 4].data_ptr(), -n, self.y)
+        self.net.forward(self.ring[j + 4].data_ptr(), -n, self.y, tensor_cores=self.tensor_cores)
         for k in range(N_DIR):
             _scale(lib, torch, self.y[k], self.out_scale, self.D[k], 1)
         self.f.apply_op_multi(self.D, out=self.Q)
@@ -363,7 +374,8 @@ def solve_sequence(f, slopes, rtol, max_iter, kcap=8, augmented=True, learned=No
             flush.zero_()
         ev[t][0].record()
         used = learned.prepare(slopes[t], c, st) if learned is not None else False
-        f.solve(slopes[t], c, st, max_iter, rtol=rtol, augmented=augmented, stats=stats[t])
+        # after prepare() the state holds this step's right-hand side
+        f.solve(slopes[t], c, st, max_iter, rtol=rtol, augmented=augmented, stats=stats[t], rhs_in_state=used)
         ev[t][1].record()
         if learned is not None:
             learned.push(c)

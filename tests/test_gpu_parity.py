@@ -206,3 +206,26 @@ def test_invalid_arguments(lib):
         f.solve(dev(s[0], torch.float64), c, st, 0)
     with pytest.raises(lib.FewhaError):
         f.solve(dev(s[0], torch.float64), c, st, 10000)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_solve_with_rhs_in_state(lib, prec):
+    """rhs_in_state: the caller has folded the step's right-hand side into the
+    state (b_prev <- b, r_prev <- (b - b_prev) + r_prev, as the deflated warm
+    start leaves it); the solve then skips its own right-hand side and gives
+    the oracle's time step (Algorithm 3 then Algorithm 2), s not read."""
+    geom, s, w, o = setup("tiny")
+    f = lib.Fewha(geom, w, prec)
+    dt = torch.float64 if prec == "f64" else torch.float32
+    st_o, st_g = o.new_state(4), f.new_state(4)
+    c = torch.zeros(o.n, dtype=dt, device="cuda")
+    for t in range(4):
+        o.solve(s[t], st_o, max_iter=5, augmented=True)
+        b = f.rhs(dev(s[t], dt))
+        st_g.r_prev.copy_((b - st_g.b_prev) + st_g.r_prev)
+        st_g.b_prev.copy_(b)
+        rg = f.read_stats(f.solve(None, c, st_g, 5, rhs_in_state=True))
+        assert rg["status"] == 0 and rg["iterations"] == 5
+        assert rel(c.cpu().numpy(), st_o["c"]) < TOL[prec], t
+        assert rel(st_g.r_prev.cpu().numpy(), st_o["r_prev"]) < 10 * TOL[prec], t
+    f.close()

@@ -161,3 +161,12 @@ def test_deflation_gate_keeps_the_plain_warm_start():
     taken, c1, bp1, rp1, w, n1, n0 = L.deflate_warm_start(b, D, D @ M, c, b, np.zeros(n))
     assert not taken and n0 == 0.0
     assert np.array_equal(c1, c) and np.array_equal(rp1, np.zeros(n))
+    # not taken: with d = e_0 and q = e_0 + 10 e_1, r0 = e_0 gives w = 1 and
+    # ||r0 - q w|| = 10 > ||r0||, so the plain warm restart r0 = (b - b_prev)
+    # + r_prev is folded into the state unchanged
+    e0, e1 = np.eye(n)[0], np.eye(n)[1]
+    b2 = b + e0
+    taken, c1, bp1, rp1, w, n1, n0 = L.deflate_warm_start(b2, e0[None, :], (e0 + 10 * e1)[None, :], c, b,
+                                                          np.zeros(n))
+    assert not taken and abs(w[0] - 1.0) < 1e-15 and abs(n1 - 10.0) < 1e-12
+    assert np.array_equal(c1, c) and np.array_equal(bp1, b2) and np.array_equal(rp1, (b2 - b) + np.zeros(n))
