@@ -293,11 +293,19 @@ __device__ void block_partials(A (&v)[NV], double *part, const int (&slot)[NV], 
         if (lane == 0) sred[i * 32 + warp] = (double)s;
     }
     __syncthreads();
-    // compile-time indices into slot[] (a runtime index would place the
-    // caller's slot array in local memory)
+    if constexpr (NV <= kThreads / 32) {
+        // one slot per warp at most: compile-time indices into slot[] (a
+        // runtime index would place the caller's slot array in local memory)
 #pragma unroll
-    for (int i = 0; i < NV; i++) {
-        if (i % nw == warp) {
+        for (int i = 0; i < NV; i++) {
+            if (i == warp) {
+                double s = lane < nw ? sred[i * 32 + lane] : 0.0;
+                s = warp_sum(s);
+                if (lane == 0) part[(size_t)slot[i] * kMaxCtas + cta] = s;
+            }
+        }
+    } else {
+        for (int i = warp; i < NV; i += nw) {
             double s = lane < nw ? sred[i * 32 + lane] : 0.0;
             s = warp_sum(s);
             if (lane == 0) part[(size_t)slot[i] * kMaxCtas + cta] = s;

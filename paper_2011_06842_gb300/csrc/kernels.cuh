@@ -253,7 +253,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_rhs_update(const __grid_constan
 {
     FEWHA_PHASE_GUARD
     (void)sc;
-    phase_rhs_update<T, S>(A, b, dyn_smem<T>(), sred);
+    if (A.rhs_in_state)
+        phase_rhs_update<T, S, true>(A, b, dyn_smem<T>(), sred);
+    else
+        phase_rhs_update<T, S, false>(A, b, dyn_smem<T>(), sred);
 }
 
 template <typename T, typename S>
@@ -408,9 +411,10 @@ __device__ __forceinline__ bool true_residual_phases(const Args<T, T> &V, const 
 
 // --- the whole time step of one instance, run by its group of CTAs ----------
 // TR: the kernel variant with the residual replacement (fewha_solve_opts.
-// true_res_every > 0); the variant without it carries none of its code, so
-// the iteration's register allocation is the same as without the option.
-template <typename T, typename S, bool TR>
+// true_res_every > 0); RIS: the variant for a right-hand side already in the
+// state (fewha_solve_opts.rhs_in_state).  The default variant carries the
+// code of neither, so its register allocation does not depend on them.
+template <typename T, typename S, bool TR, bool RIS = false>
 __device__ void solve_body(const Args<T, S> &A, Scal &sc, double *sred)
 {
     T *sm = dyn_smem<T>();
@@ -431,7 +435,7 @@ __device__ void solve_body(const Args<T, S> &A, Scal &sc, double *sred)
     const Args<T, T> *V = nullptr;  // residual replacement's view of the arguments
     if constexpr (TR) V = TrView<T, S>::get(A);
     trace_begin(A.trace != nullptr);
-    const bool rhs = !A.rhs_in_state;  // form the right-hand side (else it is in the state)
+    constexpr bool rhs = !RIS;  // form the right-hand side (else it is in the state)
     do {
         if (rhs) wfs_phase<T, S, true>(A, sm);
         if (b.kv > 0) phase_gram<T, S>(A, b, sm, (int)(A.smem_bytes / sizeof(T)));
@@ -443,7 +447,7 @@ __device__ void solve_body(const Args<T, S> &A, Scal &sc, double *sred)
             phase_D1<T, S>(A, sm);  // the finest analysis level of u
             if (!sync(6)) break;
         }
-        phase_rhs_update<T, S>(A, b, sm, sred);  // b, r0 and P^T r0
+        phase_rhs_update<T, S, RIS>(A, b, sm, sred);  // b, r0 and P^T r0
         if (!sync(3)) break;
         if (b.kv > 0) {
             phase_init<T, S>(A, b, sc, sred);
@@ -491,14 +495,14 @@ __device__ void solve_body(const Args<T, S> &A, Scal &sc, double *sred)
 }
 
 // One instance on the whole grid (cooperative launch).
-template <typename T, typename S, bool TR>
+template <typename T, typename S, bool TR, bool RIS = false>
 __global__ void __launch_bounds__(kThreads, 1) k_solve_persistent(const __grid_constant__ Args<T, S> Ap)
 {
     __shared__ Scal sc;
     __shared__ double sred[kSred];
     __shared__ __align__(16) Args<T, S> A;
     args_to_smem(Ap, A);
-    solve_body<T, S, TR>(A, sc, sred);
+    solve_body<T, S, TR, RIS>(A, sc, sred);
 }
 
 // Many instances in one cooperative launch: CTA c runs instance cta_inst[c]
@@ -1004,6 +1008,8 @@ struct Impl : ImplBase {
         CK(setattr((const void *)k_TE<T, S>));
         CK(setattr((const void *)k_solve_persistent<T, S, false>));
         CK(setattr((const void *)k_solve_persistent<T, S, true>));
+        CK(setattr((const void *)k_solve_persistent<T, S, false, true>));
+        CK(setattr((const void *)k_solve_persistent<T, S, true, true>));
         CK(cudaFuncSetAttribute((const void *)k_solve_batched<T, S, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 200 * 1024));
         CK(cudaFuncSetAttribute((const void *)k_solve_batched<T, S, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1494,8 +1500,13 @@ struct Impl : ImplBase {
             attr[0].val.cooperative = 1;
             cfg.attrs = attr;
             cfg.numAttrs = 1;
-            if (A.true_res_every > 0)
+            const bool tr = A.true_res_every > 0, ris = A.rhs_in_state != 0;
+            if (tr && ris)
+                CK(cudaLaunchKernelEx(&cfg, k_solve_persistent<T, S, true, true>, A));
+            else if (tr)
                 CK(cudaLaunchKernelEx(&cfg, k_solve_persistent<T, S, true>, A));
+            else if (ris)
+                CK(cudaLaunchKernelEx(&cfg, k_solve_persistent<T, S, false, true>, A));
             else
                 CK(cudaLaunchKernelEx(&cfg, k_solve_persistent<T, S, false>, A));
             return launch_check();

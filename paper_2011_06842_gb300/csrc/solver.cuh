@@ -994,14 +994,14 @@ __device__ __noinline__ void rhs_ptr_pass(const Args<T, S> &A, const Basis &b,
     block_partials<2 + KV>(pr, A.part, slots, sred, A.vrank());
 }
 
-template <typename T, typename S>
+template <typename T, typename S, bool RIS>
 __device__ __forceinline__ void phase_rhs_update(const Args<T, S> &A, const Basis &b, T *buf, double *sred)
 {
     typedef typename AccT<T>::type Acc;
     constexpr int W = VW<T>::W;
     const int kv = b.kv;
     Acc acc[2] = {0, 0};
-    if (A.rhs_in_state) {
+    if constexpr (RIS) {
         // the state already holds b (in b_prev) and r0: partial sums only
         for_updated_vectors(A, [&](long e) {
             T bv[W], r0[W];
