@@ -54,6 +54,8 @@ def parse():
     p.add_argument("--batched-steps", type=int, default=20)
     p.add_argument("--learned", action="store_true",
                    help="learned warm start study instead of the time-step benchmark")
+    p.add_argument("--conv-layers", action="store_true",
+                   help="time each 3x3 convolution of the learned predictor (tensor cores and FP32)")
     p.add_argument("--learned-train", type=int, default=20000, help="training frames")
     p.add_argument("--learned-eval", type=int, default=500, help="held-out frames")
     p.add_argument("--epochs", type=int, default=2)
@@ -705,6 +707,42 @@ def run_reference(args):
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def run_conv_layers(args):
+    """Device time of every convolution launch of the learned predictor's
+    forward pass on the configuration's layer groups (random activations and
+    weights): the tcgen05 kernel against the FP32 kernel, 3 warm-up and
+    args.steps (at most 50) timed launches each, in forward order."""
+    import torch
+    from paper_2011_06842_gb300 import build, learned
+    from synth import configs
+    build.build()
+    geom = configs.get(args.config)
+    net = learned.ConvNet(geom, seed=7)
+    x = torch.randn(learned.CHANNELS[0], net.n, device="cuda")
+    y = torch.empty(learned.N_DIR, net.n, device="cuda")
+    reps = max(1, min(args.steps, 50))
+    out = {"metric": "3x3 convolution launches of the learned predictor", "unit": "us", "config": {
+        "workload": "%s layer groups %s, channels %s" % (geom.name, [(c, n) for _, c, n in net.groups],
+                                                         list(learned.CHANNELS))}, "layers": []}
+    for tc in (True, False):
+        for name, flops, launch in net.convolutions(x.data_ptr(), net.n, y, tensor_cores=tc):
+            for _ in range(3):
+                assert launch() == 0, name
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a.record()
+            for _ in range(reps):
+                launch()
+            b.record()
+            torch.cuda.synchronize()
+            us = a.elapsed_time(b) * 1e3 / reps
+            out["layers"].append({"conv": name, "kernel": "tcgen05" if tc else "fp32", "us": us,
+                                  "tflops": flops / us * 1e-6})
+        if tc:
+            out["tc_status"] = int(net.tc_status.item())
+    return out
+
+
 def run_learned(args):
     """Learned warm start vs the plain warm start of Algorithm 3 (both with
     augmented PCG, FP32): train on frames the plain method solves, then run
@@ -795,6 +833,9 @@ def main():
     args = parse()
     if args.diagnostics:
         print(json.dumps(run_diagnostics(args)))
+        return
+    if args.conv_layers:
+        print(json.dumps(run_conv_layers(args)))
         return
     if args.learned:
         print(json.dumps(run_learned(args)))

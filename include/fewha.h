@@ -128,8 +128,8 @@ typedef struct {
     int augmented;        /* 0: PCG (Algorithm 1); 1: augmented PCG (Algorithm 2) */
     int recycle_mode;     /* FEWHA_RECYCLE_LAST (paper) or FEWHA_RECYCLE_ALL */
     int launch_mode;      /* FEWHA_LAUNCH_PERSISTENT (one kernel) or FEWHA_LAUNCH_PHASES */
-    /* N > 0: residual replacement.  After every N-th iteration (the last one
-     * included) the recurrence residual r is replaced by the true residual
+    /* N > 0: residual replacement.  After iterations N, 2N, 3N, ... (counting
+     * from 1) the recurrence residual r is replaced by the true residual
      * b - M c, computed with one more operator application whose
      * intermediates are stored in the working precision (FP32 also for
      * FEWHA_BF16S); z = J^{-1} r, the projection, (r, z) and beta of the next

@@ -470,9 +470,15 @@ __device__ inline bool chol_solve(int k, const double *Graw, const double *rhs, 
     return true;
 }
 
+// Error bit of the barrier counter: set together with the status, so that a
+// CTA waiting at (or arriving at) a grid barrier sees the error in the word it
+// polls anyway, without a second load.
+constexpr unsigned int kBarErr = 0x80000000u;
+
 __device__ __forceinline__ void set_status(Record *rec, int st)
 {
     atomicCAS(&rec->status, 0, st);
+    atomicOr(&rec->bar.count, kBarErr);
 }
 
 // Grid barrier with a time limit.  Returns false (and the CTA must return)
@@ -494,8 +500,9 @@ __device__ __forceinline__ unsigned int ld_acquire_gpu(const unsigned int *p)
 // Barrier over the nctas CTAs of a group, with a time limit.  Thread 0 arrives
 // with an acquire-release add on a counter that only grows during a solve
 // (after the block barrier, publishing the CTA's writes) and waits with
-// acquire loads until the counter reaches the next multiple of nctas.  Returns false (and the CTA must
-// return) when any CTA has recorded an error or the wait ran past timeout_ns.
+// acquire loads until the counter reaches the next multiple of nctas.  Returns
+// false (and the CTA must return) when the counter's error bit is set (any CTA
+// recorded an error) or the wait ran past timeout_ns.
 // When this CTA passed its previous barrier (phase trace); trace_begin()
 // stamps the start of the solve.
 static __shared__ unsigned long long t_pass;
@@ -517,22 +524,25 @@ __device__ inline bool grid_sync(Record *rec, unsigned long long timeout_ns, int
             atomicMax(trace_slot + 1, now);
             if (t_pass) atomicMax(trace_slot, now - t_pass);
         }
-        volatile int *vst = &rec->status;
         // the counter only grows within a solve (reset before every launch):
         // the barrier of this arrival completes when it reaches the next
-        // multiple of nctas
+        // multiple of nctas; an error anywhere sets its top bit
         const unsigned int prev = atom_add_acq_rel_gpu(&rec->bar.count, 1u);
-        const unsigned int target = (prev / (unsigned int)nctas + 1u) * (unsigned int)nctas;
-        if (prev + 1u != target) {
-            const unsigned long long t0 = gtimer();
-            unsigned int polls = 0;
-            while (ld_acquire_gpu(&rec->bar.count) < target) {
-                if ((++polls & 7u) == 1u) {  // polls 1, 9, 17, ...: status and time limit
-                    if (*vst != 0) {
+        if (prev & kBarErr) {
+            ok = 0;
+        } else {
+            const unsigned int target = (prev / (unsigned int)nctas + 1u) * (unsigned int)nctas;
+            if (prev + 1u != target) {
+                const unsigned long long t0 = gtimer();
+                unsigned int polls = 0;
+                for (;;) {
+                    const unsigned int c = ld_acquire_gpu(&rec->bar.count);
+                    if (c & kBarErr) {
                         ok = 0;
                         break;
                     }
-                    if (gtimer() - t0 > timeout_ns) {
+                    if (c >= target) break;
+                    if ((++polls & 7u) == 0u && gtimer() - t0 > timeout_ns) {  // time limit
                         set_status(rec, FEWHA_ERR_TIMEOUT);
                         ok = 0;
                         break;
@@ -540,7 +550,6 @@ __device__ inline bool grid_sync(Record *rec, unsigned long long timeout_ns, int
                 }
             }
         }
-        if (*vst != 0) ok = 0;
         if (trace_slot && rank == 0) trace_slot[2] = gtimer();
         t_pass = trace_slot ? gtimer() : 0ull;
     }
@@ -1000,8 +1009,10 @@ __device__ __forceinline__ void band_gather(const Args<T, S> &A, T *sm, const Ba
             {
                 const int total = s_base[ng];  // staged rows
                 int q = 0;                     // guide star of the staged row (rows only grow)
-                if (tab && (int)blockDim.x % n == 0) {
-                    // each thread keeps one column b and the rows r0 + k rstep;
+                if (tab && (int)blockDim.x % n == 0 && (blockDim.x & (blockDim.x - 1)) == 0) {
+                    // each thread keeps one column b and the rows r0 + k rstep
+                    // (rstep = blockDim.x / n, a power of two: rows congruent to
+                    // r0 modulo rstep, found with a mask);
                     // guide star after guide star, its weights in registers and
                     // the taps unrolled up to the warp's largest count
                     const int bcol = threadIdx.x & (n - 1), r0 = threadIdx.x >> lgn, rstep = blockDim.x >> lgn;
@@ -1013,7 +1024,7 @@ __device__ __forceinline__ void band_gather(const Args<T, S> &A, T *sm, const Ba
 #pragma unroll
                         for (int c = 0; c < kAdjW; c++) wr[c] = c < cnt ? xw[(size_t)c * nxt + ti] : T(0);
                         const int rb = s_base[q], re = s_base[q + 1], mq = G.gs_m[g0 + q];
-                        for (int row = rb + ((r0 - rb) % rstep + rstep) % rstep; row < re; row += rstep) {
+                        for (int row = rb + ((r0 - rb) & (rstep - 1)); row < re; row += rstep) {
                             const T *rowp = ps + s_cum[q] + (row - rb) * mq + jlo;
                             T v = 0;
 #pragma unroll

@@ -116,6 +116,14 @@ class ConvNet:
         tensor_cores: the convolutions run on the tcgen05 kernel (bfloat16
         operands, FP32 accumulation; inference), else on the FP32 kernel
         (training: its activations feed the backward pass)."""
+        for name, _, launch in self.convolutions(x_ptr, x_cs, y, tensor_cores):
+            self._ck(launch(), name)
+        return y
+
+    def convolutions(self, x_ptr, x_cs, y, tensor_cores=False):
+        """The launches of forward(), in order: (name, FLOPs, launch) per 3x3
+        convolution of each group of equal-size layers; launch() returns the
+        C-ABI status."""
         lib, s = self.lib, _stream_ptr(self.torch)
         c0, c1, c2, c3 = CHANNELS
         if tensor_cores:
@@ -125,19 +133,22 @@ class ConvNet:
             conv = lambda *a: lib.fewha_conv3x3_fwd_tc(*a[:-1], st, a[-1])  # noqa: E731
         else:
             conv = lib.fewha_conv3x3_fwd
+        out = []
         for gi, (off, cnt, nl) in enumerate(self.groups):
             hw = nl * nl
             h1, h2 = self.h1[gi], self.h2[gi]
-            self._ck(conv(C.c_void_p(x_ptr + 4 * off), hw, x_cs, c0, self._p(self.param, "w1"),
-                          self._p(self.param, "b1"), C.c_void_p(h1.data_ptr()), 32 * hw, hw, c1, cnt, nl, nl, 1, s),
-                     "conv1")
-            self._ck(conv(C.c_void_p(h1.data_ptr()), 32 * hw, hw, c1, self._p(self.param, "w2"),
-                          self._p(self.param, "b2"), C.c_void_p(h2.data_ptr()), 32 * hw, hw, c2, cnt, nl, nl, 1, s),
-                     "conv2")
-            self._ck(conv(C.c_void_p(h2.data_ptr()), 32 * hw, hw, c2, self._p(self.param, "w3"),
-                          self._p(self.param, "b3"), C.c_void_p(y.data_ptr() + 4 * off), hw, y.stride(0), c3, cnt,
-                          nl, nl, 0, s), "conv3")
-        return y
+            stages = ((C.c_void_p(x_ptr + 4 * off), hw, x_cs, c0, "w1", "b1", C.c_void_p(h1.data_ptr()), 32 * hw,
+                       hw, c1, 1),
+                      (C.c_void_p(h1.data_ptr()), 32 * hw, hw, c1, "w2", "b2", C.c_void_p(h2.data_ptr()), 32 * hw,
+                       hw, c2, 1),
+                      (C.c_void_p(h2.data_ptr()), 32 * hw, hw, c2, "w3", "b3", C.c_void_p(y.data_ptr() + 4 * off),
+                       hw, y.stride(0), c3, 0))
+            for i, (xp, xbs, xcs, ci, wn, bn, yp, ybs, ycs, co, relu) in enumerate(stages):
+                args = (xp, xbs, xcs, ci, self._p(self.param, wn), self._p(self.param, bn), yp, ybs, ycs, co, cnt,
+                        nl, nl, relu, s)
+                out.append(("conv%d %dx%dx%d %d->%d" % (i + 1, cnt, nl, nl, ci, co), 18.0 * cnt * hw * ci * co,
+                            (lambda a=args: conv(*a))))
+        return out
 
     def backward(self, x_ptr, x_cs, gy):
         """Parameter gradients (self.grad) of sum(gy * y) after forward() on the same x."""
