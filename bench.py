@@ -54,6 +54,8 @@ def parse():
     p.add_argument("--batched-steps", type=int, default=20)
     p.add_argument("--learned", action="store_true",
                    help="learned warm start study instead of the time-step benchmark")
+    p.add_argument("--trace", action="store_true",
+                   help="per-phase trace of the time step (plain and augmented PCG)")
     p.add_argument("--conv-layers", action="store_true",
                    help="time each 3x3 convolution of the learned predictor (tensor cores and FP32)")
     p.add_argument("--learned-train", type=int, default=20000, help="training frames")
@@ -65,11 +67,28 @@ def parse():
     return p.parse_args()
 
 
+def sensors_name(geom):
+    """The asterism as text: '6 GS (LGS H=90 km), 84x84 SH' when every guide
+    star has the same kind and sensor, else its groups in order."""
+    def kind(g):
+        return "LGS H=%.0f km" % (g.H / 1e3) if g.H > 0 else "NGS"
+    groups = []
+    for i, g in enumerate(geom.gs):
+        key = (kind(g), geom.sensor_ns(i))
+        if groups and groups[-1][0] == key:
+            groups[-1][1] += 1
+        else:
+            groups.append([key, 1])
+    if len(groups) == 1:
+        (k, ns), cnt = groups[0]
+        return "%d GS (%s), %dx%d SH" % (cnt, k, ns, ns)
+    return "%d GS (%s) SH" % (len(geom.gs), ", ".join("%d %s %dx%d" % (cnt, k, ns, ns) for (k, ns), cnt in groups))
+
+
 def workload_name(geom, args):
-    return ("%s: D=%.0f m, %d GS (%s), %dx%d SH, %d layers (%s), n=%d, Daubechies-%d, k=%d, "
+    return ("%s: D=%.0f m, %s, %d layers (%s), n=%d, Daubechies-%d, k=%d, "
             "%s PCG to rel. residual %g, SNR %g"
-            % (geom.name, geom.D, len(geom.gs), "LGS H=90 km" if geom.gs[0].H > 0 else "NGS",
-               geom.n_sub, geom.n_sub, len(geom.layers),
+            % (geom.name, geom.D, sensors_name(geom), len(geom.layers),
                "+".join("%d^2" % l.n for l in geom.layers), geom.n_unknowns, geom.wavelet_N,
                args.k, "plain" if args.plain else "augmented", args.rtol, geom.snr))
 
@@ -101,10 +120,16 @@ def cpu_model():
     return "unknown"
 
 
+# the sources of k_solve_persistent's translation unit and of its launch and
+# tables (the ncu traffic in profiles/traffic.json is valid while they are unchanged)
+KERNEL_SOURCES = ("api.cu", "device.cuh", "inst_f32.cu", "kernels.cuh", "mcao.cuh", "plan.cpp", "plan.h",
+                  "solver.cuh")
+
+
 def source_hash():
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2011_06842_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
+    for f in KERNEL_SOURCES:
         h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -321,7 +346,11 @@ def run_ours(args):
 
     if rank == 0:
         out["e2e"] = run_e2e(f, geom, frames, sdt, args, aug, flush)
-        out["algorithm3"] = run_algorithm3(f, frames, sdt, args, aug, flush)
+        if len({geom.sensor_ns(g) for g in range(len(geom.gs))}) == 1:
+            out["algorithm3"] = run_algorithm3(f, frames, sdt, args, aug, flush)
+        else:
+            out["algorithm3"] = {"skipped": "pseudo-open-loop slopes need every sensor on the ground mirror's "
+                                            "node grid; this asterism has sensors of different sizes"}
         out["mcao_fit"] = run_mcao(f, geom, frames, sdt, args, aug, flush)
         if not args.no_compare:
             out["compare"] = run_compare(geom, w, frames, args, stats_buf, flush,
@@ -707,6 +736,63 @@ def run_reference(args):
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def run_trace(args):
+    """Per-phase trace of the persistent time step (fewha_set_trace) on the
+    configuration, plain and augmented PCG: 20 warm-up frames, 10 untimed-trace
+    frames timed with CUDA events (L2 flushed before each), then 5 traced frames;
+    per phase tag the mean span (last CTA done minus CTA 0 leaving the previous
+    barrier), barrier wait and longest single-CTA phase, in microseconds."""
+    import collections
+    import numpy as np
+    import torch
+    from paper_2011_06842_gb300 import Fewha, build
+    from synth import configs
+    build.build()
+    torch.cuda.set_device(0)
+    geom = configs.get(args.config)
+    if args.snr:
+        geom.snr = args.snr
+    geom.k_recycle = args.k
+    frames, w = make_frames(geom, 35, seed=101, device="cuda")
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    out = {"metric": "per-phase trace of one time step", "unit": "us",
+           "config": bench_config(geom, args, True), "forms": {}}
+    for aug in (False, True):
+        f = Fewha(geom, w, args.precision)
+        sdt = torch.bfloat16 if args.precision == "bf16s" else f.dtype
+        sl = frames.to(sdt)
+        st, c = f.new_state(args.k), torch.zeros(f.n, dtype=f.dtype, device="cuda")
+        for t in range(20):
+            f.solve(sl[t], c, st, args.max_iter, rtol=args.rtol, augmented=aug)
+        torch.cuda.synchronize()
+        us, its = [], []
+        for t in range(20, 30):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            stt = f.solve(sl[t], c, st, args.max_iter, rtol=args.rtol, augmented=aug)
+            b.record()
+            torch.cuda.synchronize()
+            us.append(a.elapsed_time(b) * 1e3)
+            its.append(f.read_stats(stt)["iterations"])
+        buf = torch.zeros((512, 4), dtype=torch.int64, device="cuda")
+        f.set_trace(buf)
+        agg = collections.defaultdict(list)
+        for t in range(30, 35):
+            flush.zero_()
+            f.solve(sl[t], c, st, args.max_iter, rtol=args.rtol, augmented=aug)
+            for tag, span, bar, mx in f.read_trace():
+                agg[tag].append((span, bar, mx))
+        f.set_trace(None)
+        f.close()
+        phases = {tag: {"n_per_frame": len(v) / 5.0, "span_us": float(np.mean([x[0] for x in v])) / 1e3,
+                        "barrier_us": float(np.mean([x[1] for x in v])) / 1e3,
+                        "max_cta_us": float(np.mean([x[2] for x in v])) / 1e3} for tag, v in agg.items()}
+        out["forms"]["augmented" if aug else "plain"] = {"us_per_frame": float(np.mean(us)),
+                                                          "iterations": float(np.mean(its)), "phases": phases}
+    return out
+
+
 def run_conv_layers(args):
     """Device time of every convolution launch of the learned predictor's
     forward pass on the configuration's layer groups (random activations and
@@ -836,6 +922,9 @@ def main():
         return
     if args.conv_layers:
         print(json.dumps(run_conv_layers(args)))
+        return
+    if args.trace:
+        print(json.dumps(run_trace(args)))
         return
     if args.learned:
         print(json.dumps(run_learned(args)))

@@ -10,10 +10,11 @@
 //   2. all threads stage the four input rows y0-1 .. y0+2 once in shared
 //      memory as BF16, channel-minor: per (row, group of 8 channels) an array
 //      of RP pixels of 16 bytes (8 channels), pixel q holding x = q - 1 (zero
-//      for x outside the image and for padded channels); and the weights as
+//      for x outside the image and for padded channels), each 16-byte row
+//      packed in registers and written with one store; and the weights as
 //      per (tap, group of 8 input channels) the 8-row x 16-byte core matrices
-//      of the output channels; each 16-byte row is packed in registers and
-//      written with one store;
+//      of the output channels, read from w in its own (coalesced) order and
+//      written value by value into a zeroed image;
 //   3. one thread issues one tcgen05.mma (M = 128, N = Np, K = 16: two
 //      channel groups) per output row, tap and channel-group pair: the A
 //      operand of tap (ky, kx) for output row h is the staged row h + ky seen
@@ -155,36 +156,62 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     }
     if (tid == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)) : "memory");
 
-    // Every 16-byte row of a core matrix holds 8 consecutive input channels:
-    // a thread packs them and writes them with one 16-byte store (threads
-    // with consecutive pixels / output channels write consecutive rows).
-    // Weights: row (tap t, channel group g, output channel co).
+    // Every 16-byte row of a core matrix holds 8 consecutive input channels.
+    // Weights, row (tap t, channel group g, output channel co): the image is
+    // zeroed (padded channels stay 0), then w is read in its own order with
+    // consecutive threads on consecutive floats (coalesced; the old per-row
+    // gather touched a separate sector for every value) and each value is
+    // written as bfloat16 to its place in the row.
     const int nb = NP >> 3;
-    for (int e = tid; e < 9 * ncg * NP; e += kTcThreads) {
-        const int t = e / (ncg * NP), g = (e / NP) % ncg, co = e % NP;
-        float v[8];
-#pragma unroll
-        for (int j = 0; j < 8; j++) {
-            const int ci = g * 8 + j;
-            v[j] = (co < Cout && ci < Cin) ? __ldg(w + ((long)co * Cin + ci) * 9 + t) : 0.f;
-        }
-        *reinterpret_cast<uint4 *>(Wt + ((t * ncg + g) * nb + (co >> 3)) * 128 + (co & 7) * 16) = pack8(v);
-    }
+    const int wvec = 9 * ncg * nb * 8;  // 16-byte words of the weight image
+    for (int e = tid; e < wvec; e += kTcThreads) reinterpret_cast<uint4 *>(Wt)[e] = make_uint4(0u, 0u, 0u, 0u);
     // input: row (staged row r, channel group g, pixel q), q holding x = q - 1
     // and staged row r input row y0 + r - 1 (zero outside the image: the halo
-    // pixels and rows beyond it)
-    for (int e = tid; e < SR * ncg * kRP; e += kTcThreads) {
-        const int r = e / (ncg * kRP), g = (e / kRP) % ncg, q = e % kRP;
-        const int yy = y0 + r - 1, x = q - 1;
-        const bool inside = yy >= 0 && yy < H && x >= 0 && x < W;
-        const float *px = in + (long)b * in_bs + (long)yy * W + x;
-        float v[8];
+    // pixels and rows beyond it); threads with consecutive pixels read
+    // consecutive addresses of each channel, two rows of 8 channels at once
+    const int nx = SR * ncg * kRP;
+    for (int e0 = tid; e0 < nx; e0 += 2 * kTcThreads) {
+        float v[2][8];
 #pragma unroll
-        for (int j = 0; j < 8; j++) {
-            const int ci = g * 8 + j;
-            v[j] = (inside && ci < Cin) ? __ldg(px + (long)ci * in_cs) : 0.f;
+        for (int u = 0; u < 2; u++) {
+            const int e = e0 + u * kTcThreads;
+            const int r = e / (ncg * kRP), g = (e / kRP) % ncg, q = e % kRP;
+            const int yy = y0 + r - 1, x = q - 1;
+            const bool inside = e < nx && yy >= 0 && yy < H && x >= 0 && x < W;
+            const float *px = in + (long)b * in_bs + (long)yy * W + x;
+#pragma unroll
+            for (int j = 0; j < 8; j++) {
+                const int ci = g * 8 + j;
+                v[u][j] = (inside && ci < Cin) ? __ldg(px + (long)ci * in_cs) : 0.f;
+            }
         }
-        *reinterpret_cast<uint4 *>(X + ((r * ncg + g) * kRP + q) * 16) = pack8(v);
+#pragma unroll
+        for (int u = 0; u < 2; u++) {
+            const int e = e0 + u * kTcThreads;
+            if (e < nx) *reinterpret_cast<uint4 *>(X + (size_t)e * 16) = pack8(v[u]);
+        }
+    }
+    __syncthreads();  // the weight image is zero
+    {
+        const int nw = Cout * Cin * 9;
+        constexpr int UW = 8;  // loads in flight per thread
+        for (int e0 = tid; e0 < nw; e0 += UW * kTcThreads) {
+            float v[UW];
+#pragma unroll
+            for (int u = 0; u < UW; u++) {
+                const int e = e0 + u * kTcThreads;
+                v[u] = e < nw ? __ldg(w + e) : 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < UW; u++) {
+                const int e = e0 + u * kTcThreads;
+                if (e < nw) {
+                    const int t = e % 9, cc = e / 9, ci = cc % Cin, co = cc / Cin;  // e = (co Cin + ci) 9 + t
+                    unsigned char *row = Wt + (((t * ncg + (ci >> 3)) * nb + (co >> 3)) * 128 + (co & 7) * 16);
+                    reinterpret_cast<__nv_bfloat16 *>(row)[ci & 7] = __float2bfloat16_rn(v[u]);
+                }
+            }
+        }
     }
     // the operands become visible to the tensor core (async proxy)
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");

@@ -661,10 +661,10 @@ def autotune_batch(fewhas, step, candidates=None, reps=3, tiles=((8, 8), (16, 16
     stars, subapertures) form a class and share their settings.  Stages:
       1. CTA split and rounds: the library's work-proportional split in one
          round; two rounds with the largest class first on the whole GPU
-         (CTAs per instance = SMs / instances of that class) and the others
-         after it, split in proportion to their work; variants of those
-         splits (scaled by 3/4 and 5/4 within the SM count).  `candidates`
-         (a list of (ctas, rounds) pairs) replaces the generated ones.
+         (CTAs per instance = SMs / instances of that class, in one or in two
+         rounds of its own) and the others after it, split in proportion to
+         their work.  `candidates` (a list of (ctas, rounds) pairs) replaces
+         the generated ones.
       2. WFS tile shape per class (`tiles`), in turn, keeping a change only
          when the step gets faster.
       3. P^T band heights per class (`bands`: rows on the largest and on the
