@@ -603,15 +603,18 @@ def run_compare(geom, w, frames, args, stats_buf, flush, main):
     K = min(args.steps, 60)
     sdts = {"f64": torch.float64, "f32": torch.float32, "bf16s": torch.bfloat16}
 
-    def one(g, wts, fr, prec, aug, tre=0):
+    def one(g, wts, fr, prec, aug, tre=0, rtol=None, nframes=None):
         f = Fewha(g, wts, prec, tile=args.tile, grid=args.grid)
         a = copy.copy(args)
-        times, stats = time_solves(f, fr, sdts[prec], a, args.warmup, K, aug, flush, stats_buf, args.rtol,
-                                   true_res_every=tre)
+        n = nframes or K
+        if rtol is not None:
+            a.max_iter = 1000  # the largest a solve takes (FEWHA_MAX_ITER)
+        times, stats = time_solves(f, fr, sdts[prec], a, args.warmup, n, aug, flush, stats_buf,
+                                   args.rtol if rtol is None else rtol, true_res_every=tre)
         f.close()
         it = [x["iterations"] for x in stats]
-        return {"us_per_frame": sum(times) / K * 1e3, "frames_per_s": K / (sum(times) / 1e3),
-                "iterations_mean": float(np.mean(it)), "frames": K,
+        return {"us_per_frame": sum(times) / n * 1e3, "frames_per_s": n / (sum(times) / 1e3),
+                "iterations_mean": float(np.mean(it)), "frames": n,
                 "status_ok": all(x["status"] == 0 for x in stats)}
 
     res = {}
@@ -633,6 +636,18 @@ def run_compare(geom, w, frames, args, stats_buf, flush, main):
     for snr, r in res.items():
         if "plain_f32" in r and "aug_f32" in r:
             r["aug_minus_plain_us"] = r["aug_f32"]["us_per_frame"] - r["plain_f32"]["us_per_frame"]
+    # tighter residual targets (at most 1000 iterations a frame), plain against
+    # augmented, FP32 and FP64, on the first frames of both sequences
+    ns = min(K, 20)
+    sweep = {}
+    for rt in (1e-3, 1e-4):
+        for tag, g, wts, fr in ((snr0, geom, w, frames), ("snr100", g100, w100, fr100)):
+            r = {}
+            for prec in ("f32", "f64"):
+                for aug in (False, True):
+                    r["%s_%s" % ("aug" if aug else "plain", prec)] = one(g, wts, fr, prec, aug, rtol=rt, nframes=ns)
+            sweep["rtol %g, %s" % (rt, tag)] = r
+    res["rtol_sweep"] = sweep
     return res
 
 
