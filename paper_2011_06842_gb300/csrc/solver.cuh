@@ -109,8 +109,11 @@ __device__ __forceinline__ void phase_gram(const Args<T, S> &A, const Basis &b, 
     const int CH = (sm_elems / nvec) / W * W;  // elements of the slice staged at once
     __shared__ const T *sp[kK], *sq[kK];
     basis_table(A, b, sp, sq);
-    Acc acc[(kK * kK + 31) / 32];
-    for (int i = 0; i < (kK * kK + 31) / 32; i++) acc[i] = 0;
+    // warp w sums slots w, w + nw, w + 2 nw, ...: at most kGramT of them
+    // (nw = kThreads / 32 warps; k = FEWHA_MAX_K gives kK^2 slots)
+    constexpr int kGramT = (kK * kK + kThreads / 32 - 1) / (kThreads / 32);
+    Acc acc[kGramT];
+    for (int i = 0; i < kGramT; i++) acc[i] = 0;
     for (long c0 = lo; c0 < hi; c0 += CH) {
         const int len = (int)min((long)CH, hi - c0);
         const int nv = len / W, total = nvec * nv;
@@ -135,7 +138,7 @@ __device__ __forceinline__ void phase_gram(const Args<T, S> &A, const Basis &b, 
             }
         }
         __syncthreads();
-        for (int s2 = warp, t = 0; s2 < nslot; s2 += nw, t++) {
+        for (int s2 = warp, t = 0; s2 < nslot && t < kGramT; s2 += nw, t++) {
             const T *X = sm + (s2 / kv) * CH, *Y = sm + (kv + s2 % kv) * CH;
             Acc a = 0;
             for (int e = lane; e < len; e += 32) a += (Acc)X[e] * (Acc)Y[e];
@@ -143,7 +146,7 @@ __device__ __forceinline__ void phase_gram(const Args<T, S> &A, const Basis &b, 
         }
         __syncthreads();
     }
-    for (int s2 = warp, t = 0; s2 < nslot; s2 += nw, t++) {
+    for (int s2 = warp, t = 0; s2 < nslot && t < kGramT; s2 += nw, t++) {
         const Acc a = warp_sum_t(acc[t]);
         if (lane == 0) A.part[(size_t)(kSlotGram + s2) * kMaxCtas + A.vrank()] = (double)a;
     }

@@ -1,0 +1,136 @@
+"""GPU parity at the limits of the C ABI and in the method's degenerate
+cases, against the FP64 oracle: 16 guide stars and 16 layers
+(FEWHA_MAX_GS, FEWHA_MAX_LAYERS) with a recycled basis of FEWHA_MAX_K = 16
+directions (a 16 x 16 Gram matrix); a 128 x 128 layer transformed to the
+deepest level J = 7 (a 1 x 1 approximation, periodic folds shorter than the
+filter); one guide star and one layer; and the other Daubechies orders
+(Haar, Daubechies-2 and -4: 2, 4 and 8 taps).  Operator application (Eq. M)
+and augmented time steps (Algorithm 2 inside Algorithm 3) in FP64 at 1e-10
+and FP32 at 1e-5, persistent and per-phase launches."""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import Oracle  # noqa: E402
+from synth import FrozenFlowSensors, configs, random_vector  # noqa: E402
+
+TOL = {"f64": 1e-10, "f32": 1e-5}
+DT = {"f64": torch.float64, "f32": torch.float32}
+A = configs.ARCSEC
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def many():
+    """16 guide stars (NGS and LGS alternating, 8 x 8 sensors) and 16 layers of
+    16 x 16 nodes, 4 levels; recycled basis of 16."""
+    gs = [configs.GuideStar(20 * A * math.cos(2 * math.pi * k / 16), 20 * A * math.sin(2 * math.pi * k / 16),
+                            90000.0 if k % 2 else 0.0, 8) for k in range(16)]
+    layers = [configs.Layer(800.0 * i, 1.0 / 16, 16, 4) for i in range(16)]
+    return configs.Geometry("max16", D=4.0, obstruction=0.0, n_sub=8, gs=gs, layers=layers, r0=0.15,
+                            k_recycle=16, wind=[(10.0, 0.3 * i) for i in range(16)])
+
+
+def deep():
+    """One NGS and one 128 x 128 ground layer transformed to J = 7 levels."""
+    return configs.Geometry("deep", D=8.0, obstruction=0.1, n_sub=16, gs=[configs.GuideStar(5 * A, 0.0, 0.0)],
+                            layers=[configs.Layer(0.0, 1.0, 128, 7)], r0=0.15, k_recycle=4, wind=[(8.0, 0.2)])
+
+
+def order(N):
+    g = configs.tiny()
+    g.wavelet_N = N
+    g.name = "tiny_db%d" % N
+    return g
+
+
+GEOMS = {"max16": many, "deep": deep, "db1": lambda: order(1), "db2": lambda: order(2), "db4": lambda: order(4)}
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2011_06842_gb300 import build
+    build.build()
+    import paper_2011_06842_gb300 as P
+    return P
+
+
+_cache = {}
+
+
+def setup(name):
+    if name not in _cache:
+        geom = GEOMS[name]()
+        s, w = FrozenFlowSensors(geom, seed=3).sequence(4, seed=4)
+        _cache[name] = (geom, s.numpy(), w, Oracle(geom, w))
+    return _cache[name]
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("name", sorted(GEOMS))
+def test_operator_and_rhs_at_the_limits(lib, name, prec):
+    geom, s, w, o = setup(name)
+    f = lib.Fewha(geom, w, prec)
+    x = random_vector(o.n, 21)
+    xd = torch.tensor(x, dtype=DT[prec], device="cuda")
+    assert rel(f.apply_op(xd).cpu().numpy(), o.apply_op(x)) < TOL[prec]
+    sl = torch.tensor(s[0], dtype=DT[prec], device="cuda")
+    assert rel(f.rhs(sl).cpu().numpy(), o.rhs(s[0])) < TOL[prec]
+    f.close()
+
+
+@pytest.mark.parametrize("persistent", [True, False])
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("name", sorted(GEOMS))
+def test_augmented_steps_at_the_limits(lib, name, prec, persistent):
+    """Four time steps of augmented PCG with a fixed iteration count; the
+    recycled basis holds the last min(iterations, k) directions of the
+    previous step, so on max16 (18 iterations) the steps after the first
+    project onto 16 directions (a 16 x 16 Gram matrix and Cholesky factor).
+    FP32 runs 4 iterations a step, like the other few-iteration FP32 parity
+    tests: longer FP32 runs drift from the FP64 oracle at the level kappa u_32
+    (CG amplifies rounding), not within 1e-5.  The unobservable piston of a
+    J = lg n layer is left out of the comparison (`observable`)."""
+    geom, s, w, o = setup(name)
+    k = geom.k_recycle
+    its = (18 if name == "max16" else 6) if prec == "f64" else 4
+    f = lib.Fewha(geom, w, prec)
+    st_o, st_g = o.new_state(k), f.new_state(k)
+    c = torch.zeros(o.n, dtype=DT[prec], device="cuda")
+    for t in range(4):
+        ro = o.solve(s[t], st_o, max_iter=its, augmented=True)
+        rg = f.read_stats(f.solve(torch.tensor(s[t], dtype=DT[prec], device="cuda"), c, st_g, its,
+                                  persistent=persistent))
+        assert rg["status"] == 0 and rg["iterations"] == ro["iterations"], (t, rg)
+        if t > 0:
+            assert rg["basis_count"] == min(its, k)
+        keep = observable(geom)
+        assert rel(c.cpu().numpy()[keep], st_o["c"][keep]) < TOL[prec], t
+    f.close()
+
+
+def observable(geom):
+    """Coefficients other than the piston of a layer transformed to the
+    deepest level (J = lg n: its 1 x 1 approximation is the layer's mean).
+    Shack-Hartmann slopes do not see a constant phase, so that coefficient's
+    row of M is alpha D_00 alone and its value b_0 / (alpha D_00) is the
+    rounding of b_0 (zero in exact arithmetic) times ~1 / (alpha D_00) (~2e7
+    on the deep geometry): ~1e-9 in FP64, different on each side, ~10 in FP32.
+    The comparisons leave these coefficients out (max16 has one per layer)."""
+    keep = np.ones(geom.n_unknowns, dtype=bool)
+    off = 0
+    for lay in geom.layers:
+        if lay.n >> lay.J == 1:
+            keep[off] = False
+        off += lay.n * lay.n
+    return keep
