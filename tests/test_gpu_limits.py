@@ -99,23 +99,33 @@ def test_augmented_steps_at_the_limits(lib, name, prec, persistent):
     project onto 16 directions (a 16 x 16 Gram matrix and Cholesky factor).
     FP32 runs 4 iterations a step, like the other few-iteration FP32 parity
     tests: longer FP32 runs drift from the FP64 oracle at the level kappa u_32
-    (CG amplifies rounding), not within 1e-5.  The unobservable piston of a
+    (CG amplifies rounding), not within 1e-5.  FP64: 1e-10, or 100 times the
+    oracle's own sensitivity to a 1e-16 perturbation of the slopes when 18
+    iterations amplify rounding beyond that.  The unobservable piston of a
     J = lg n layer is left out of the comparison (`observable`)."""
     geom, s, w, o = setup(name)
     k = geom.k_recycle
     its = (18 if name == "max16" else 6) if prec == "f64" else 4
     f = lib.Fewha(geom, w, prec)
-    st_o, st_g = o.new_state(k), f.new_state(k)
+    st_o, st_t, st_g = o.new_state(k), o.new_state(k), f.new_state(k)
     c = torch.zeros(o.n, dtype=DT[prec], device="cuda")
+    keep = observable(geom)
+    rng = np.random.default_rng(5)
     for t in range(4):
         ro = o.solve(s[t], st_o, max_iter=its, augmented=True)
+        # FP64: the oracle's own rounding sensitivity over these iterations
+        # (a twin run on slopes perturbed by 1e-16 relative) bounds the GPU's
+        # distance from it, as for the residual-driven solves at ELT size
+        o.solve(s[t] * (1 + 1e-16 * rng.standard_normal(s[t].shape)), st_t, max_iter=its, augmented=True)
+        sens = rel(st_t["c"][keep], st_o["c"][keep])
+        tol = max(TOL[prec], 100 * sens) if prec == "f64" else TOL[prec]
         rg = f.read_stats(f.solve(torch.tensor(s[t], dtype=DT[prec], device="cuda"), c, st_g, its,
                                   persistent=persistent))
         assert rg["status"] == 0 and rg["iterations"] == ro["iterations"], (t, rg)
         if t > 0:
             assert rg["basis_count"] == min(its, k)
-        keep = observable(geom)
-        assert rel(c.cpu().numpy()[keep], st_o["c"][keep]) < TOL[prec], t
+        err = rel(c.cpu().numpy()[keep], st_o["c"][keep])
+        assert err < tol, (t, err, sens)
     f.close()
 
 
