@@ -232,7 +232,10 @@ int fewha_apply_op(void *handle, const void *x, void *y, cudaStream_t stream);
 #define FEWHA_MAX_MULTI 8
 int fewha_apply_op_multi(void *handle, const void *x, long ldx, void *y, long ldy, int nvec, cudaStream_t stream);
 
-/* b = W^{-T} A^T C_eta^{-1} s (right-hand side of Eq. fewha; Algorithm 3). */
+/* b = W^{-T} A^T C_eta^{-1} s (right-hand side of Eq. fewha; Algorithm 3).
+ * s: device, managed or page-locked host memory (cudaHostAlloc,
+ * cudaMallocHost, cudaHostRegister), read by the kernels where it lies;
+ * pageable host memory is refused (FEWHA_ERR_ARG). */
 int fewha_rhs(void *handle, const void *s, void *b, cudaStream_t stream);
 
 /* Mirror side of the reconstructor loop (Algorithm 3).  Reading of the
@@ -267,6 +270,9 @@ int fewha_control(void *handle, int closed, double gain, const void *a_im1, cons
  *   b = rhs(s); r0 = (b - b_prev) + r_prev; b_prev <- b;
  *   (aug)PCG from the warm start c, updating c (in/out, device, n) and r_prev;
  *   the directions of this solve become the recycled basis of the next one.
+ * s: as for fewha_rhs (device, managed or page-locked host memory: a frame's
+ * slopes can be read by the kernel straight from the page-locked buffer the
+ * sensors write, with no copy on the stream); pageable host memory is refused.
  * stats_dev: device pointer to a fewha_stats, written at the end. */
 int fewha_solve(void *handle, const void *s, void *c, const fewha_state *state,
                 const fewha_solve_opts *opts, fewha_stats *stats_dev, cudaStream_t stream);
@@ -482,6 +488,14 @@ int fewha_apply_op_noalloc(void *handle, const void *x, void *y, cudaStream_t st
 int fewha_read_probe(const void *buf, long bytes, int reps, float *sink, cudaStream_t stream);
 
 /* Text of a status code. */
+/* Copies `bytes` (a multiple of 16, both addresses 16-byte aligned, no
+ * overlap) from src to dst with a kernel on `stream`; either side may be
+ * device, managed or page-locked host memory (the typical use: a time step's
+ * solution into the page-locked buffer the host reads, without a copy-engine
+ * transfer on the stream).  FEWHA_ERR_ARG for pageable host memory or bad
+ * sizes; asynchronous. */
+int fewha_store(void *dst, const void *src, long bytes, cudaStream_t stream);
+
 const char *fewha_strerror(int status);
 
 #ifdef __cplusplus

@@ -8,7 +8,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libfewha.so")
 BUILD = os.path.join(HERE, "_build")
-CUDA_SOURCES = ["api.cu", "inst_f64.cu", "inst_f32.cu", "inst_bf16.cu", "noalloc.cu", "learned.cu", "probe.cu", "conv_tc.cu"]
+CUDA_SOURCES = ["api.cu", "inst_f64.cu", "inst_f32.cu", "inst_bf16.cu", "noalloc.cu", "learned.cu", "probe.cu", "conv_tc.cu", "transfer.cu"]
 CXX_SOURCES = ["plan.cpp"]
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
               "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off"]

@@ -25,6 +25,8 @@ struct Handle {
 // Vectors are accessed with 16-byte loads and stores.
 static bool aligned16(const void *p) { return ((size_t)p & 15) == 0; }
 
+const void *fewha_device_view(const void *p);  // transfer.cu
+
 ImplBase *handle_impl(void *handle) { return handle ? static_cast<Handle *>(handle)->w() : nullptr; }
 int handle_device(const void *handle) { return handle ? static_cast<const Handle *>(handle)->device : -1; }
 
@@ -313,6 +315,8 @@ int fewha_control(void *handle, int closed, double gain, const void *a_im1, cons
 int fewha_rhs(void *handle, const void *s, void *b, cudaStream_t stream)
 {
     if (!handle || !s || !b || !aligned16(b)) return FEWHA_ERR_ARG;
+    s = fewha_device_view(s);  // device, managed or page-locked host slopes
+    if (!s) return FEWHA_ERR_ARG;
     return static_cast<Handle *>(handle)->w()->rhs(s, b, stream);
 }
 
@@ -330,6 +334,10 @@ int fewha_solve(void *handle, const void *s, void *c, const fewha_state *st, con
     if (o->true_res_every < 0 || o->true_res_every > FEWHA_MAX_ITER) return FEWHA_ERR_ARG;
     if (o->launch_mode != FEWHA_LAUNCH_PERSISTENT && o->launch_mode != FEWHA_LAUNCH_PHASES) return FEWHA_ERR_ARG;
     if (o->recycle_mode != FEWHA_RECYCLE_LAST && o->recycle_mode != FEWHA_RECYCLE_ALL) return FEWHA_ERR_ARG;
+    if (!o->rhs_in_state) {
+        s = fewha_device_view(s);  // device, managed or page-locked host slopes
+        if (!s) return FEWHA_ERR_ARG;
+    }
     return static_cast<Handle *>(handle)->w()->solve(s, c, st, o, stats, stream);
 }
 

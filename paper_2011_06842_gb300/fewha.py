@@ -97,6 +97,8 @@ def load_library(path=LIB_PATH):
     lib.fewha_layer_spacing.restype = C.c_double
     lib.fewha_read_probe.argtypes = [vp, C.c_long, C.c_int, vp, vp]
     lib.fewha_read_probe.restype = C.c_int
+    lib.fewha_store.argtypes = [vp, vp, C.c_long, vp]
+    lib.fewha_store.restype = C.c_int
     lib.fewha_set_pt_bands.argtypes = [vp, C.c_int, C.c_int]
     lib.fewha_set_pt_bands.restype = C.c_int
     lib.fewha_set_noise.argtypes = [vp, dp, C.c_int]
@@ -193,7 +195,7 @@ def exported_symbols():
             "fewha_mse_grad", "fewha_adam_step", "fewha_scale", "fewha_learned_targets",
             "fewha_deflate_warm_start", "fewha_mcao_create", "fewha_mcao_n_actuators", "fewha_mcao_fit",
             "fewha_mcao_destroy", "fewha_get_launch_info", "fewha_set_noise", "fewha_read_probe", "fewha_set_pt_bands",
-            "fewha_batch_create_ex", "fewha_batch_tiles", "fewha_conv3x3_fwd_tc"]
+            "fewha_batch_create_ex", "fewha_batch_tiles", "fewha_conv3x3_fwd_tc", "fewha_store"]
 
 
 def make_geometry(geom, noise_w, precision="f64", tile=0, grid=0) -> GEOMETRY:
@@ -313,10 +315,15 @@ class Fewha:
         if st != 0:
             raise FewhaError(st, what)
 
-    def _vec(self, t, n, dtype, name):
+    def _vec(self, t, n, dtype, name, host_ok=False):
+        """Pointer of a contiguous tensor of n elements: a CUDA tensor, or with
+        host_ok a page-locked (pinned) CPU tensor, which the kernels read in
+        place over the host link."""
         torch = self._torch
-        if not isinstance(t, torch.Tensor) or t.device.type != "cuda" or t.dtype != dtype:
-            raise TypeError("%s must be a CUDA tensor of %s" % (name, dtype))
+        on_host = host_ok and isinstance(t, torch.Tensor) and t.device.type == "cpu" and t.is_pinned()
+        if not isinstance(t, torch.Tensor) or (t.device.type != "cuda" and not on_host) or t.dtype != dtype:
+            raise TypeError("%s must be a CUDA tensor%s of %s" % (name, " or a pinned CPU tensor" if host_ok else "",
+                                                                 dtype))
         if t.numel() != n or not t.is_contiguous():
             raise ValueError("%s must be contiguous with %d elements" % (name, n))
         return C.c_void_p(t.data_ptr())
@@ -354,7 +361,7 @@ class Fewha:
     def rhs(self, s, out=None):
         """b = W^{-T} A^T C_eta^{-1} s."""
         b = out if out is not None else self._torch.empty(self.n, dtype=self.dtype, device=self.device)
-        self._check(self.lib.fewha_rhs(self._h, self._vec(s, self.n_slopes, self.slope_dtype, "s"),
+        self._check(self.lib.fewha_rhs(self._h, self._vec(s, self.n_slopes, self.slope_dtype, "s", host_ok=True),
                                        self._vec(b, self.n, self.dtype, "b"), _stream_ptr(self._torch)),
                     "fewha_rhs")
         return b
@@ -407,13 +414,15 @@ class Fewha:
         """One time step; c is updated in place.  Returns the device stats buffer.
         true_res_every = N > 0 replaces the residual by b - M c after every N-th
         iteration; rhs_in_state: the state already holds this step's
-        right-hand side (after fewha_deflate_warm_start), s is not read."""
+        right-hand side (after fewha_deflate_warm_start), s is not read.
+        s: a CUDA tensor, or a pinned CPU tensor that the kernel reads in place."""
         o = OPTS(int(max_iter), float(rtol), 1 if augmented else 0,
                  RECYCLE_ALL if recycle_all else RECYCLE_LAST,
                  LAUNCH_PERSISTENT if persistent else LAUNCH_PHASES, int(true_res_every),
                  1 if rhs_in_state else 0)
         stats = stats if stats is not None else self.new_stats()
-        sp = None if (rhs_in_state and s is None) else self._vec(s, self.n_slopes, self.slope_dtype, "s")
+        sp = None if (rhs_in_state and s is None) else self._vec(s, self.n_slopes, self.slope_dtype, "s",
+                                                                 host_ok=True)
         self._check(self.lib.fewha_solve(self._h, sp,
                                          self._vec(c, self.n, self.dtype, "c"), C.byref(state.c_struct),
                                          C.byref(o), C.c_void_p(stats.data_ptr()),
@@ -455,6 +464,22 @@ class Fewha:
             out.append((self.TRACE_TAGS.get(int(tag), str(tag)), span, int(passed - end), int(maxcta)))
             prev = passed
         return out
+
+    def store(self, src, dst):
+        """dst <- src by a library kernel (fewha_store): e.g. a solution into a
+        pinned CPU tensor without a copy-engine transfer on the stream.  Both
+        contiguous, the same number of bytes (a multiple of 16)."""
+        torch = self._torch
+        for t, nm in ((src, "src"), (dst, "dst")):
+            if not isinstance(t, torch.Tensor) or not t.is_contiguous() or not (
+                    t.device.type == "cuda" or (t.device.type == "cpu" and t.is_pinned())):
+                raise TypeError("%s must be a contiguous CUDA tensor or pinned CPU tensor" % nm)
+        nb = src.numel() * src.element_size()
+        if dst.numel() * dst.element_size() != nb:
+            raise ValueError("src and dst differ in size")
+        self._check(self.lib.fewha_store(C.c_void_p(dst.data_ptr()), C.c_void_p(src.data_ptr()), nb,
+                                         _stream_ptr(torch)), "fewha_store")
+        return dst
 
     @staticmethod
     def read_stats(stats):

@@ -229,3 +229,35 @@ def test_solve_with_rhs_in_state(lib, prec):
         assert rel(c.cpu().numpy(), st_o["c"]) < TOL[prec], t
         assert rel(st_g.r_prev.cpu().numpy(), st_o["r_prev"]) < 10 * TOL[prec], t
     f.close()
+
+
+def test_host_slopes_and_store(lib):
+    """Slopes in page-locked host memory are read by the kernels in place and
+    give bit-identical results to the same slopes in device memory;
+    fewha_store writes a solution into page-locked host memory; pageable host
+    memory is refused before any launch."""
+    import ctypes as C
+    geom, s, w, o = setup("tiny")
+    f = lib.Fewha(geom, w, "f64")
+    host = torch.tensor(np.asarray(s[:3]), dtype=torch.float64).pin_memory()
+    dev_s = host.cuda()
+    b_dev, b_host = f.rhs(dev_s[0]), f.rhs(host[0])
+    assert torch.equal(b_dev, b_host)
+    st_d, st_h = f.new_state(4), f.new_state(4)
+    c_d = torch.zeros(o.n, dtype=torch.float64, device="cuda")
+    c_h = torch.zeros_like(c_d)
+    for t in range(3):
+        assert f.read_stats(f.solve(dev_s[t], c_d, st_d, 4))["status"] == 0
+        assert f.read_stats(f.solve(host[t], c_h, st_h, 4))["status"] == 0
+        assert torch.equal(c_d, c_h)
+    out = torch.empty(o.n, dtype=torch.float64).pin_memory()
+    f.store(c_h, out)
+    torch.cuda.synchronize()
+    assert torch.equal(out, c_h.cpu())
+    # pageable host memory: refused by the C ABI before anything runs
+    pageable = np.ascontiguousarray(s[0], dtype=np.float64)
+    stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    assert f.lib.fewha_rhs(f._h, C.c_void_p(pageable.ctypes.data), C.c_void_p(b_dev.data_ptr()), stream) == -1
+    page_out = np.empty(o.n, dtype=np.float64)
+    assert f.lib.fewha_store(C.c_void_p(page_out.ctypes.data), C.c_void_p(c_h.data_ptr()), o.n * 8, stream) == -1
+    f.close()
