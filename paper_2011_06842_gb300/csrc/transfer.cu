@@ -9,6 +9,8 @@
 
 #include "../../include/fewha.h"
 
+namespace fewha {
+
 // The address under which the device reaches p: p itself for device and
 // managed memory, the mapped address for page-locked host memory
 // (cudaHostAlloc, cudaMallocHost, cudaHostRegister); nullptr for pageable
@@ -32,6 +34,8 @@ const void *fewha_device_view(const void *p)
     }
 }
 
+}  // namespace fewha
+
 namespace {
 
 __global__ void __launch_bounds__(256) k_store(const float4 *__restrict__ src, float4 *__restrict__ dst, long n16)
@@ -45,8 +49,8 @@ __global__ void __launch_bounds__(256) k_store(const float4 *__restrict__ src, f
 extern "C" int fewha_store(void *dst, const void *src, long bytes, cudaStream_t stream)
 {
     if (!dst || !src || bytes < 16 || (bytes & 15) || ((size_t)src & 15)) return FEWHA_ERR_ARG;
-    void *d = const_cast<void *>(fewha_device_view(dst));
-    const void *s = fewha_device_view(src);
+    void *d = const_cast<void *>(fewha::fewha_device_view(dst));
+    const void *s = fewha::fewha_device_view(src);
     if (!d || !s || ((size_t)d & 15) || ((size_t)s & 15)) return FEWHA_ERR_ARG;
     const char *sb = static_cast<const char *>(s), *db = static_cast<const char *>(d);
     if (sb < db + bytes && db < sb + bytes) return FEWHA_ERR_ARG;  // no overlap
