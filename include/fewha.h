@@ -15,7 +15,9 @@
  *    (barrier timeout, CG breakdown) are reported in fewha_stats.status,
  *    valid after the stream has been synchronised.
  *  - Memory: all vectors passed to the compute calls are DEVICE pointers owned
- *    by the caller, allocated on the device the handle was created on.
+ *    by the caller, allocated on the device the handle was created on; the
+ *    slopes of fewha_rhs / fewha_solve may also be page-locked host memory
+ *    (read in place by the kernels), and fewha_store may write to it.
  *    Coefficient vectors (x, y, b, c and the state vectors) must be 16-byte
  *    aligned (FEWHA_ERR_ARG otherwise); slopes need only element alignment.  The
  *    handle owns its constant tables and its scratch memory.  Nothing is
