@@ -458,11 +458,11 @@ def run_batched(args, flush):
 def run_e2e(f, geom, frames, sdt, args, aug, flush):
     """Same metric through the public API with host buffers: every frame's
     slopes come from pinned host memory and its solution c goes back to pinned
-    host memory inside the frame's timed window.  The slopes are read by the
-    solve kernel in place (fewha_solve accepts page-locked host slopes) and c is
-    written by the library's store kernel (fewha_store), so the bytes cross the
-    host link with no copy-engine transfer on the stream.  L2 is flushed before
-    every frame (outside the window), as for `value`."""
+    host memory inside the frame's timed window.  The solve kernel reads the
+    slopes in place (fewha_solve accepts page-locked host slopes) and writes c
+    into the host buffer at the end of the step (fewha_solve_opts.c_out), so
+    the bytes cross the host link with no transfer on the stream.  L2 is
+    flushed before every frame (outside the window), as for `value`."""
     import torch
     K = args.steps
     host = frames[args.warmup:args.warmup + K].to(sdt).cpu().pin_memory()
@@ -481,8 +481,7 @@ def run_e2e(f, geom, frames, sdt, args, aug, flush):
             flush.zero_()
         ev[t][0].record()
         f.solve(host[t], c, st, args.max_iter, rtol=args.rtol, augmented=aug,
-                persistent=args.launch == "persistent", stats=stats)
-        f.store(c, out_host[t])
+                persistent=args.launch == "persistent", stats=stats, c_out=out_host[t])
         ev[t][1].record()
     torch.cuda.synchronize()
     ms = sum(a.elapsed_time(b) for a, b in ev)
@@ -513,7 +512,7 @@ def run_e2e(f, geom, frames, sdt, args, aug, flush):
     return {"value": K / (ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": f.n_slopes * esz,
             "d2h_bytes_per_step": f.n * c.element_size(), "us_per_frame": ms / K * 1e3,
             "transfer": "slopes read by the solve kernel from pinned host memory; c written to pinned host "
-                        "memory by fewha_store",
+                        "memory by the solve kernel (fewha_solve_opts.c_out)",
             "result_check": ok,
             "copy_engine": {"value": K / (ms_ce / 1e3), "us_per_frame": ms_ce / K * 1e3},
             "l2": "flushed before every frame (outside the timed window), as for value"}

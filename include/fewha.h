@@ -146,6 +146,13 @@ typedef struct {
      * right-hand side and warm restart from s. */
     int rhs_in_state;
     int pad;
+    /* Optional (NULL: none): at the end of the time step the solution c is
+     * also written here by the solve kernel itself: device, managed or
+     * page-locked host memory (n elements of c's type, 16-byte aligned, not
+     * overlapping c); pageable host memory is refused (FEWHA_ERR_ARG).  With
+     * page-locked host memory the solution reaches the host with no transfer
+     * on the stream.  Ignored by the batch calls. */
+    void *c_out;
 } fewha_solve_opts;
 
 /* Written on the device at the end of fewha_solve. */

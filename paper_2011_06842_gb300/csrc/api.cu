@@ -338,7 +338,17 @@ int fewha_solve(void *handle, const void *s, void *c, const fewha_state *st, con
         s = fewha_device_view(s);  // device, managed or page-locked host slopes
         if (!s) return FEWHA_ERR_ARG;
     }
-    return static_cast<Handle *>(handle)->w()->solve(s, c, st, o, stats, stream);
+    fewha_solve_opts ov = *o;
+    if (ov.c_out) {
+        // the second destination of the solution, as the device reaches it
+        Handle *h = static_cast<Handle *>(handle);
+        const size_t bytes = (size_t)h->plan.n * (h->w()->precision_id() == FEWHA_F64 ? 8 : 4);
+        ov.c_out = const_cast<void *>(fewha_device_view(o->c_out));
+        if (!ov.c_out || !aligned16(ov.c_out)) return FEWHA_ERR_ARG;
+        const char *a = static_cast<const char *>(ov.c_out), *cc = static_cast<const char *>(c);
+        if (a < cc + bytes && cc < a + bytes) return FEWHA_ERR_ARG;  // must not overlap c
+    }
+    return static_cast<Handle *>(handle)->w()->solve(s, c, st, &ov, stats, stream);
 }
 
 int fewha_batch_create(void *const *handles, int n, const int *ctas, void **batch_out)

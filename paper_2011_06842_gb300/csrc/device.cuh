@@ -138,6 +138,7 @@ struct __align__(16) Args {
     const S *slopes; // rhs / solve: measured slopes
     // solver
     T *c, *r, *b_prev;
+    T *c_out;        // optional second destination of the solution (written at the end)
     T *P, *Q;        // [2][kcap][n]
     double *pq;      // [2][kcap]
     int *meta;

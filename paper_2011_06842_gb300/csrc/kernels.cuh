@@ -370,6 +370,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_finish(const __grid_constant__ 
     __shared__ Scal sc;
     __shared__ __align__(16) Args<T, S> A;
     args_to_smem(Ap, A);
+    if (A.c_out) phase_store_c<T, S>(A);
     if (A.vrank() != 0) return;
     const Basis b = basis_info(A);
     int K = ldcgi(&A.rec->done) ? ldcgi(&A.rec->iters) : A.max_iter;
@@ -491,6 +492,7 @@ __device__ void solve_body(const Args<T, S> &A, Scal &sc, double *sred)
     } while (0);
     // on a device-side error the stats carry the status; the other fields are
     // then not meaningful
+    if (A.c_out) phase_store_c<T, S>(A);
     if (rank == 0) phase_finish<T, S>(A, b, K, sc);
 }
 
@@ -1428,6 +1430,7 @@ struct Impl : ImplBase {
         A.recycle_all = o->recycle_mode == FEWHA_RECYCLE_ALL ? 1 : 0;
         A.true_res_every = o->true_res_every;
         A.rhs_in_state = o->rhs_in_state ? 1 : 0;
+        A.c_out = static_cast<T *>(o->c_out);
         A.stats = stats;
         return A;
     }
@@ -1436,6 +1439,7 @@ struct Impl : ImplBase {
                    fewha_stats *stats, int cta0, int nct, int ty, int tx, size_t sm) const override
     {
         Args<T, S> A = solve_args(sl, c, st, o, stats);
+        A.c_out = nullptr;  // the batch calls have no second destination
         A.cta0 = cta0;
         A.ncta = nct;
         set_tiles(A.geo, ty, tx);

@@ -56,7 +56,7 @@ class STATE(C.Structure):
 class OPTS(C.Structure):
     _fields_ = [("max_iter", C.c_int), ("rtol", C.c_double), ("augmented", C.c_int),
                 ("recycle_mode", C.c_int), ("launch_mode", C.c_int), ("true_res_every", C.c_int),
-                ("rhs_in_state", C.c_int), ("pad", C.c_int)]
+                ("rhs_in_state", C.c_int), ("pad", C.c_int), ("c_out", C.c_void_p)]
 
 
 class LAUNCH_INFO(C.Structure):
@@ -410,16 +410,19 @@ class Fewha:
         return self._torch.zeros(STATS_BYTES, dtype=self._torch.uint8, device=self.device)
 
     def solve(self, s, c, state, max_iter, rtol=0.0, augmented=True, recycle_all=False,
-              persistent=True, stats=None, true_res_every=0, rhs_in_state=False):
+              persistent=True, stats=None, true_res_every=0, rhs_in_state=False, c_out=None):
         """One time step; c is updated in place.  Returns the device stats buffer.
         true_res_every = N > 0 replaces the residual by b - M c after every N-th
         iteration; rhs_in_state: the state already holds this step's
         right-hand side (after fewha_deflate_warm_start), s is not read.
-        s: a CUDA tensor, or a pinned CPU tensor that the kernel reads in place."""
+        s: a CUDA tensor, or a pinned CPU tensor that the kernel reads in place.
+        c_out: optional CUDA or pinned CPU tensor that the solve kernel also
+        writes the solution into at the end of the step."""
+        co = None if c_out is None else self._vec(c_out, self.n, self.dtype, "c_out", host_ok=True)
         o = OPTS(int(max_iter), float(rtol), 1 if augmented else 0,
                  RECYCLE_ALL if recycle_all else RECYCLE_LAST,
                  LAUNCH_PERSISTENT if persistent else LAUNCH_PHASES, int(true_res_every),
-                 1 if rhs_in_state else 0)
+                 1 if rhs_in_state else 0, 0, co)
         stats = stats if stats is not None else self.new_stats()
         sp = None if (rhs_in_state and s is None) else self._vec(s, self.n_slopes, self.slope_dtype, "s",
                                                                  host_ok=True)

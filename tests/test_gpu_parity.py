@@ -258,6 +258,16 @@ def test_host_slopes_and_store(lib):
     f.store(c_h, out)
     torch.cuda.synchronize()
     assert torch.equal(out, c_h.cpu())
+    # the solve kernel writes the solution into page-locked host memory itself
+    # (fewha_solve_opts.c_out), in the persistent and the per-phase launches
+    for persistent in (True, False):
+        st_x = f.new_state(4)
+        c_x = torch.zeros_like(c_d)
+        c_out = torch.full((o.n,), float("nan"), dtype=torch.float64).pin_memory()
+        for t in range(3):
+            assert f.read_stats(f.solve(host[t], c_x, st_x, 4, persistent=persistent, c_out=c_out))["status"] == 0
+            assert torch.equal(c_out, c_x.cpu()), (persistent, t)
+        assert torch.equal(c_x, c_d)
     # pageable host memory: refused by the C ABI before anything runs
     pageable = np.ascontiguousarray(s[0], dtype=np.float64)
     stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
