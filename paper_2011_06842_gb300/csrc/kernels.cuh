@@ -370,7 +370,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_finish(const __grid_constant__ 
     __shared__ Scal sc;
     __shared__ __align__(16) Args<T, S> A;
     args_to_smem(Ap, A);
-    if (A.c_out) phase_store_c<T, S>(A);
+    if (A.c_out) phase_store_c<T, S>(A, blockIdx.x, gridDim.x);  // this launch's CTAs
     if (A.vrank() != 0) return;
     const Basis b = basis_info(A);
     int K = ldcgi(&A.rec->done) ? ldcgi(&A.rec->iters) : A.max_iter;
@@ -492,7 +492,7 @@ __device__ void solve_body(const Args<T, S> &A, Scal &sc, double *sred)
     } while (0);
     // on a device-side error the stats carry the status; the other fields are
     // then not meaningful
-    if (A.c_out) phase_store_c<T, S>(A);
+    if (A.c_out) phase_store_c<T, S>(A, rank, A.ncta);
     if (rank == 0) phase_finish<T, S>(A, b, K, sc);
 }
 

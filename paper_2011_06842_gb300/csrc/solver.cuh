@@ -1129,14 +1129,15 @@ struct TrView<T, T> {
 
 // Stats and the recycled-basis metadata for the next time step (CTA 0).
 // The solution into its optional second destination (fewha_solve_opts.c_out,
-// e.g. page-locked host memory): each CTA writes its element range once c is
-// final (after the last barrier of the time step).
+// e.g. page-locked host memory): CTA `rank` of `nranks` writes its element
+// range once c is final (after the last barrier of the time step, or in a
+// launch of its own).
 template <typename T, typename S>
-__device__ __forceinline__ void phase_store_c(const Args<T, S> &A)
+__device__ __forceinline__ void phase_store_c(const Args<T, S> &A, int rank, int nranks)
 {
     constexpr int W = VW<T>::W;
     long lo, hi;
-    cta_range_vec(A.geo.n, W, A.vrank(), A.ncta, lo, hi);
+    cta_range_vec(A.geo.n, W, rank, nranks, lo, hi);
     for (long e = lo + (long)threadIdx.x * W; e < hi; e += (long)blockDim.x * W) {
         T x[W];
         vld_cg(A.c + e, x);
